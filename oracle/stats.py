@@ -1,0 +1,169 @@
+"""FP64 NumPy oracle of the ensemble statistics (test infrastructure only).
+
+Each function states the passage it follows.  Library primitives (numpy.fft,
+numpy.sort) serve as single steps; nothing is blocked, fused or reordered
+beyond the written definition.  Velocity fields are u [M][3][N][N][N]
+(components x, y, z; array axes z, y, x) in physical units unless noted.
+"""
+import numpy as np
+
+
+def to_physical(u_lat, ulat, uc=1.0):
+    """u_phys = u_lat U_c / U_lat (lattice -> physical velocity)."""
+    return np.asarray(u_lat, dtype=np.float64) * (uc / ulat)
+
+
+def kinetic_energy(u):
+    """E_m = (1/N^3) sum_x |u|^2 / 2 (energy per unit volume, Appendix
+    "Computation of the energy spectrum": N^-d sum |u|^2 = sum Phi)."""
+    u = np.asarray(u, dtype=np.float64)
+    return 0.5 * np.mean(np.sum(u * u, axis=1), axis=(1, 2, 3))
+
+
+def enstrophy(u):
+    """Z_m = (1/N^3) sum_x |curl u|^2 / 2 with second-order central differences,
+    dx = 2 pi / N (enstrophy is not defined in the paper; this is the reading
+    used throughout the library)."""
+    u = np.asarray(u, dtype=np.float64)
+    N = u.shape[-1]
+    dx = 2 * np.pi / N
+
+    def d(field, axis):  # axis: 0 = x, 1 = y, 2 = z in physical terms
+        ax = {0: -1, 1: -2, 2: -3}[axis]
+        return (np.roll(field, -1, axis=ax) - np.roll(field, 1, axis=ax)) / (2 * dx)
+
+    ux, uy, uz = u[:, 0], u[:, 1], u[:, 2]
+    wx = d(uz, 1) - d(uy, 2)
+    wy = d(ux, 2) - d(uz, 0)
+    wz = d(uy, 0) - d(ux, 1)
+    return 0.5 * np.mean(wx * wx + wy * wy + wz * wz, axis=(1, 2, 3))
+
+
+def mean_var(u):
+    """Ensemble mean and unbiased (M - 1) variance of every velocity component at
+    every node, Eqs. (spectrum_mean), (spectrum_var) applied pointwise."""
+    u = np.asarray(u, dtype=np.float64)
+    M = u.shape[0]
+    mean = u.sum(axis=0) / M
+    var = ((u - mean) ** 2).sum(axis=0) / (M - 1)
+    return mean, var
+
+
+def _wavenumbers(N):
+    """Signed integer wavenumber of every FFT index, in K_N = {-N/2+1, ..., N/2}."""
+    k = np.fft.fftfreq(N, d=1.0 / N).astype(np.int64)
+    k[k == -N // 2] = N // 2
+    return k
+
+
+def energy_spectrum(u):
+    """Shell spectrum E_m(kappa), kappa = 0..N/2, Eqs. (dftCoeff), (energySpecDisc):
+    u~ = DFT / N^3, Phi = |u~|^2, S_kappa = {k in K_N : round(|k|) = kappa},
+    E_m(kappa) = 4 pi / |S_kappa| sum_{S_kappa} |k|^2 Phi / 2.  Returns [M][N/2+1]."""
+    u = np.asarray(u, dtype=np.float64)
+    M, N = u.shape[0], u.shape[-1]
+    k = _wavenumbers(N)
+    kz, ky, kx = np.meshgrid(k, k, k, indexing="ij")
+    k2 = (kx * kx + ky * ky + kz * kz).astype(np.float64)
+    shell = np.rint(np.sqrt(k2)).astype(np.int64)
+    out = np.zeros((M, N // 2 + 1))
+    for m in range(M):
+        phi = np.zeros((N, N, N))
+        for a in range(3):
+            uh = np.fft.fftn(u[m, a]) / N**3
+            phi += (uh * np.conj(uh)).real
+        for kappa in range(N // 2 + 1):
+            sel = shell == kappa
+            cnt = int(sel.sum())
+            out[m, kappa] = 4 * np.pi / cnt * np.sum(0.5 * k2[sel] * phi[sel])
+    return out
+
+
+def shell_counts(N):
+    """|S_kappa| for kappa = 0..N/2 over K_N."""
+    k = _wavenumbers(N)
+    kz, ky, kx = np.meshgrid(k, k, k, indexing="ij")
+    shell = np.rint(np.sqrt((kx * kx + ky * ky + kz * kz).astype(np.float64))).astype(np.int64)
+    return np.array([(shell == r).sum() for r in range(N // 2 + 1)])
+
+
+def autocorrelation(u_m):
+    """R_h = N^-3 F^-1(sum_i |F(u_i)|^2)_h, Eq. (PSD_def) (F unnormalised forward,
+    F^-1 with the factor N^-3, as numpy's ifftn)."""
+    N = u_m.shape[-1]
+    psi = np.zeros((N, N, N))
+    for a in range(3):
+        fh = np.fft.fftn(u_m[a])
+        psi += (fh * np.conj(fh)).real
+    return np.fft.ifftn(psi).real / N**3
+
+
+def structure_function_trace(u):
+    """S2_m(r), r = 0..N/2, Algorithm "SF_spectral": S2_m(r) = 1/|C_r| sum_{h in C_r}
+    2 (R_0 - R_h), C_r = {h in {-N/2+1..N/2}^3 : round(|h|) = r}.  Returns [M][N/2+1]."""
+    u = np.asarray(u, dtype=np.float64)
+    M, N = u.shape[0], u.shape[-1]
+    h = _wavenumbers(N)
+    hz, hy, hx = np.meshgrid(h, h, h, indexing="ij")
+    shell = np.rint(np.sqrt((hx * hx + hy * hy + hz * hz).astype(np.float64))).astype(np.int64)
+    out = np.zeros((M, N // 2 + 1))
+    for m in range(M):
+        R = autocorrelation(u[m])
+        for r in range(N // 2 + 1):
+            sel = shell == r
+            out[m, r] = np.sum(2.0 * (R[0, 0, 0] - R[sel])) / sel.sum()
+    return out
+
+
+def structure_function_axes(u, pmax=6):
+    """Longitudinal structure functions along the lattice axes, Eq. (structuresLocal)
+    restricted to n in {e_x, e_y, e_z} with the modulus of Eq. (structures):
+    S_p,m(r) = 1/(3 N^3) sum_x sum_a |u_a(x + r e_a) - u_a(x)|^p, r = 1..N/2,
+    p = 2..pmax.  Returns [M][pmax-1][N/2] (index r-1)."""
+    u = np.asarray(u, dtype=np.float64)
+    M, N = u.shape[0], u.shape[-1]
+    out = np.zeros((M, pmax - 1, N // 2))
+    axis_of = {0: -1, 1: -2, 2: -3}
+    for m in range(M):
+        for r in range(1, N // 2 + 1):
+            incs = [np.abs(np.roll(u[m, a], -r, axis=axis_of[a]) - u[m, a]) for a in range(3)]
+            for p in range(2, pmax + 1):
+                out[m, p - 2, r - 1] = sum(np.sum(d**p) for d in incs) / (3 * N**3)
+    return out
+
+
+def restrict(u, Q=8):
+    """Exact restriction to the common Q^3 grid (node n = j N / Q), Appendix
+    "Computation of the Wasserstein distance".  Returns [M][Q^3][3]."""
+    u = np.asarray(u, dtype=np.float64)
+    N = u.shape[-1]
+    assert N % Q == 0
+    s = N // Q
+    sub = u[:, :, ::s, ::s, ::s]  # [M][3][Q][Q][Q] (z, y, x)
+    return np.ascontiguousarray(sub.reshape(u.shape[0], 3, Q**3).transpose(0, 2, 1))
+
+
+def w1_empirical(a, b):
+    """1-D W1 between the empirical laws of samples a and b (equal weights within
+    each): the L1 distance of the two empirical CDFs over the merged support,
+    which for equal sizes is the sorted-rearrangement cost (1/M) sum |a_(m) - b_(m)|."""
+    a = np.sort(np.asarray(a, dtype=np.float64))
+    b = np.sort(np.asarray(b, dtype=np.float64))
+    allv = np.sort(np.concatenate([a, b]))
+    deltas = np.diff(allv)
+    Fa = np.searchsorted(a, allv[:-1], side="right") / a.size
+    Fb = np.searchsorted(b, allv[:-1], side="right") / b.size
+    return float(np.sum(np.abs(Fa - Fb) * deltas))
+
+
+def w1_one_point(ua, ub, Q=8, per_point=False):
+    """W_{1,1} of Algorithm "WassersteinDistance1": for each of the Q^3 points and each
+    component the 1-D W1 between the two ensembles' values, summed over components and
+    averaged over points.  ua [M_A][Q^3][3], ub [M_B][Q^3][3] (restricted fields)."""
+    G = Q**3
+    D = np.zeros((G, 3))
+    for i in range(G):
+        for c in range(3):
+            D[i, c] = w1_empirical(ua[:, i, c], ub[:, i, c])
+    total = D.sum() / G
+    return (total, D) if per_point else total

@@ -1,0 +1,172 @@
+"""NumPy front end of the C oracle stepper (test infrastructure only).
+
+Arrays are C-contiguous float64 (or complex128 for the complex-step twin).
+Population fields are [M][19][N][N][N] (x fastest) in the oracle's own
+velocity order, which ``lattice()`` reports.
+"""
+import ctypes
+
+import numpy as np
+
+from .build import load_oracle
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+def _ptr(a, dtype):
+    assert a.dtype == dtype and a.flags["C_CONTIGUOUS"], (a.dtype, a.flags)
+    return a.ctypes.data_as(_dp)
+
+
+def _arr(a, cplx=False):
+    dt = np.complex128 if cplx else np.float64
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def _fn(name, cplx=False):
+    lib = load_oracle()
+    return getattr(lib, ("orcz_" if cplx else "orc_") + name)
+
+
+def lattice():
+    """(c [19,3] int, w [19] float64, opp [19] int) of the oracle's D3Q19 set."""
+    c = np.zeros((19, 3), dtype=np.int32)
+    w = np.zeros(19)
+    opp = np.zeros(19, dtype=np.int32)
+    load_oracle().orc_lattice(c.ctypes.data_as(_ip), _ptr(w, np.float64), opp.ctypes.data_as(_ip))
+    return c.astype(np.int64), w, opp.astype(np.int64)
+
+
+def units(N, Re, Ma, Uc=1.0):
+    """Diffusive-scaling units: dict dx, ulat, dt, nu_lat, tau, omega."""
+    out = np.zeros(6)
+    fn = load_oracle().orc_units
+    fn.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp]
+    fn(int(N), float(Re), float(Ma), float(Uc), _ptr(out, np.float64))
+    return dict(zip(("dx", "ulat", "dt", "nu_lat", "tau", "omega"), out.tolist()))
+
+
+def equilibrium(rho, u):
+    """f^eq(rho, u) of Eq. (equilibrium), real arguments."""
+    u = _arr(u)
+    feq = np.zeros(19)
+    fn = _fn("equilibrium")
+    fn.argtypes = [ctypes.c_double, _dp, _dp]
+    fn(float(rho), _ptr(u, np.float64), _ptr(feq, np.float64))
+    return feq
+
+
+def shear_part(fneq):
+    fneq = _arr(fneq)
+    ds = np.zeros(19)
+    _fn("shear_part")(_ptr(fneq, np.float64), _ptr(ds, np.float64))
+    return ds
+
+
+def collide(f, omega, cplx=False):
+    """One-node KBC collision: returns (f*, gamma, Ds, Dh)."""
+    f = _arr(f, cplx)
+    dt = f.dtype
+    fs = np.zeros(19, dtype=dt)
+    ds = np.zeros(19, dtype=dt)
+    dh = np.zeros(19, dtype=dt)
+    g = np.zeros(1, dtype=dt)
+    fn = _fn("collide", cplx)
+    fn.argtypes = [_dp, ctypes.c_double, _dp, _dp, _dp, _dp]
+    fn(_ptr(f, dt), float(omega), _ptr(fs, dt), _ptr(g, dt), _ptr(ds, dt), _ptr(dh, dt))
+    return fs, g[0], ds, dh
+
+
+def init_ensemble(N, params, ulat, uc=1.0, density_mode=0, M=None, cplx=False):
+    """Equilibrium-initialised RTGV ensemble [M][19][N][N][N]; params [M][24] or None."""
+    dt = np.complex128 if cplx else np.float64
+    if params is not None:
+        params = _arr(params, cplx).reshape(-1, 24)
+        M = params.shape[0]
+    assert M is not None
+    f = np.zeros((M, 19, N, N, N), dtype=dt)
+    fn = _fn("init", cplx)
+    fn.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp]
+    fn(int(N), int(M), None if params is None else _ptr(params, dt), float(ulat), float(uc), int(density_mode),
+       _ptr(f, dt))
+    return f
+
+
+def step(f, omega, with_gamma=False):
+    """Advance f (modified in place) by one stream+collide step; optionally return gamma [M][N^3]."""
+    cplx = f.dtype == np.complex128
+    M, q, N = f.shape[0], f.shape[1], f.shape[2]
+    assert q == 19 and f.flags["C_CONTIGUOUS"]
+    scratch = np.empty_like(f)
+    g = np.zeros((M, N * N * N), dtype=f.dtype) if with_gamma else None
+    fn = _fn("step", cplx)
+    fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp]
+    fn(int(N), int(M), float(omega), _ptr(f, f.dtype), _ptr(scratch, f.dtype),
+       None if g is None else _ptr(g, f.dtype))
+    return g
+
+
+def run(f, omega, nsteps):
+    """Advance f (in place) by nsteps steps."""
+    cplx = f.dtype == np.complex128
+    M, N = f.shape[0], f.shape[2]
+    scratch = np.empty_like(f)
+    fn = _fn("run", cplx)
+    fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp]
+    fn(int(N), int(M), float(omega), int(nsteps), _ptr(f, f.dtype), _ptr(scratch, f.dtype))
+    return f
+
+
+def moments(f):
+    """(rho [M][N][N][N], u [M][3][N][N][N]) in lattice units."""
+    cplx = f.dtype == np.complex128
+    M, N = f.shape[0], f.shape[2]
+    rho = np.zeros((M, N, N, N), dtype=f.dtype)
+    u = np.zeros((M, 3, N, N, N), dtype=f.dtype)
+    fn = _fn("moments", cplx)
+    fn.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
+    fn(int(N), int(M), _ptr(f, f.dtype), _ptr(rho, f.dtype), _ptr(u, f.dtype))
+    return rho, u
+
+
+def energy(u, ulat, uc=1.0):
+    """(E [M], Z [M]): kinetic energy and enstrophy per sample, physical units."""
+    cplx = u.dtype == np.complex128
+    u = np.ascontiguousarray(u)
+    M, N = u.shape[0], u.shape[2]
+    E = np.zeros(M, dtype=u.dtype)
+    Z = np.zeros(M, dtype=u.dtype)
+    fn = _fn("energy", cplx)
+    fn.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp]
+    fn(int(N), int(M), _ptr(u, u.dtype), float(ulat), float(uc), _ptr(E, u.dtype), _ptr(Z, u.dtype))
+    return E, Z
+
+
+def hrel(f):
+    """Global relative entropy H_rel, Eq. (relEntropy2)."""
+    f = _arr(f)
+    M, N = f.shape[0], f.shape[2]
+    fn = load_oracle().orc_hrel
+    fn.argtypes = [ctypes.c_int, ctypes.c_int, _dp]
+    fn.restype = ctypes.c_double
+    return fn(int(N), int(M), _ptr(f, np.float64))
+
+
+def complex_step_grad(N, params, ulat, omega, nsteps, objective="energy", h=1e-30, uc=1.0):
+    """d J / d X (J = mean kinetic energy or enstrophy of each sample at step nsteps)
+    by complex-step differentiation of the whole oracle: J(X + i h e_k) has imaginary
+    part h dJ/dX_k to machine precision.  Returns [M][24]."""
+    params = np.asarray(params, dtype=np.float64).reshape(-1, 24)
+    M = params.shape[0]
+    grad = np.zeros((M, 24))
+    for k in range(24):
+        p = params.astype(np.complex128)
+        p[:, k] += 1j * h
+        f = init_ensemble(N, p, ulat, uc, cplx=True)
+        run(f, omega, nsteps)
+        _, u = moments(f)
+        E, Z = energy(u, ulat, uc)
+        J = E if objective == "energy" else Z
+        grad[:, k] = J.imag / h
+    return grad

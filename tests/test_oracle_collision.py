@@ -1,0 +1,208 @@
+"""Pins of the oracle's lattice, equilibrium and KBC collision against what the
+paper and the mathematics fix (no GPU needed)."""
+from fractions import Fraction
+from itertools import product
+
+import numpy as np
+import pytest
+
+import ensemble_inputs as gen
+import oracle
+
+
+def test_velocity_set_is_d3q19():
+    """D3Q19 (Sec. "Entropic multi-relaxation"): the 19 vectors of {-1,0,1}^3 with
+    |c|^2 <= 2, opposite pairs, weights 1/3, 1/18, 1/36."""
+    c, w, opp = oracle.lattice()
+    assert c.shape == (19, 3)
+    assert len({tuple(v) for v in c}) == 19
+    assert all((v * v).sum() <= 2 for v in c)
+    for i in range(19):
+        assert (c[opp[i]] == -c[i]).all()
+    n2 = (c * c).sum(1)
+    for i in range(19):
+        assert w[i] == {0: 1 / 3, 1: 1 / 18, 2: 1 / 36}[int(n2[i])]
+
+
+def test_weight_moments_isotropic_exact():
+    """Lattice moments (exact rationals): sum w = 1, sum w c = 0, sum w c_a c_b = d_ab/3,
+    sum w c_a^2 c_b^2 = 1/9 (a != b), sum w c_a^4 = 1/3, all odd moments 0."""
+    c, w, _ = oracle.lattice()
+    wf = [Fraction(1, 3) if abs(x - 1 / 3) < 1e-15 else (Fraction(1, 18) if abs(x - 1 / 18) < 1e-15
+                                                          else Fraction(1, 36)) for x in w]
+    assert sum(wf) == 1
+    for a in range(3):
+        assert sum(wf[i] * c[i, a] for i in range(19)) == 0
+        for b in range(3):
+            s = sum(wf[i] * c[i, a] * c[i, b] for i in range(19))
+            assert s == (Fraction(1, 3) if a == b else 0)
+            for g in range(3):
+                assert sum(wf[i] * c[i, a] * c[i, b] * c[i, g] for i in range(19)) == 0
+            if a != b:
+                assert sum(wf[i] * c[i, a] ** 2 * c[i, b] ** 2 for i in range(19)) == Fraction(1, 9)
+        assert sum(wf[i] * c[i, a] ** 4 for i in range(19)) == Fraction(1, 3)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_equilibrium_moments(seed):
+    """Eq. (equilibrium) reproduces rho, rho u and rho (c_s^2 delta + u u)."""
+    c, w, _ = oracle.lattice()
+    r = gen.uniform(seed, 4)
+    rho = 1.0 + 0.1 * r[0]
+    u = 0.1 * r[1:]
+    feq = oracle.equilibrium(rho, u)
+    assert abs(feq.sum() - rho) <= 1e-15 * rho
+    np.testing.assert_allclose(c.T @ feq, rho * u, rtol=0, atol=1e-16)
+    P = np.einsum("ia,ib,i->ab", c, c, feq)
+    np.testing.assert_allclose(P, rho * (np.eye(3) / 3 + np.outer(u, u)), rtol=0, atol=2e-16)
+
+
+def _moment_matrix(c):
+    """Raw monomial moment basis of D3Q19, Eq. (momentDefin): 1, c_a, c_a c_b (a<=b),
+    c_a c_b^2 (a != b), c_a^2 c_b^2 (a < b): 1 + 3 + 6 + 6 + 3 = 19 rows."""
+    rows = [np.ones(19)]
+    rows += [c[:, a].astype(float) for a in range(3)]
+    rows += [(c[:, a] * c[:, b]).astype(float) for a in range(3) for b in range(a, 3)]
+    rows += [(c[:, a] * c[:, b] ** 2).astype(float) for a in range(3) for b in range(3) if a != b]
+    rows += [(c[:, a] ** 2 * c[:, b] ** 2).astype(float) for a in range(3) for b in range(a + 1, 3)]
+    return np.array(rows)
+
+
+@pytest.mark.parametrize("seed", [3, 4, 5, 6])
+def test_shear_part_is_the_moment_space_projection(seed):
+    """The shear part carries exactly the deviatoric second moments of f^neq (tensors N,
+    Pi of Table "frequencySummary") and no other moment of the D3Q19 basis: it equals
+    M^-1 m_s with m_s = (0, 0, dev(P), 0, 0) for the invertible raw-moment matrix M."""
+    c, w, _ = oracle.lattice()
+    Mm = _moment_matrix(c)
+    assert np.linalg.matrix_rank(Mm) == 19
+    fneq = 1e-3 * gen.uniform(seed, 19)
+    ds = oracle.shear_part(fneq)
+    P = np.einsum("ia,ib,i->ab", c, c, fneq)
+    D = P - np.eye(3) * np.trace(P) / 3
+    m_s = np.zeros(19)
+    k = 4
+    for a in range(3):
+        for b in range(a, 3):
+            m_s[k] = D[a, b]
+            k += 1
+    expect = np.linalg.solve(Mm, m_s)
+    np.testing.assert_allclose(ds, expect, rtol=0, atol=1e-17)
+    # invariants of the reading
+    assert abs(ds.sum()) < 1e-18
+    np.testing.assert_allclose(c.T @ ds, 0, atol=1e-18)
+    np.testing.assert_allclose(np.einsum("ia,ib,i->ab", c, c, ds), D, atol=1e-18)
+
+
+def _random_node(seed, amp=1e-2, u_scale=0.05, zero_u=False):
+    """A positive population vector near equilibrium: w (1 + amp r) on top of f^eq."""
+    c, w, _ = oracle.lattice()
+    r = gen.uniform(seed, 23)
+    rho = 1.0 + 0.02 * r[0]
+    u = np.zeros(3) if zero_u else u_scale * r[1:4]
+    f = oracle.equilibrium(rho, u) + amp * w * r[4:23]
+    if zero_u:
+        # remove the mass and momentum the noise added so that rho = 1 + .. and u = 0
+        f = f - w * (f.sum() - rho)
+        j = c.T @ f
+        f = f - 3 * w * (c @ j)
+    return f
+
+
+@pytest.mark.parametrize("seed", [10, 11, 12])
+def test_collision_conserves_mass_and_momentum(seed):
+    c, w, _ = oracle.lattice()
+    f = _random_node(seed)
+    fs, g, ds, dh = oracle.collide(f, omega=1.7)
+    assert abs(fs.sum() - f.sum()) <= 1e-15
+    np.testing.assert_allclose(c.T @ fs, c.T @ f, rtol=0, atol=1e-16)
+
+
+def test_equilibrium_is_a_fixed_point():
+    c, w, _ = oracle.lattice()
+    feq = oracle.equilibrium(1.01, np.array([0.03, -0.02, 0.01]))
+    fs, g, ds, dh = oracle.collide(feq, omega=1.9)
+    np.testing.assert_allclose(fs, feq, rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("seed", [13, 14])
+def test_omega_one_gives_bgk(seed):
+    """At omega_nu = 1, gamma = 2/1 - 0 = 2 and KBC = BGK (Eq. (kbcCollision), gamma = 2)."""
+    f = _random_node(seed)
+    fs, g, ds, dh = oracle.collide(f, omega=1.0)
+    assert g == 2.0
+    rho, u = f.sum(), None
+    c, w, _ = oracle.lattice()
+    u = (c.T @ f) / rho
+    feq = oracle.equilibrium(rho, u)
+    np.testing.assert_allclose(fs, f - 1.0 * (f - feq), rtol=2e-15, atol=1e-17)
+
+
+@pytest.mark.parametrize("seed", [21, 22])
+def test_gamma_two_is_bgk(seed):
+    """Eq. (kbcCollision) at gamma = 2: f - omega Ds - omega Dh = f - omega f^neq."""
+    c, w, _ = oracle.lattice()
+    f = _random_node(seed)
+    omega = 1.6
+    fs, g, ds, dh = oracle.collide(f, omega)
+    rho = f.sum()
+    feq = oracle.equilibrium(rho, (c.T @ f) / rho)
+    np.testing.assert_allclose(ds + dh, f - feq, rtol=0, atol=1e-17)
+    np.testing.assert_allclose(f - omega * ds - omega * dh, f - omega * (f - feq), rtol=2e-15, atol=1e-17)
+
+
+def _bisect(fun, lo, hi, iters=200):
+    flo = fun(lo)
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        fm = fun(mid)
+        if (fm > 0) == (flo > 0):
+            lo, flo = mid, fm
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+@pytest.mark.parametrize("seed", range(30, 30 + 64))
+def test_closed_form_gamma_is_root_of_linearised_stationarity(seed):
+    """Eq. (entropyControl) is the root in gamma of the first-order stationarity condition
+    sum_i Dh_i (f*_i(gamma) - f^eq_i) / f^eq_i = 0 of Eq. (kbc_entropy); found here by
+    bisection on the 4^3 = 64 random near-equilibrium nodes of a small lattice."""
+    c, w, _ = oracle.lattice()
+    f = _random_node(seed, amp=5e-3)
+    omega = 1.95
+    fs, g, ds, dh = oracle.collide(f, omega)
+    rho = f.sum()
+    feq = oracle.equilibrium(rho, (c.T @ f) / rho)
+
+    def cond(gp):
+        fstar = f - omega * ds - 0.5 * omega * gp * dh
+        return np.sum(dh * (fstar - feq) / feq)
+
+    root = _bisect(cond, -50.0, 50.0)
+    assert abs(root - g) <= 1e-12 * abs(g)
+    np.testing.assert_allclose(fs, f - omega * ds - 0.5 * omega * g * dh, rtol=2e-15, atol=1e-17)
+
+
+def test_closed_form_gamma_approaches_exact_entropic_minimiser():
+    """The exact gamma minimises H(f*) = sum f* ln(f*/w), Eq. (kbc_entropy).  At u = 0 the
+    closed form is its first-order approximation: the gap shrinks in proportion to the
+    non-equilibrium amplitude."""
+    omega = 1.9
+    gaps = []
+    for amp in (1e-2, 1e-3, 1e-4):
+        gap_amp = []
+        for seed in (40, 41, 42):
+            f = _random_node(seed, amp=amp, zero_u=True)
+            fs, g, ds, dh = oracle.collide(f, omega)
+            c, w, _ = oracle.lattice()
+
+            def dH(gp):
+                fstar = f - omega * ds - 0.5 * omega * gp * dh
+                return np.sum(-0.5 * omega * dh * (np.log(fstar / w) + 1.0))
+
+            g_exact = _bisect(dH, g - 5.0, g + 5.0)
+            gap_amp.append(abs(g_exact - g))
+        gaps.append(max(gap_amp))
+    r1, r2 = gaps[0] / gaps[1], gaps[1] / gaps[2]
+    assert 5 < r1 < 20 and 5 < r2 < 20, gaps
