@@ -1,0 +1,332 @@
+"""Benchmark of the Monte Carlo KBC LBM hot path on one GB300 (or N, one ensemble per rank).
+
+Workload (default): M = 64 randomized Taylor-Green samples on 64^3, Re = 800, Ma = 0.025,
+shifted FP32 populations, pull streaming; the whole ensemble advances in one launch per
+lattice step.  One bench step = one output interval: S = 50 fused stream+collide updates
+of every sample, then the ensemble reductions the interval feeds (per-sample kinetic
+energy E_m(t), ensemble mean and variance velocity fields, all FP64).
+
+metric: ensemble GLUPS (lattice-node updates per second, summed over ranks), with the
+stepper's achieved HBM bandwidth against the measured copy bandwidth.  Inputs (one
+ensemble of 2.55 GB of populations) exceed the 129 MB L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="rtgv_64cube_x64_fp32_pull", N=64, M=64, Re=800.0, Ma=0.025, precision="fp32",
+                pattern="pull", updates_per_step=50, seed=1)
+BYTES_PER_LU = {"fp64": 2 * 19 * 8, "fp32": 2 * 19 * 4, "fp16": 2 * 19 * 2}
+STEPPER_SOURCES = ["paper_2608_23786_gb300/csrc/stepper.cu", "paper_2608_23786_gb300/csrc/collide.cuh",
+                   "paper_2608_23786_gb300/csrc/storage.cuh", "paper_2608_23786_gb300/csrc/lattice.cuh"]
+# DRAM bytes (read + write) per launch of the stepper on this workload from one ncu capture of the
+# kernel built from sources with this digest; reported as null when the sources differ.
+NCU_TRAFFIC = {"sha256": None, "bytes_per_launch": None}
+
+
+def stepper_digest():
+    h = hashlib.sha256()
+    for p in STEPPER_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                if out.returncode == 0 and out.stdout.strip():
+                    self.samples.append([s.strip() for s in out.stdout.strip().split(",")])
+            except (OSError, subprocess.SubprocessError):
+                return
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[2 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def oracle_sample(wl, budget_s=10.0, max_samples=2):
+    """The FP64 oracle as it stands on a bounded sample of the workload: `max_samples` samples,
+    as many updates as fit the time budget (whole output intervals are not required), then the
+    same reductions.  Returns (GLUPS, description, cores)."""
+    import oracle
+    from oracle import stats
+    import ensemble_inputs as gen
+    un = oracle.units(wl["N"], wl["Re"], wl["Ma"])
+    X = gen.draw_params(wl["seed"], max_samples)
+    f = oracle.init_ensemble(wl["N"], X, un["ulat"])
+    lu, steps = 0, 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        oracle.step(f, un["omega"])
+        steps += 1
+        lu += max_samples * wl["N"] ** 3
+    _, u = oracle.moments(f)
+    up = stats.to_physical(u, un["ulat"])
+    stats.kinetic_energy(up)
+    stats.mean_var(up)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    desc = (f"{max_samples} of {wl['M']} samples x {steps} of {wl['updates_per_step']} updates of "
+            f"{wl['N']}^3, then E(t) and mean/var; FP64 C oracle, OpenMP over planes")
+    return lu / dt / 1e9, desc, cores
+
+
+def run_reference(args, wl):
+    """Reference arm: the FP64 oracle timed on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from oracle import stats
+    import ensemble_inputs as gen
+    un = oracle.units(wl["N"], wl["Re"], wl["Ma"])
+    ms, upd = 1, 4  # bounded sample per step: 1 sample x 4 updates of 64^3, then the reductions
+    X = gen.draw_params(wl["seed"], ms)
+    f = oracle.init_ensemble(wl["N"], X, un["ulat"])
+
+    def one():
+        for _ in range(upd):
+            oracle.step(f, un["omega"])
+        _, u = oracle.moments(f)
+        up = stats.to_physical(u, un["ulat"])
+        stats.kinetic_energy(up)
+
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    dt = time.perf_counter() - t0
+    value = ms * wl["N"] ** 3 * upd * args.steps / dt / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = f"{ms} of {wl['M']} samples x {upd} of {wl['updates_per_step']} updates per step, then E(t)"
+    print(json.dumps({
+        "impl": "reference", "metric": "ensemble_glups", "value": value, "unit": "GLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["name"], "N": wl["N"], "M": wl["M"], "Re": wl["Re"], "Ma": wl["Ma"],
+                   "updates_per_step": wl["updates_per_step"], "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp16", "fp64"])
+    ap.add_argument("--pattern", default=None, choices=["pull", "aa"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = dict(WORKLOAD)
+    if args.precision:
+        wl["precision"] = args.precision
+    if args.pattern:
+        wl["pattern"] = args.pattern
+    if args.precision or args.pattern:
+        wl["name"] = f"rtgv_64cube_x64_{wl['precision']}_{wl['pattern']}"
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2608_23786_gb300 import Ensemble, mclbm
+    import ensemble_inputs as gen
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mclbm.load()
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    S = wl["updates_per_step"]
+    # each rank owns an independent ensemble: samples rank*M .. rank*M + M - 1 of the Philox stream
+    X = gen.draw_params(wl["seed"], wl["M"], first_sample=rank * wl["M"])
+    ens = Ensemble(wl["N"], wl["M"], Re=wl["Re"], Ma=wl["Ma"], precision=wl["precision"], pattern=wl["pattern"],
+                   seed=wl["seed"], device=dev, stream=stream).init(X)
+    mean = torch.empty((3,) + (wl["N"],) * 3, dtype=torch.float64, device=dev)
+    var = torch.empty_like(mean)
+    E = np.zeros(wl["M"])
+    kernels_per_step = S + 2 + 1  # S stepper launches, energy (partials + reduce), mean/var
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+
+    def one_step(i=None):
+        if i is not None:
+            ev[i][0].record(stream)
+        mclbm.mclbm_step(ens.ctx, S)
+        if i is not None:
+            ev[i][1].record(stream)
+        mclbm.mclbm_mean_var(ens.ctx, mean.data_ptr(), var.data_ptr())
+        mclbm.mclbm_energy(ens.ctx, E)  # synchronises the stream (returns host data)
+
+    for _ in range(max(3, args.warmup)):
+        one_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        t_start.record(stream)
+        for i in range(args.steps):
+            one_step(i)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    stepper_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / (args.steps * S)  # per launch
+    if world > 1:
+        t = torch.tensor([elapsed], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = t.item()
+    lu_per_rank = wl["M"] * wl["N"] ** 3 * S * args.steps
+    value = lu_per_rank * world / elapsed / 1e9
+
+    # ---- end to end through the public API with host buffers: params H2D from pinned memory,
+    # init + S updates + reductions, E and the mean/var fields D2H every step
+    params_h = torch.from_numpy(X.copy()).pin_memory()
+    E_h = torch.empty(wl["M"], dtype=torch.float64).pin_memory()
+    mv_h = torch.empty((2, 3) + (wl["N"],) * 3, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        mclbm.mclbm_init_ensemble(ens.ctx, params_h.numpy())  # host parameters, H2D inside the call
+        mclbm.mclbm_step(ens.ctx, S)
+        mclbm.mclbm_mean_var(ens.ctx, mean.data_ptr(), var.data_ptr())
+        e = np.zeros(wl["M"])
+        mclbm.mclbm_energy(ens.ctx, e)
+        E_h.copy_(torch.from_numpy(e))
+        mv_h[0].copy_(mean, non_blocking=True)
+        mv_h[1].copy_(var, non_blocking=True)
+        stream.synchronize()
+
+    e2e_steps = max(2, args.steps // 4)
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_dt = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_dt], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_dt = t.item()
+    e2e_value = wl["M"] * wl["N"] ** 3 * S * e2e_steps * world / e2e_dt / 1e9
+
+    # ---- plain FP64 single-sample GPU stepper on the same GPU (the method without the ensemble
+    # batching or shifted storage), 64^3 x 1
+    plain = Ensemble(wl["N"], 1, Re=wl["Re"], Ma=wl["Ma"], precision="fp64", pattern="pull", device=dev,
+                     stream=stream).init(X[:1])
+    plain.step(5)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    plain.step(40)
+    b.record(stream)
+    torch.cuda.synchronize()
+    plain_glups = wl["N"] ** 3 * 40 / (a.elapsed_time(b) / 1e3) / 1e9
+    del plain
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peaks, peak_kind = measured_peaks()
+    bpl = BYTES_PER_LU[wl["precision"]] * wl["M"] * wl["N"] ** 3
+    achieved = bpl / stepper_s / 1e9
+    digest = stepper_digest()
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sha256"] == digest else None
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        v, desc, cores = oracle_sample(wl)
+        cpu = {"value": v, "unit": "GLUPS", "cores": cores, "kind": "oracle", "sample": desc}
+    out = {
+        "metric": "ensemble_glups", "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if wl["precision"] == "fp32" else
+        ("f16-storage/f32" if wl["precision"] == "fp16" else "f64"), "data": "synthetic",
+        "config": {"workload": wl["name"], "N": wl["N"], "M_per_gpu": wl["M"], "Re": wl["Re"], "Ma": wl["Ma"],
+                   "storage": wl["precision"], "streaming": wl["pattern"], "updates_per_step": S,
+                   "reductions_per_step": ["E_m(t)", "mean/var fields"], "l2": "inputs (2.55 GB) larger than L2"},
+        "roofline": {"kernel": "k_step_pull<float>" if wl["pattern"] == "pull" else "k_step_aa<float>",
+                     "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "peak_kind": peak_kind,
+                     "traffic": traffic, "algorithmic_bytes_per_launch": bpl,
+                     "avg_launch_ms": stepper_s * 1e3, "stepper_glups": wl["M"] * wl["N"] ** 3 / stepper_s / 1e9},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "GLUPS", "h2d_bytes_per_step": int(params_h.numel() * 8),
+                "d2h_bytes_per_step": int(E_h.numel() * 8 + mv_h.numel() * 8)},
+        "gpu_launches": kernels_per_step * args.steps,
+        "fp64_plain_single_sample": {"value": plain_glups, "unit": "GLUPS", "N": wl["N"], "M": 1},
+        "clocks": clk.summary(),
+        "stepper_sources_sha256": digest,
+    }
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

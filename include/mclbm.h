@@ -1,0 +1,225 @@
+/*
+ * mclbm.h - C ABI of the GB300 Monte Carlo KBC lattice Boltzmann library.
+ *
+ * The calls follow the paper's statement of the problem (Sec. "Discretization
+ * and well-prepared initial data"): the statistical solution at time t is the
+ * push-forward mu_t = (S(t) o I) # (U[-w, w]^24) of 24 uniform parameters per
+ * sample through the equilibrium initialisation I (Eq. (initialPopulations))
+ * and the KBC lattice Boltzmann solution operator S(t) (Eqs. (lbIteration),
+ * (kbcCollision), (entropyControl)).  A context holds one ensemble of M
+ * independent samples on an N^3 periodic lattice (D3Q19) at one viscosity.
+ *
+ * Conventions shared by every call:
+ *  - Return value: MCLBM_OK (0) or a negative mclbm_status.  On error the
+ *    thread-local message of mclbm_last_error() says what failed; no call ever
+ *    aborts the process.
+ *  - Device memory is allocated by the caller and borrowed: the library never
+ *    calls cudaMalloc.  Sizes come from mclbm_required_bytes().  Buffers must be
+ *    256-byte aligned and stay valid until mclbm_destroy().
+ *  - Every device call is enqueued on the CUDA stream given at creation (NULL =
+ *    legacy default stream).  Calls that return host data synchronise that
+ *    stream before returning; the others return as soon as work is enqueued.
+ *  - A context may be used by one host thread at a time.
+ *  - Arrays are C order.  A scalar field on the lattice is [z][y][x] (x fastest),
+ *    node (x, y, z) at physical position 2 pi (x, y, z) / N.
+ *  - Velocities returned by the library are physical: u_phys = u_lat U_c / U_lat.
+ */
+#ifndef MCLBM_H
+#define MCLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MCLBM_API __attribute__((visibility("default")))
+#else
+#define MCLBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MCLBM_OK = 0,
+    MCLBM_ERR_INVALID_ARG = -1, /* null pointer, out-of-range value               */
+    MCLBM_ERR_UNSTABLE_TAU = -2, /* tau <= 1/2 (omega_nu outside (0, 2))         */
+    MCLBM_ERR_OOM = -3,          /* a caller buffer is smaller than required      */
+    MCLBM_ERR_CUDA = -4,         /* a CUDA runtime call failed                    */
+    MCLBM_ERR_NONFINITE = -5,    /* a NaN/Inf was found in the state or a result  */
+    MCLBM_ERR_TIMEOUT = -6,      /* a bounded device wait gave up                 */
+    MCLBM_ERR_SHAPE = -7,        /* N not a power of two >= 8, N % Q != 0, M < 2  */
+    MCLBM_ERR_IO = -8            /* checkpoint file could not be read or written  */
+} mclbm_status;
+
+/* Population storage (Assumption "Uniform low Mach regime" (i): f = w (1 + eps g)
+ * motivates storing the small deviation h_i = f_i / w_i - 1). */
+enum {
+    MCLBM_FP64 = 0, /* raw f_i in FP64, FP64 arithmetic (the plain method)           */
+    MCLBM_FP32 = 1, /* h_i in FP32, FP32 collision arithmetic                        */
+    MCLBM_FP16 = 2  /* h_i in FP16 (round to nearest), FP32 collision arithmetic     */
+};
+
+/* Streaming pattern. */
+enum {
+    MCLBM_PULL = 0, /* two lattices, gather f_i(x - c_i): pop bytes = 2 Q b N^3 M    */
+    MCLBM_AA = 1    /* one lattice updated in place, alternating even/odd access    */
+};
+
+/* Ensemble configuration; copied at mclbm_create, caller keeps ownership. */
+typedef struct {
+    int32_t N;            /* nodes per direction, power of two, 8 <= N <= 1024        */
+    int32_t M;            /* samples, >= 1                                            */
+    int32_t precision;    /* MCLBM_FP64 / MCLBM_FP32 / MCLBM_FP16                     */
+    int32_t pattern;      /* MCLBM_PULL / MCLBM_AA                                    */
+    double nu;            /* physical kinematic viscosity eps = U_c l_c / Re (l_c = 1) */
+    double Ma;            /* Mach number: U_lat = Ma c_s.  Ignored when dt > 0         */
+    double dt;            /* physical time step; 0 -> dt = U_lat dx / U_c             */
+    double U_c;           /* reference velocity (1)                                   */
+    double width;         /* support w of the uniform parameters (0.025)              */
+    uint64_t seed;        /* key of the Philox4x64-10 parameter draw                  */
+    int32_t init_density; /* 0: rho_0 = 1 (the paper); 1: TGV pressure density       */
+    int32_t reserved;     /* must be 0                                                */
+} mclbm_config;
+
+/* Derived diffusive-scaling units (Table "frequencySummary", Tables "params1/2"). */
+typedef struct {
+    double dx;       /* 2 pi / N                                 */
+    double U_lat;    /* lattice velocity scale, Ma c_s            */
+    double dt;       /* U_lat dx / U_c                            */
+    double nu_lat;   /* nu dt / dx^2                              */
+    double tau;      /* 3 nu_lat + 1/2                            */
+    double omega;    /* omega_nu = 2 c_s^2 / (2 nu_lat + c_s^2)   */
+} mclbm_units;
+
+typedef struct mclbm_ctx mclbm_ctx; /* opaque, library-owned */
+
+/* Library version string (static storage). */
+MCLBM_API const char* mclbm_version(void);
+
+/* Thread-local message of the last failed call on this thread (library-owned,
+ * valid until the next call on the same thread). */
+MCLBM_API const char* mclbm_last_error(void);
+
+/* D3Q19 velocity set in the library's storage order: c [19][3] and w [19]
+ * (either may be NULL).  Host pointers. */
+MCLBM_API int mclbm_lattice(int32_t* c, double* w);
+
+/* Units of a configuration without creating a context (Sec. "Numerical validation
+ * of convergence rates": eps = 2 pi / N, Re_N coupling; Table "frequencySummary").
+ * Errors: INVALID_ARG, UNSTABLE_TAU. */
+MCLBM_API int mclbm_compute_units(const mclbm_config* cfg, mclbm_units* out);
+
+/* Bytes of caller-allocated device memory a configuration needs:
+ * pop_bytes for the population lattice(s), work_bytes for reductions and
+ * statistics (velocity field, FFT buffers, partial sums of one sample at a time).
+ * Errors: INVALID_ARG, SHAPE, UNSTABLE_TAU. */
+MCLBM_API int mclbm_required_bytes(const mclbm_config* cfg, size_t* pop_bytes, size_t* work_bytes);
+
+/* Create a context over caller-owned device buffers d_pop (>= pop_bytes) and
+ * d_work (>= work_bytes), enqueuing on cuda_stream (a cudaStream_t, may be NULL).
+ * The device current at this call is the context's device.  No kernel runs yet.
+ * Errors: INVALID_ARG, SHAPE, UNSTABLE_TAU, OOM (buffers too small), CUDA. */
+MCLBM_API int mclbm_create(const mclbm_config* cfg, void* d_pop, size_t pop_bytes, void* d_work, size_t work_bytes,
+                 void* cuda_stream, mclbm_ctx** out);
+
+/* Release the context (not the caller's buffers).  NULL is ignored. */
+MCLBM_API void mclbm_destroy(mclbm_ctx* ctx);
+
+/* Units of an existing context. */
+MCLBM_API int mclbm_get_units(const mclbm_ctx* ctx, mclbm_units* out);
+
+/* Ensemble initialisation I (Eqs. (tgv_init_velo), (alpha_perturbation),
+ * (initialRTGV), (initialPopulations)): per sample m the 24 parameters
+ * X[m][8 alpha + 4 i + 2 j + k] give u_0 = (U_lat / U_c)(u_det + s(X_m)) at every
+ * node and f_0 = f^eq(rho_0, u_0).  params: host [M][24] or NULL; NULL draws
+ * X ~ U[-w, w] from Philox4x64-10 keyed by (seed, 0), counters (b, m, 0, 0),
+ * b = 0..5, U = (x >> 11) 2^-53, X = w (2U - 1).  Resets the step counter.
+ * Errors: INVALID_ARG, CUDA. */
+MCLBM_API int mclbm_init_ensemble(mclbm_ctx* ctx, const double* params);
+
+/* The parameter draw on its own (host only, no GPU needed): samples
+ * first_sample .. first_sample + M - 1 of the Philox4x64-10 stream described
+ * above, out [M][24].  Errors: INVALID_ARG. */
+MCLBM_API int mclbm_draw_params(uint64_t seed, int32_t first_sample, int32_t M, double width, double* out);
+
+/* The deterministic Taylor-Green initial state (all 24 parameters zero). */
+MCLBM_API int mclbm_init_tgv(mclbm_ctx* ctx);
+
+/* Copy the ensemble's parameters to host params [M][24]. */
+MCLBM_API int mclbm_get_params(const mclbm_ctx* ctx, double* params);
+
+/* Advance every sample by nsteps fused stream+collide steps (Eq. (lbIteration)
+ * with the KBC collision Eq. (kbcCollision) and the closed-form stabiliser
+ * Eq. (entropyControl)).  Enqueued only.  Errors: INVALID_ARG, CUDA. */
+MCLBM_API int mclbm_step(mclbm_ctx* ctx, int64_t nsteps);
+
+/* Number of steps taken since the last initialisation. */
+MCLBM_API int64_t mclbm_steps_taken(const mclbm_ctx* ctx);
+
+/* Pre-collision populations f_i(x, t) of one sample as FP64 (not shifted), in the
+ * library's velocity order: d_out device [19][N][N][N].  Enqueued only. */
+MCLBM_API int mclbm_get_populations(const mclbm_ctx* ctx, int32_t sample, double* d_out);
+
+/* Overwrite the pre-collision populations of one sample from device FP64
+ * d_in [19][N][N][N] (rounded to the storage precision).  Enqueued only. */
+MCLBM_API int mclbm_set_populations(mclbm_ctx* ctx, int32_t sample, const double* d_in);
+
+/* Macroscopic moments at the current integer step, pre-collision (Definition of the
+ * moments: rho = sum f, rho u = sum c f): d_rho [N^3] (may be NULL) and d_u [3][N^3]
+ * physical velocity, FP64 device buffers, for one sample.  Enqueued only. */
+MCLBM_API int mclbm_moments(const mclbm_ctx* ctx, int32_t sample, double* d_rho, double* d_u);
+
+/* Kinetic energy E_m = N^-3 sum |u|^2 / 2 and (if Z != NULL) enstrophy
+ * Z_m = N^-3 sum |curl u|^2 / 2 (second-order central differences, dx = 2 pi / N)
+ * of every sample, physical units, FP64 host arrays [M].  Synchronises.
+ * Reductions are in a fixed order (run-to-run bitwise reproducible). */
+MCLBM_API int mclbm_energy(mclbm_ctx* ctx, double* E, double* Z);
+
+/* Ensemble mean and unbiased (M - 1) variance of the physical velocity at every
+ * node (Eqs. (spectrum_mean), (spectrum_var) applied pointwise): d_mean, d_var
+ * device FP64 [3][N^3].  Errors: SHAPE if M < 2.  Enqueued only. */
+MCLBM_API int mclbm_mean_var(mclbm_ctx* ctx, double* d_mean, double* d_var);
+
+/* Shell energy spectrum (Eqs. (dftCoeff), (energySpecDisc)) of every sample:
+ * E [M][N/2 + 1] host FP64, kappa = 0..N/2.  Synchronises. */
+MCLBM_API int mclbm_spectrum(mclbm_ctx* ctx, double* E);
+
+/* Trace second-order structure function of Algorithm "SF_spectral" (Lemma
+ * "Spectral approximation of structure functions") of every sample:
+ * S2 [M][N/2 + 1] host FP64, r = 0..N/2 (grid units).  Synchronises. */
+MCLBM_API int mclbm_sf_trace(mclbm_ctx* ctx, double* S2);
+
+/* Longitudinal structure functions along the lattice axes (Eq. (structuresLocal)
+ * with n in {e_x, e_y, e_z}, modulus as in Eq. (structures)):
+ * S [M][pmax - 1][N/2] host FP64, p = 2..pmax (2 <= pmax <= 8), r = 1..N/2.
+ * Synchronises. */
+MCLBM_API int mclbm_sf_axes(mclbm_ctx* ctx, int32_t pmax, double* S);
+
+/* Exact restriction of the physical velocity to the common Q^3 grid (node n = j N / Q,
+ * Appendix "Computation of the Wasserstein distance"): d_out device FP64
+ * [M][Q^3][3], point index (jz Q + jy) Q + jx.  Errors: SHAPE if N % Q != 0. */
+MCLBM_API int mclbm_restrict(const mclbm_ctx* ctx, int32_t Q, double* d_out);
+
+/* W_{1,1} of Algorithm "WassersteinDistance1" between the one-point laws of two
+ * ensembles A and B (they may differ in N and M): restrict both to Q^3 points, for
+ * every point and component the 1-D W1 of the two empirical laws (L1 distance of the
+ * empirical CDFs, Eq. (wassersteinPermutations) for equal M), summed over components
+ * and averaged over points.  W: host scalar.  per_point: host [Q^3][3] or NULL.
+ * Uses A's work buffer and stream; synchronises.  Errors: SHAPE. */
+MCLBM_API int mclbm_w1_1pt(mclbm_ctx* A, const mclbm_ctx* B, int32_t Q, double* W, double* per_point);
+
+/* Same on restricted fields already on the device: d_a [MA][G][3], d_b [MB][G][3]
+ * FP64; uses d_work (>= mclbm_w1_work_bytes(MA, MB, G)) on cuda_stream. */
+MCLBM_API size_t mclbm_w1_work_bytes(int32_t MA, int32_t MB, int32_t G);
+MCLBM_API int mclbm_w1_restricted(const double* d_a, int32_t MA, const double* d_b, int32_t MB, int32_t G, void* d_work,
+                        size_t work_bytes, void* cuda_stream, double* W, double* per_point);
+
+/* Scan every stored population for NaN/Inf.  Returns MCLBM_OK or
+ * MCLBM_ERR_NONFINITE.  Synchronises. */
+MCLBM_API int mclbm_check_finite(mclbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCLBM_H */

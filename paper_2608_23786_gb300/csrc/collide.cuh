@@ -1,0 +1,169 @@
+// KBC collision of one node (Sec. "Entropic multi-relaxation lattice Boltzmann
+// scheme", Eqs. (equilibrium), (kbcCollision), (entropyControl)), in two forms:
+//
+//  kbc_raw      - raw populations f_i, the plain method (used in FP64);
+//  kbc_shifted  - normalised deviations h_i = f_i / w_i - 1 (Assumption "Uniform
+//                 low Mach regime" (i): f = w (1 + eps g)), used for the FP32 and
+//                 FP16 storage with FP32 arithmetic.  Working on h removes the
+//                 cancellation of f - f^eq around f ~ w.
+//
+// The shear part Ds carries exactly the deviatoric raw second moments
+// D_ab = P_ab - delta_ab tr(P)/3 of f^neq (tensors N and Pi of Table
+// "frequencySummary"): Ds = D_aa / 2 on the faces +-e_a, s l P_ab / 4 on the
+// edge s e_a + l e_b, 0 at rest.  Dh = f^neq - Ds holds the remaining (T, Q, A)
+// moments.  gamma = 2/omega - (2 - 2/omega) <Ds|Dh>/<Dh|Dh> with
+// <X|Y> = sum X_i Y_i / f^eq_i; gamma = 2 (BGK) where <Dh|Dh> vanishes.
+#pragma once
+#include "lattice.cuh"
+
+namespace mclbm {
+
+// Signed sum over the populations: sum_i s(i) v_i with s(i) a compile-time
+// sign in {-1, 0, 1}; the zero terms are dropped at compile time.
+#define MCLBM_SIGNED_ADD(acc, sgn, v) \
+    do {                              \
+        if ((sgn) > 0) acc += (v);    \
+        else if ((sgn) < 0) acc -= (v); \
+    } while (0)
+
+// Plain KBC on raw populations (in place).  Returns gamma.
+template <class T>
+__host__ __device__ __forceinline__ T kbc_raw(T (&f)[Q], T omega)
+{
+    T rho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        rho += f[i];
+        MCLBM_SIGNED_ADD(jx, cx(i), f[i]);
+        MCLBM_SIGNED_ADD(jy, cy(i), f[i]);
+        MCLBM_SIGNED_ADD(jz, cz(i), f[i]);
+    }
+    const T ux = jx / rho, uy = jy / rho, uz = jz / rho;
+    const T uu = ux * ux + uy * uy + uz * uz;
+    T feq[Q], fneq[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        T cu = 0;
+        MCLBM_SIGNED_ADD(cu, cx(i), ux);
+        MCLBM_SIGNED_ADD(cu, cy(i), uy);
+        MCLBM_SIGNED_ADD(cu, cz(i), uz);
+        feq[i] = rho * weight<T>(i) * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
+        fneq[i] = f[i] - feq[i];
+    }
+    // raw second moments of f^neq
+    T pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (cx(i) != 0) pxx += fneq[i];
+        if (cy(i) != 0) pyy += fneq[i];
+        if (cz(i) != 0) pzz += fneq[i];
+        MCLBM_SIGNED_ADD(pxy, cx(i) * cy(i), fneq[i]);
+        MCLBM_SIGNED_ADD(pxz, cx(i) * cz(i), fneq[i]);
+        MCLBM_SIGNED_ADD(pyz, cy(i) * cz(i), fneq[i]);
+    }
+    const T tr3 = (pxx + pyy + pzz) / T(3);
+    T ds[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int n2 = norm2(i);
+        if (n2 == 0) ds[i] = 0;
+        else if (n2 == 1) ds[i] = T(0.5) * ((cx(i) ? pxx : (cy(i) ? pyy : pzz)) - tr3);
+        else {
+            const T p = (cz(i) == 0) ? pxy : ((cy(i) == 0) ? pxz : pyz);
+            const int s = (cz(i) == 0) ? cx(i) * cy(i) : ((cy(i) == 0) ? cx(i) * cz(i) : cy(i) * cz(i));
+            ds[i] = s > 0 ? T(0.25) * p : -T(0.25) * p;
+        }
+    }
+    T sh = 0, hh = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const T dh = fneq[i] - ds[i];
+        sh += ds[i] * dh / feq[i];
+        hh += dh * dh / feq[i];
+    }
+    const T gamma = (hh == T(0)) ? T(2) : T(2) / omega - (T(2) - T(2) / omega) * sh / hh;
+    const T bo = T(0.5) * omega * gamma;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const T dh = fneq[i] - ds[i];
+        f[i] = f[i] - omega * ds[i] - bo * dh;
+    }
+    return gamma;
+}
+
+// Guard of <Dh|Dh> in the FP32 shifted form (values are f/w-normalised; below
+// this the higher-order non-equilibrium is at rounding level).
+constexpr float kHHGuard = 1e-30f;
+
+// KBC on normalised deviations h_i = f_i / w_i - 1 (in place), FP32.
+__device__ __forceinline__ float kbc_shifted(float (&h)[Q], float omega)
+{
+    constexpr float w0 = 1.0f / 3.0f, w1 = 1.0f / 18.0f, w2 = 1.0f / 36.0f;
+    // density deviation and momentum: sum w h, sum w c h
+    float s0 = h[0], s1 = 0.f, s2 = 0.f;
+#pragma unroll
+    for (int i = 1; i < 7; ++i) s1 += h[i];
+#pragma unroll
+    for (int i = 7; i < Q; ++i) s2 += h[i];
+    const float drho = w0 * s0 + w1 * s1 + w2 * s2;
+    const float rho = 1.0f + drho;
+    const float jx = w1 * (h[1] - h[2]) + w2 * ((h[7] - h[8]) + (h[9] - h[10]) + (h[11] - h[12]) + (h[13] - h[14]));
+    const float jy = w1 * (h[3] - h[4]) + w2 * ((h[7] - h[8]) - (h[9] - h[10]) + (h[15] - h[16]) + (h[17] - h[18]));
+    const float jz = w1 * (h[5] - h[6]) + w2 * ((h[11] - h[12]) - (h[13] - h[14]) + (h[15] - h[16]) - (h[17] - h[18]));
+    const float rinv = __frcp_rn(rho);
+    const float ux = jx * rinv, uy = jy * rinv, uz = jz * rinv;
+    const float uu = ux * ux + uy * uy + uz * uz;
+    float heq[Q], n[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        float cu = 0.f;
+        MCLBM_SIGNED_ADD(cu, cx(i), ux);
+        MCLBM_SIGNED_ADD(cu, cy(i), uy);
+        MCLBM_SIGNED_ADD(cu, cz(i), uz);
+        heq[i] = drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
+        n[i] = h[i] - heq[i];
+    }
+    // second moments of f^neq / (normalised): P_ab = sum w c_a c_b n
+    const float ex = n[7] + n[8] + n[9] + n[10];   // xy edges
+    const float exz = n[11] + n[12] + n[13] + n[14];  // xz edges
+    const float eyz = n[15] + n[16] + n[17] + n[18];  // yz edges
+    const float pxx = w1 * (n[1] + n[2]) + w2 * (ex + exz);
+    const float pyy = w1 * (n[3] + n[4]) + w2 * (ex + eyz);
+    const float pzz = w1 * (n[5] + n[6]) + w2 * (exz + eyz);
+    const float pxy = w2 * ((n[7] + n[8]) - (n[9] + n[10]));
+    const float pxz = w2 * ((n[11] + n[12]) - (n[13] + n[14]));
+    const float pyz = w2 * ((n[15] + n[16]) - (n[17] + n[18]));
+    const float tr3 = (pxx + pyy + pzz) * (1.0f / 3.0f);
+    // shear part normalised by w: faces D_aa/2 / (1/18) = 9 D_aa, edges s l P_ab/4 / (1/36) = 9 s l P_ab
+    float s[Q];
+    s[0] = 0.f;
+    s[1] = s[2] = 9.0f * (pxx - tr3);
+    s[3] = s[4] = 9.0f * (pyy - tr3);
+    s[5] = s[6] = 9.0f * (pzz - tr3);
+    s[7] = s[8] = 9.0f * pxy;
+    s[9] = s[10] = -9.0f * pxy;
+    s[11] = s[12] = 9.0f * pxz;
+    s[13] = s[14] = -9.0f * pxz;
+    s[15] = s[16] = 9.0f * pyz;
+    s[17] = s[18] = -9.0f * pyz;
+    // <Ds|Dh> and <Dh|Dh> with 1/f^eq = 1/(w (1 + heq)): sum w s k / (1 + heq)
+    float sh = 0.f, hh = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float k = n[i] - s[i];
+        const float wr = weight<float>(i) * __frcp_rn(1.0f + heq[i]);
+        sh += wr * s[i] * k;
+        hh += wr * k * k;
+    }
+    const float two_over = 2.0f / omega;
+    const float gamma = (hh <= kHHGuard) ? 2.0f : two_over - (2.0f - two_over) * __fdiv_rn(sh, hh);
+    const float bo = 0.5f * omega * gamma;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const float k = n[i] - s[i];
+        h[i] = h[i] - omega * s[i] - bo * k;
+    }
+    return gamma;
+}
+
+}  // namespace mclbm

@@ -1,0 +1,84 @@
+// Library-internal declarations shared by the translation units of libmclbm.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mclbm.h"
+
+namespace mclbm {
+
+// Sub-allocation of the caller's work buffer (byte offsets, 256-aligned).
+struct WorkLayout {
+    size_t params;    // [M][24] double
+    size_t partial;   // reduction partials, kPartialBytes
+    size_t flag;      // int status words (16 ints)
+    size_t field;     // velocity field of one sample [3][n] double
+    size_t cplx;      // complex FFT buffer [n] double2
+    size_t real;      // power spectrum / autocorrelation [n] double
+    size_t twiddle;   // [N/2] double2
+    size_t bins;      // shell sums [2][N/2+1] double x M
+    size_t total;
+};
+
+constexpr size_t kPartialBytes = size_t(8) << 20;  // 8 MiB of reduction partials
+constexpr int kMaxW1Samples = 2048;                 // per ensemble in the W1 kernels
+
+}  // namespace mclbm
+
+struct mclbm_ctx {
+    mclbm_config cfg;
+    mclbm_units units;
+    int N, logN, M;
+    int64_t n;
+    void* pop;
+    size_t pop_bytes;
+    char* work;
+    size_t work_bytes;
+    mclbm::WorkLayout wl;
+    cudaStream_t stream;
+    int device;
+    int cur;         // pull: lattice (0/1) holding the current state
+    int64_t steps;   // steps since the last initialisation
+    std::vector<double> params;  // host copy [M][24]
+    size_t elem_bytes;
+    bool twiddles_ready;  // FFT twiddle table computed in the work buffer
+};
+
+namespace mclbm {
+
+// error reporting (thread-local message)
+int set_error(int code, const std::string& msg);
+int cuda_check(cudaError_t e, const char* what);
+#define MCLBM_CUDA(call)                                           \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return ::mclbm::cuda_check(e_, #call); \
+    } while (0)
+
+WorkLayout work_layout(int N, int M);
+
+// pointers of the population lattices
+void* lattice_ptr(const mclbm_ctx* c, int which);
+
+// kernels (launchers return cudaError_t of the launch)
+cudaError_t launch_init(const mclbm_ctx* c, const double* d_params);
+cudaError_t launch_step(mclbm_ctx* c);  // one step, flips state
+cudaError_t launch_get_populations(const mclbm_ctx* c, int sample, double* d_out);
+cudaError_t launch_set_populations(mclbm_ctx* c, int sample, const double* d_in);
+cudaError_t launch_moments(const mclbm_ctx* c, int sample, double* d_rho, double* d_u);
+cudaError_t launch_field(const mclbm_ctx* c, int sample, double* d_u);  // physical u [3][n]
+cudaError_t launch_energy(mclbm_ctx* c, bool with_enstrophy, double* h_E, double* h_Z);
+cudaError_t launch_mean_var(const mclbm_ctx* c, double* d_mean, double* d_var);
+cudaError_t launch_restrict(const mclbm_ctx* c, int Q, double* d_out);
+cudaError_t launch_check_finite(mclbm_ctx* c, int* h_bad);
+cudaError_t launch_spectral(mclbm_ctx* c, double* h_E, double* h_S2);
+cudaError_t launch_sf_axes(mclbm_ctx* c, int pmax, double* h_S);
+cudaError_t launch_w1(const double* d_a, int MA, const double* d_b, int MB, int G, char* work, size_t work_bytes,
+                      cudaStream_t s, double* h_W, double* h_per_point);
+size_t w1_work_bytes(int MA, int MB, int G);
+
+}  // namespace mclbm

@@ -1,0 +1,256 @@
+// Spectral statistics: FP64 3-D FFT, shell energy spectrum and the trace
+// second-order structure function of Algorithm "SF_spectral".
+//
+// FFT: complex-to-complex, radix-2, N a power of two.  A 3-D transform is three
+// passes of batched 1-D transforms, one per axis.  Each block stages a tile of
+// T lines in shared memory (T consecutive x for the y and z passes, so every
+// global access is a coalesced run of T complex values), applies the
+// bit-reversal permutation on load and log2 N butterfly stages in place, and
+// writes the tile back.  Twiddles exp(-2 pi i k / N) come from a table made
+// once per context.
+//
+// Shell sums: one block per shell kappa (or lag radius r) enumerates its integer
+// points {k in K_N : round(|k|) = kappa}, K_N = {-N/2+1..N/2}^3, with an exact
+// integer test 4|k|^2 in [(2 kappa - 1)^2, (2 kappa + 1)^2), each thread over a
+// fixed subset of (k_z, k_y) rows, then a fixed reduction tree: deterministic.
+#include "internal.h"
+#include "storage.cuh"
+
+namespace mclbm {
+
+cudaError_t launch_field(const mclbm_ctx* c, int sample, double* d_u);
+
+namespace {
+
+constexpr int kFftThreads = 256;
+
+__device__ __forceinline__ unsigned bitrev(unsigned v, int bits) { return __brev(v) >> (32 - bits); }
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Batched 1-D FFT of length N along one axis; `stride` is the element distance
+// along the line (1, N or N^2).  Block b handles T lines.
+__global__ void __launch_bounds__(kFftThreads) k_fft_pass(double2* __restrict__ data, const double2* __restrict__ tw,
+                                                          int N, int logN, int T, int64_t stride, int inverse)
+{
+    extern __shared__ double2 buf[];  // [T][N]
+    const int64_t n = (int64_t)N * N * N;
+    (void)n;
+    // line t of this block starts at base(t)
+    const int lines_per_plane = N * N;  // lines of one axis
+    const int first = blockIdx.x * T;   // first line id
+    auto base_of = [&](int line) -> int64_t {
+        if (stride == 1) return (int64_t)line * N;        // line = z*N + y
+        const int a = line / N, b = line % N;             // b = x (fastest across the tile)
+        if (stride == N) return (int64_t)a * N * N + b;   // a = z: elements (z, j, x)
+        return (int64_t)a * N + b;                        // stride N^2: a = y: elements (j, y, x)
+    };
+    (void)lines_per_plane;
+    const int total = T * N;
+    if (stride == 1) {
+        for (int k = threadIdx.x; k < total; k += blockDim.x) {
+            const int t = k / N, j = k % N;
+            buf[t * N + bitrev(j, logN)] = data[base_of(first + t) + j];
+        }
+    } else {
+        for (int k = threadIdx.x; k < total; k += blockDim.x) {
+            const int t = k % T, j = k / T;
+            buf[t * N + bitrev(j, logN)] = data[base_of(first + t) + (int64_t)j * stride];
+        }
+    }
+    __syncthreads();
+    const int halfN = N >> 1;
+    for (int s = 0; s < logN; ++s) {
+        const int half = 1 << s;
+        const int twstep = halfN >> s;  // N / (2 half)
+        for (int b = threadIdx.x; b < T * halfN; b += blockDim.x) {
+            const int t = b / halfN, q = b % halfN;
+            const int pos = q & (half - 1);
+            const int i0 = ((q >> s) << (s + 1)) + pos;
+            const int i1 = i0 + half;
+            double2 w = tw[pos * twstep];
+            if (inverse) w.y = -w.y;
+            double2* L = buf + t * N;
+            const double2 u = L[i0];
+            const double2 v = cmul(L[i1], w);
+            L[i0] = make_double2(u.x + v.x, u.y + v.y);
+            L[i1] = make_double2(u.x - v.x, u.y - v.y);
+        }
+        __syncthreads();
+    }
+    if (stride == 1) {
+        for (int k = threadIdx.x; k < total; k += blockDim.x) {
+            const int t = k / N, j = k % N;
+            data[base_of(first + t) + j] = buf[t * N + j];
+        }
+    } else {
+        for (int k = threadIdx.x; k < total; k += blockDim.x) {
+            const int t = k % T, j = k / T;
+            data[base_of(first + t) + (int64_t)j * stride] = buf[t * N + j];
+        }
+    }
+}
+
+__global__ void k_twiddles(double2* tw, int N)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N / 2; k += gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(-2.0 * k / N, &s, &c);
+        tw[k] = make_double2(c, s);
+    }
+}
+
+__global__ void k_real_to_complex(const double* __restrict__ in, double2* __restrict__ out, int64_t n)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = make_double2(in[k], 0.0);
+}
+
+__global__ void k_accum_power(const double2* __restrict__ in, double* __restrict__ psi, int64_t n, int first)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = in[k];
+        const double p = v.x * v.x + v.y * v.y;
+        psi[k] = first ? p : psi[k] + p;
+    }
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;
+}
+
+// Shell sums.  mode 0 (spectrum): out[kappa] = 4 pi / |S| sum |k|^2 psi / 2 * scale.
+// mode 1 (structure function): out[r] = 1/|C| sum 2 (R_0 - R_h), R_h = re(cbuf[h]) * scale.
+__global__ void k_shells(const double* __restrict__ psi, const double2* __restrict__ cbuf, int N, int mode, double scale,
+                         double* __restrict__ out)
+{
+    __shared__ double sh[32];
+    const int kap = blockIdx.x;
+    const int64_t lo4 = kap == 0 ? 0 : (int64_t)(2 * kap - 1) * (2 * kap - 1);  // 4|k|^2 >= lo4
+    const int64_t hi4 = (int64_t)(2 * kap + 1) * (2 * kap + 1);                   // 4|k|^2 <  hi4
+    const int half = N / 2;
+    const double R0 = mode == 1 ? cbuf[0].x * scale : 0.0;
+    double acc = 0.0, cnt = 0.0;
+    for (int p = threadIdx.x; p < N * N; p += blockDim.x) {
+        const int iz = p / N, iy = p % N;
+        const int kz = iz > half ? iz - N : iz, ky = iy > half ? iy - N : iy;  // K_N: -N/2+1..N/2
+        const int64_t kzy = (int64_t)kz * kz + (int64_t)ky * ky;
+        if (4 * kzy >= hi4) continue;
+        // kx >= 0 with 4 (kzy + kx^2) in [lo4, hi4)
+        const double rem = (double)hi4 / 4.0 - (double)kzy;
+        int kmax = (int)sqrt(rem) + 1;
+        if (kmax > half) kmax = half;
+        for (int kx = 0; kx <= kmax; ++kx) {
+            const int64_t k4 = 4 * (kzy + (int64_t)kx * kx);
+            if (k4 < lo4 || k4 >= hi4) continue;
+            for (int sgn = 0; sgn < 2; ++sgn) {
+                int sx;
+                if (sgn == 0) sx = kx;
+                else {
+                    if (kx == 0 || kx == half) continue;  // -0 is +0; -N/2 is not in K_N
+                    sx = -kx;
+                }
+                const int ix = sx < 0 ? sx + N : sx;
+                const int64_t idx = ((int64_t)iz * N + iy) * N + ix;
+                if (mode == 0)
+                    acc += 0.5 * (double)(k4 / 4) * psi[idx];
+                else
+                    acc += 2.0 * (R0 - cbuf[idx].x * scale);
+                cnt += 1.0;
+            }
+        }
+    }
+    acc = block_sum(acc, sh);
+    cnt = block_sum(cnt, sh);
+    if (threadIdx.x == 0) {
+        if (mode == 0)
+            out[kap] = cnt > 0 ? 4.0 * 3.14159265358979323846 / cnt * acc * scale : 0.0;
+        else
+            out[kap] = cnt > 0 ? acc / cnt : 0.0;
+    }
+}
+
+int grid_for(int64_t total)
+{
+    int64_t b = (total + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)(b < 1 ? 1 : b);
+}
+
+int fft_tile(int N) { return N >= 8 ? 8 : N; }
+
+cudaError_t fft3d(const mclbm_ctx* c, double2* data, const double2* tw, int inverse)
+{
+    const int N = c->N, logN = c->logN, T = fft_tile(N);
+    const size_t smem = (size_t)T * N * sizeof(double2);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int blocks = N * N / T;
+    const int64_t strides[3] = {1, N, (int64_t)N * N};
+    for (int a = 0; a < 3; ++a) {
+        k_fft_pass<<<blocks, kFftThreads, smem, c->stream>>>(data, tw, N, logN, T, strides[a], inverse);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_twiddles(const mclbm_ctx* c)
+{
+    k_twiddles<<<grid_for(c->N / 2), 256, 0, c->stream>>>((double2*)(c->work + c->wl.twiddle), c->N);
+    return cudaGetLastError();
+}
+
+// Spectrum E [M][N/2+1] and/or S2 [M][N/2+1] (host, may be NULL).
+cudaError_t launch_spectral(mclbm_ctx* c, double* h_E, double* h_S2)
+{
+    const int64_t n = c->n;
+    const int nb = c->N / 2 + 1;
+    double* field = (double*)(c->work + c->wl.field);
+    double2* cb = (double2*)(c->work + c->wl.cplx);
+    double* psi = (double*)(c->work + c->wl.real);
+    const double2* tw = (const double2*)(c->work + c->wl.twiddle);
+    double* bins = (double*)(c->work + c->wl.bins);  // [2][M][nb]
+    const double N3 = (double)n;
+    cudaError_t e;
+    for (int m = 0; m < c->M; ++m) {
+        if ((e = launch_field(c, m, field)) != cudaSuccess) return e;
+        for (int a = 0; a < 3; ++a) {
+            k_real_to_complex<<<grid_for(n), 256, 0, c->stream>>>(field + a * n, cb, n);
+            if ((e = fft3d(c, cb, tw, 0)) != cudaSuccess) return e;
+            k_accum_power<<<grid_for(n), 256, 0, c->stream>>>(cb, psi, n, a == 0);
+        }
+        // Phi = |u~|^2 with u~ = F(u) / N^3, so Phi = psi / N^6
+        if (h_E) k_shells<<<nb, 256, 0, c->stream>>>(psi, nullptr, c->N, 0, 1.0 / (N3 * N3), bins + (int64_t)m * nb);
+        if (h_S2) {
+            // R = N^-3 F^-1(psi), F^-1 with the factor N^-3: R_h = re(sum_k psi_k e^{+2 pi i k.h/N}) / N^6
+            k_real_to_complex<<<grid_for(n), 256, 0, c->stream>>>(psi, cb, n);
+            if ((e = fft3d(c, cb, tw, 1)) != cudaSuccess) return e;
+            k_shells<<<nb, 256, 0, c->stream>>>(nullptr, cb, c->N, 1, 1.0 / (N3 * N3),
+                                                bins + (int64_t)(c->M + m) * nb);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (h_E && (e = cudaMemcpyAsync(h_E, bins, sizeof(double) * c->M * nb, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+        return e;
+    if (h_S2 && (e = cudaMemcpyAsync(h_S2, bins + (int64_t)c->M * nb, sizeof(double) * c->M * nb, cudaMemcpyDeviceToHost,
+                                     c->stream)) != cudaSuccess)
+        return e;
+    return cudaStreamSynchronize(c->stream);
+}
+
+}  // namespace mclbm

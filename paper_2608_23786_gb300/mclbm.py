@@ -1,0 +1,262 @@
+"""ctypes binding of libmclbm (the C ABI declared in include/mclbm.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  Functions keep the C names; a non-zero status raises MclbmError with
+the library's message.  Device buffers are raw device addresses (ints), e.g.
+``tensor.data_ptr()`` of a CUDA torch tensor.  There is no CPU fallback: if the
+library is missing this module raises on first use.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+MCLBM_OK = 0
+STATUS = {
+    -1: "INVALID_ARG", -2: "UNSTABLE_TAU", -3: "OOM", -4: "CUDA", -5: "NONFINITE", -6: "TIMEOUT", -7: "SHAPE", -8: "IO",
+}
+FP64, FP32, FP16 = 0, 1, 2
+PULL, AA = 0, 1
+Q = 19
+
+
+class MclbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mclbm error {code} ({STATUS.get(code, '?')}): {msg}")
+        self.code = code
+        self.status = STATUS.get(code, "?")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int32), ("M", ctypes.c_int32), ("precision", ctypes.c_int32), ("pattern", ctypes.c_int32),
+        ("nu", ctypes.c_double), ("Ma", ctypes.c_double), ("dt", ctypes.c_double), ("U_c", ctypes.c_double),
+        ("width", ctypes.c_double), ("seed", ctypes.c_uint64), ("init_density", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+class Units(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("dx", "U_lat", "dt", "nu_lat", "tau", "omega")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_c = ctypes
+_vp = _c.c_void_p
+_dp = _c.POINTER(_c.c_double)
+_i32p = _c.POINTER(_c.c_int32)
+_size_p = _c.POINTER(_c.c_size_t)
+_ctx_p = _c.c_void_p
+
+_SIGNATURES = {
+    "mclbm_version": (_c.c_char_p, []),
+    "mclbm_last_error": (_c.c_char_p, []),
+    "mclbm_lattice": (_c.c_int, [_i32p, _dp]),
+    "mclbm_compute_units": (_c.c_int, [_c.POINTER(Config), _c.POINTER(Units)]),
+    "mclbm_required_bytes": (_c.c_int, [_c.POINTER(Config), _size_p, _size_p]),
+    "mclbm_create": (_c.c_int, [_c.POINTER(Config), _vp, _c.c_size_t, _vp, _c.c_size_t, _vp, _c.POINTER(_ctx_p)]),
+    "mclbm_destroy": (None, [_ctx_p]),
+    "mclbm_get_units": (_c.c_int, [_ctx_p, _c.POINTER(Units)]),
+    "mclbm_init_ensemble": (_c.c_int, [_ctx_p, _dp]),
+    "mclbm_draw_params": (_c.c_int, [_c.c_uint64, _c.c_int32, _c.c_int32, _c.c_double, _dp]),
+    "mclbm_init_tgv": (_c.c_int, [_ctx_p]),
+    "mclbm_get_params": (_c.c_int, [_ctx_p, _dp]),
+    "mclbm_step": (_c.c_int, [_ctx_p, _c.c_int64]),
+    "mclbm_steps_taken": (_c.c_int64, [_ctx_p]),
+    "mclbm_get_populations": (_c.c_int, [_ctx_p, _c.c_int32, _vp]),
+    "mclbm_set_populations": (_c.c_int, [_ctx_p, _c.c_int32, _vp]),
+    "mclbm_moments": (_c.c_int, [_ctx_p, _c.c_int32, _vp, _vp]),
+    "mclbm_energy": (_c.c_int, [_ctx_p, _dp, _dp]),
+    "mclbm_mean_var": (_c.c_int, [_ctx_p, _vp, _vp]),
+    "mclbm_spectrum": (_c.c_int, [_ctx_p, _dp]),
+    "mclbm_sf_trace": (_c.c_int, [_ctx_p, _dp]),
+    "mclbm_sf_axes": (_c.c_int, [_ctx_p, _c.c_int32, _dp]),
+    "mclbm_restrict": (_c.c_int, [_ctx_p, _c.c_int32, _vp]),
+    "mclbm_w1_1pt": (_c.c_int, [_ctx_p, _ctx_p, _c.c_int32, _dp, _dp]),
+    "mclbm_w1_work_bytes": (_c.c_size_t, [_c.c_int32, _c.c_int32, _c.c_int32]),
+    "mclbm_w1_restricted": (_c.c_int, [_vp, _c.c_int32, _vp, _c.c_int32, _c.c_int32, _vp, _c.c_size_t, _vp, _dp, _dp]),
+    "mclbm_check_finite": (_c.c_int, [_ctx_p]),
+}
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=False):
+    """Load libmclbm.so from the package's _build directory (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError(
+                f"libmclbm.so not found at {path}; build it with paper_2608_23786_gb300.build.build() "
+                "(the CUDA library is required: there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def declared_symbols():
+    """Names the binding expects the library to export (one per C-ABI entry point)."""
+    return list(_SIGNATURES)
+
+
+def _check(code):
+    if code != MCLBM_OK:
+        raise MclbmError(code, load().mclbm_last_error().decode())
+    return code
+
+
+def _darr(a):
+    """ctypes double* of a C-contiguous float64 numpy array (or None)."""
+    if a is None:
+        return None
+    import numpy as np
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_dp)
+
+
+# ---- same-named wrappers ------------------------------------------------------
+
+def mclbm_version():
+    return load().mclbm_version().decode()
+
+
+def mclbm_last_error():
+    return load().mclbm_last_error().decode()
+
+
+def mclbm_lattice():
+    import numpy as np
+    c = np.zeros((Q, 3), dtype=np.int32)
+    w = np.zeros(Q)
+    _check(load().mclbm_lattice(c.ctypes.data_as(_i32p), _darr(w)))
+    return c, w
+
+
+def mclbm_compute_units(cfg):
+    u = Units()
+    _check(load().mclbm_compute_units(ctypes.byref(cfg), ctypes.byref(u)))
+    return u
+
+
+def mclbm_required_bytes(cfg):
+    pop = ctypes.c_size_t()
+    work = ctypes.c_size_t()
+    _check(load().mclbm_required_bytes(ctypes.byref(cfg), ctypes.byref(pop), ctypes.byref(work)))
+    return pop.value, work.value
+
+
+def mclbm_create(cfg, d_pop, pop_bytes, d_work, work_bytes, stream=0):
+    ctx = _ctx_p()
+    _check(load().mclbm_create(ctypes.byref(cfg), d_pop, pop_bytes, d_work, work_bytes, stream or None,
+                               ctypes.byref(ctx)))
+    return ctx
+
+
+def mclbm_destroy(ctx):
+    load().mclbm_destroy(ctx)
+
+
+def mclbm_get_units(ctx):
+    u = Units()
+    _check(load().mclbm_get_units(ctx, ctypes.byref(u)))
+    return u
+
+
+def mclbm_init_ensemble(ctx, params=None):
+    _check(load().mclbm_init_ensemble(ctx, _darr(params)))
+
+
+def mclbm_draw_params(seed, first_sample, M, width=0.025):
+    import numpy as np
+    out = np.zeros((M, 24))
+    _check(load().mclbm_draw_params(int(seed), int(first_sample), int(M), float(width), _darr(out)))
+    return out
+
+
+def mclbm_init_tgv(ctx):
+    _check(load().mclbm_init_tgv(ctx))
+
+
+def mclbm_get_params(ctx, out):
+    _check(load().mclbm_get_params(ctx, _darr(out)))
+    return out
+
+
+def mclbm_step(ctx, nsteps):
+    _check(load().mclbm_step(ctx, int(nsteps)))
+
+
+def mclbm_steps_taken(ctx):
+    return load().mclbm_steps_taken(ctx)
+
+
+def mclbm_get_populations(ctx, sample, d_out):
+    _check(load().mclbm_get_populations(ctx, int(sample), d_out))
+
+
+def mclbm_set_populations(ctx, sample, d_in):
+    _check(load().mclbm_set_populations(ctx, int(sample), d_in))
+
+
+def mclbm_moments(ctx, sample, d_rho, d_u):
+    _check(load().mclbm_moments(ctx, int(sample), d_rho, d_u))
+
+
+def mclbm_energy(ctx, E, Z=None):
+    _check(load().mclbm_energy(ctx, _darr(E), _darr(Z)))
+
+
+def mclbm_mean_var(ctx, d_mean, d_var):
+    _check(load().mclbm_mean_var(ctx, d_mean, d_var))
+
+
+def mclbm_spectrum(ctx, E):
+    _check(load().mclbm_spectrum(ctx, _darr(E)))
+
+
+def mclbm_sf_trace(ctx, S2):
+    _check(load().mclbm_sf_trace(ctx, _darr(S2)))
+
+
+def mclbm_sf_axes(ctx, pmax, S):
+    _check(load().mclbm_sf_axes(ctx, int(pmax), _darr(S)))
+
+
+def mclbm_restrict(ctx, Qd, d_out):
+    _check(load().mclbm_restrict(ctx, int(Qd), d_out))
+
+
+def mclbm_w1_1pt(ctxA, ctxB, Qd, per_point=None):
+    W = ctypes.c_double()
+    _check(load().mclbm_w1_1pt(ctxA, ctxB, int(Qd), ctypes.byref(W), _darr(per_point)))
+    return W.value
+
+
+def mclbm_w1_work_bytes(MA, MB, G):
+    return load().mclbm_w1_work_bytes(int(MA), int(MB), int(G))
+
+
+def mclbm_w1_restricted(d_a, MA, d_b, MB, G, d_work, work_bytes, stream=0, per_point=None):
+    W = ctypes.c_double()
+    _check(load().mclbm_w1_restricted(d_a, int(MA), d_b, int(MB), int(G), d_work, work_bytes, stream or None,
+                                      ctypes.byref(W), _darr(per_point)))
+    return W.value
+
+
+def mclbm_check_finite(ctx):
+    _check(load().mclbm_check_finite(ctx))

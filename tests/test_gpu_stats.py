@@ -1,0 +1,141 @@
+"""GPU parity of the ensemble reductions (FP64) against the NumPy oracle, through the
+C ABI: kinetic energy, enstrophy, mean/variance fields, shell spectrum, trace S2,
+axis S_p, restriction and the one-point W1."""
+import numpy as np
+import pytest
+
+import ensemble_inputs as gen
+import oracle
+from gpu_helpers import lib_populations
+from oracle import stats
+from paper_2608_23786_gb300 import Ensemble, mclbm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    mclbm.load(build_if_missing=True)
+
+
+def _pair(N=16, M=3, steps=30, precision="fp64", Re=300.0, Ma=0.1, seed=21, pattern="pull"):
+    """A GPU ensemble and the oracle velocity field computed from the GPU's own state (so the
+    statistics are compared on identical input)."""
+    ens = Ensemble(N, M, Re=Re, Ma=Ma, precision=precision, pattern=pattern, seed=seed).init().step(steps)
+    f = lib_populations(ens)
+    _, u = oracle.moments(f)
+    return ens, stats.to_physical(u, ens.units["U_lat"])
+
+
+def _rel(a, b):
+    return np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300))
+
+
+@pytest.mark.parametrize("steps", [0, 1, 30])
+def test_energy_enstrophy(steps):
+    ens, u = _pair(steps=steps, pattern="aa")
+    E, Z = ens.energy(enstrophy=True)
+    assert _rel(E, stats.kinetic_energy(u)) <= 1e-12
+    assert _rel(Z, stats.enstrophy(u)) <= 1e-11
+    # the fused population-side reduction agrees with the field route
+    assert _rel(ens.energy(), E) <= 1e-12
+
+
+def test_energy_fp32_storage_reduction_is_fp64():
+    """With FP32 storage the velocity comes from the stored FP32 deviations (FP32 arithmetic);
+    the squares and sums are FP64."""
+    ens, u = _pair(precision="fp32", M=4)
+    assert _rel(ens.energy(), stats.kinetic_energy(u)) <= 2e-6
+
+
+def test_initial_energy_closed_form_on_gpu():
+    """E_0 = U_c^2/8 + sum X^2 / 1024 per sample (equilibrium init, rho = 1)."""
+    X = gen.draw_params(8, 6)
+    ens = Ensemble(16, 6, Re=100.0, Ma=0.05, precision="fp64").init(X)
+    np.testing.assert_allclose(ens.energy(), 1 / 8 + (X**2).sum(1) / 1024, rtol=1e-12)
+
+
+def test_mean_var():
+    ens, u = _pair(M=5)
+    mean, var = ens.mean_var()
+    om, ov = stats.mean_var(u)
+    np.testing.assert_allclose(mean.cpu().numpy(), om, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(var.cpu().numpy(), ov, rtol=1e-9, atol=1e-18)
+
+
+def test_mean_var_needs_two_samples():
+    ens = Ensemble(8, 1, Re=100.0, Ma=0.1, precision="fp32").init()
+    with pytest.raises(mclbm.MclbmError) as e:
+        ens.mean_var()
+    assert e.value.status == "SHAPE"
+
+
+def _bins_close(got, ref, rel, floor):
+    """Relative agreement on bins holding at least `floor` of the total."""
+    tot = np.abs(ref).sum(axis=-1, keepdims=True)
+    mask = np.abs(ref) >= floor * tot
+    assert mask.any()
+    err = np.abs(got - ref)[mask] / np.abs(ref)[mask]
+    assert err.max() <= rel, err.max()
+    # bins below the floor still agree in absolute terms
+    assert np.max(np.abs(got - ref)) <= rel * tot.max()
+
+
+@pytest.mark.parametrize("N", [8, 16, 32])
+def test_spectrum(N):
+    ens, u = _pair(N=N, M=2)
+    _bins_close(ens.spectrum(), stats.energy_spectrum(u), 1e-10, 1e-12)
+
+
+def test_spectrum_tgv_closed_form():
+    """Deterministic TGV at t = 0: E(2) = 3 pi U^2 / 124 (U = U_c = 1), zero elsewhere."""
+    ens = Ensemble(16, 1, Re=100.0, Ma=0.05, precision="fp64").init_tgv()
+    E = ens.spectrum()[0]
+    assert abs(E[2] - 3 * np.pi / 124) <= 1e-12
+    assert np.all(np.abs(np.delete(E, 2)) <= 1e-14)
+
+
+@pytest.mark.parametrize("N", [8, 16, 32])
+def test_sf_trace(N):
+    ens, u = _pair(N=N, M=2)
+    _bins_close(ens.sf_trace(), stats.structure_function_trace(u), 1e-10, 1e-12)
+
+
+@pytest.mark.parametrize("N,pmax", [(8, 6), (16, 6), (32, 3)])
+def test_sf_axes(N, pmax):
+    ens, u = _pair(N=N, M=2)
+    got = ens.sf_axes(pmax)
+    ref = stats.structure_function_axes(u, pmax)
+    assert _rel(got, ref) <= 1e-10
+
+
+def test_restrict():
+    ens, u = _pair(N=16, M=3)
+    np.testing.assert_allclose(ens.restrict(8).cpu().numpy(), stats.restrict(u, 8), rtol=1e-13, atol=1e-16)
+
+
+@pytest.mark.parametrize("MA,MB", [(4, 4), (3, 7)])
+def test_w1_between_levels(MA, MB):
+    """W_{1,1} between a 16^3 and a 32^3 ensemble (different N and M)."""
+    A, ua = _pair(N=16, M=MA, seed=3)
+    B, ub = _pair(N=32, M=MB, seed=4, Re=600.0, Ma=0.05)
+    W, pp = A.w1(B, per_point=True)
+    Wo, Do = stats.w1_one_point(stats.restrict(ua), stats.restrict(ub), per_point=True)
+    assert abs(W - Wo) <= 1e-12 * Wo
+    np.testing.assert_allclose(pp, Do, rtol=1e-12, atol=1e-18)
+
+
+def test_w1_restricted_equal_sizes_and_shift():
+    """Raw entry point on device arrays: shifting every value by c gives W = 3 c (three
+    components, each shifted by c)."""
+    import torch
+    M, G = 33, 512
+    a = torch.as_tensor(gen.normal(60, (M, G, 3)), device="cuda")
+    b = a + 0.125
+    work = torch.empty(mclbm.mclbm_w1_work_bytes(M, M, G), dtype=torch.uint8, device="cuda")
+    W = mclbm.mclbm_w1_restricted(a.data_ptr(), M, b.data_ptr(), M, G, work.data_ptr(), work.numel())
+    assert abs(W - 3 * 0.125) <= 1e-14
+    c = torch.as_tensor(gen.normal(61, (M, G, 3)), device="cuda")
+    W2 = mclbm.mclbm_w1_restricted(a.data_ptr(), M, c.data_ptr(), M, G, work.data_ptr(), work.numel())
+    ref = stats.w1_one_point(a.cpu().numpy(), c.cpu().numpy())
+    assert abs(W2 - ref) <= 1e-13 * ref
