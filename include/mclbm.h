@@ -215,6 +215,41 @@ MCLBM_API size_t mclbm_w1_work_bytes(int32_t MA, int32_t MB, int32_t G);
 MCLBM_API int mclbm_w1_restricted(const double* d_a, int32_t MA, const double* d_b, int32_t MB, int32_t G, void* d_work,
                         size_t work_bytes, void* cuda_stream, double* W, double* per_point);
 
+/* ---- launch shape and autotuning ------------------------------------------
+ * The stepper kernel updates `vec` consecutive nodes along x per thread (vec-wide
+ * loads and stores, warp shuffles for the x-shifts) in blocks of `block` threads on a
+ * persistent grid.  Supported: vec in {1, 2} (FP64), {1, 2, 4} (FP32), {2, 4, 8}
+ * (FP16), dividing N; block in {128, 256}.  Results do not depend on the shape. */
+MCLBM_API int mclbm_set_launch(mclbm_ctx* ctx, int32_t vec, int32_t block);
+MCLBM_API int mclbm_get_launch(const mclbm_ctx* ctx, int32_t* vec, int32_t* block);
+
+/* Time every supported shape on this context for trial_steps steps each (CUDA events
+ * on the context's stream), keep the fastest, and restore the initial state by
+ * re-running the initialisation from the stored parameters.  Must directly follow
+ * mclbm_init_ensemble / mclbm_init_tgv (INVALID_ARG otherwise).  Outputs may be NULL;
+ * best_ms is the time per step.  Synchronises. */
+MCLBM_API int mclbm_autotune(mclbm_ctx* ctx, int32_t trial_steps, int32_t* vec, int32_t* block, double* best_ms);
+
+/* ---- batched levels of the viscosity sequence --------------------------------
+ * Levels (contexts sharing device, stream, precision and pattern) advanced
+ * together under diffusive scaling (Remark "Diffusive scaling": dt ~ dx^2): level l
+ * takes substeps[l] steps per macro step; every substeps[l] divides the largest, S.
+ * Sub-step s of a macro step advances each level with s % (S / substeps[l]) == 0, all
+ * in one persistent launch.  With graphs enabled (default when the stream is not the
+ * legacy default stream) one period of the schedule is captured into a CUDA graph
+ * on first use and replayed.  The batch borrows the contexts; destroy it first. */
+typedef struct mclbm_batch mclbm_batch;
+MCLBM_API int mclbm_batch_create(mclbm_ctx* const* levels, int32_t nlev, const int32_t* substeps, mclbm_batch** out);
+MCLBM_API void mclbm_batch_destroy(mclbm_batch* b);
+MCLBM_API int mclbm_batch_set_graph(mclbm_batch* b, int32_t enable);
+MCLBM_API int mclbm_batch_set_launch(mclbm_batch* b, int32_t vec, int32_t block);
+/* Enqueue macro_steps macro steps.  Enqueued only. */
+MCLBM_API int mclbm_batch_step(mclbm_batch* b, int64_t macro_steps);
+MCLBM_API int64_t mclbm_batch_macro_steps(const mclbm_batch* b);
+/* Autotune the batch's launch shape (one macro step per trial, trials trials per
+ * shape), then re-initialise every level.  Must directly follow initialisation. */
+MCLBM_API int mclbm_batch_autotune(mclbm_batch* b, int32_t trials, int32_t* vec, int32_t* block, double* best_ms);
+
 /* Scan every stored population for NaN/Inf.  Returns MCLBM_OK or
  * MCLBM_ERR_NONFINITE.  Synchronises. */
 MCLBM_API int mclbm_check_finite(mclbm_ctx* ctx);

@@ -107,6 +107,13 @@ int validate(const mclbm_config* cfg, mclbm_units* u)
 
 }  // namespace
 
+LaunchConfig default_launch(int precision)
+{
+    if (precision == MCLBM_FP64) return LaunchConfig{1, 256};
+    if (precision == MCLBM_FP32) return LaunchConfig{2, 256};
+    return LaunchConfig{4, 256};
+}
+
 int set_error(int code, const std::string& msg)
 {
     g_last_error = msg;
@@ -137,6 +144,7 @@ WorkLayout work_layout(int N, int M)
     const size_t sfb = sf_axes_partial_bytes(N);
     wl.real = take(n * sizeof(double) > sfb ? n * sizeof(double) : sfb);
     wl.twiddle = take((size_t)(N / 2) * 2 * sizeof(double));
+    wl.trig = take((size_t)N * 4 * sizeof(double));
     size_t per = 2 * (size_t)(N / 2 + 1);
     if ((size_t)7 * (N / 2) > per) per = (size_t)7 * (N / 2);
     wl.bins = take((size_t)M * per * sizeof(double) + 2 * (size_t)M * sizeof(double));
@@ -240,6 +248,10 @@ int mclbm_create(const mclbm_config* cfg, void* d_pop, size_t pop_bytes, void* d
     c->params.assign((size_t)cfg->M * 24, 0.0);
     c->elem_bytes = elem_bytes_of(cfg->precision);
     c->twiddles_ready = false;
+    c->launch = default_launch(cfg->precision);
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    c->num_sms = sms;
     *out = c;
     return MCLBM_OK;
 }
@@ -302,10 +314,7 @@ int mclbm_get_params(const mclbm_ctx* ctx, double* params)
 int mclbm_step(mclbm_ctx* ctx, int64_t nsteps)
 {
     if (!ctx || nsteps < 0) return set_error(MCLBM_ERR_INVALID_ARG, "bad ctx or nsteps < 0");
-    for (int64_t s = 0; s < nsteps; ++s) {
-        MCLBM_CUDA(launch_step(ctx));
-        ctx->steps += 1;
-    }
+    for (int64_t s = 0; s < nsteps; ++s) MCLBM_CUDA(launch_step(ctx));
     return MCLBM_OK;
 }
 
@@ -435,3 +444,7 @@ int mclbm_check_finite(mclbm_ctx* ctx)
 }
 
 }  // extern "C"
+
+namespace mclbm {
+int reinit_ctx(mclbm_ctx* c) { return do_init(c); }
+}  // namespace mclbm

@@ -1,0 +1,349 @@
+// Batched multi-level stepping, CUDA-graph capture of the schedule, and the
+// autotuner of the stepper's launch shape.
+//
+// A batch holds the levels of a viscosity sequence (each an ensemble context).
+// Under diffusive scaling (dt ~ dx^2, Remark "Diffusive scaling"), halving dx with
+// the Mach number halved quarters dt, so level l takes substeps[l] lattice steps per
+// macro step (e.g. 1, 4, 16).  Sub-step s of a macro step advances every level with
+// s % (S / substeps[l]) == 0 (S = max substeps), all of them in one persistent launch
+// of the stepper kernel.  The S launches of a macro step (two macro steps when some
+// level takes an odd number of steps, so that every level's lattice parity returns
+// to its start) are captured once into a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+struct mclbm_batch {
+    std::vector<mclbm_ctx*> lev;
+    std::vector<int> sub;
+    int S;
+    int period;  // macro steps per captured graph
+    cudaStream_t stream;
+    mclbm::LaunchConfig launch;
+    bool use_graph;
+    bool warmed;
+    std::map<std::vector<int64_t>, cudaGraphExec_t> graphs;
+    int64_t macro_steps;
+};
+
+namespace mclbm {
+int reinit_ctx(mclbm_ctx* c);  // api.cu: re-run the initialisation from the stored parameters
+}
+
+using namespace mclbm;
+
+namespace {
+
+std::vector<int64_t> signature(const mclbm_batch* b)
+{
+    std::vector<int64_t> s;
+    for (auto* c : b->lev) {
+        s.push_back(c->cur);
+        s.push_back(c->steps & 1);
+    }
+    return s;
+}
+
+void clear_graphs(mclbm_batch* b)
+{
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+}
+
+cudaError_t macro_direct(mclbm_batch* b, const LaunchConfig& cfg)
+{
+    std::vector<mclbm_ctx*> part;
+    for (int s = 0; s < b->S; ++s) {
+        part.clear();
+        for (size_t l = 0; l < b->lev.size(); ++l)
+            if (s % (b->S / b->sub[l]) == 0) part.push_back(b->lev[l]);
+        if (part.empty()) continue;
+        cudaError_t e = launch_levels(part.data(), (int)part.size(), cfg, b->stream, nullptr);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+struct Saved {
+    std::vector<int> cur;
+    std::vector<int64_t> steps;
+};
+Saved save(const mclbm_batch* b)
+{
+    Saved s;
+    for (auto* c : b->lev) {
+        s.cur.push_back(c->cur);
+        s.steps.push_back(c->steps);
+    }
+    return s;
+}
+void restore(mclbm_batch* b, const Saved& s)
+{
+    for (size_t l = 0; l < b->lev.size(); ++l) {
+        b->lev[l]->cur = s.cur[l];
+        b->lev[l]->steps = s.steps[l];
+    }
+}
+
+int capture(mclbm_batch* b, cudaGraphExec_t* out)
+{
+    const Saved before = save(b);
+    MCLBM_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int p = 0; p < b->period && e == cudaSuccess; ++p) e = macro_direct(b, b->launch);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+    restore(b, before);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_check(e, "kernel launch during graph capture");
+    }
+    if (e2 != cudaSuccess) return cuda_check(e2, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_check(e, "cudaGraphInstantiate");
+    *out = exec;
+    return MCLBM_OK;
+}
+
+template <class F>
+int time_ms(cudaStream_t s, F&& body, double* ms)
+{
+    cudaEvent_t a, z;
+    MCLBM_CUDA(cudaEventCreate(&a));
+    MCLBM_CUDA(cudaEventCreate(&z));
+    MCLBM_CUDA(cudaEventRecord(a, s));
+    cudaError_t e = body();
+    cudaError_t e1 = cudaEventRecord(z, s);
+    cudaError_t e2 = cudaEventSynchronize(z);
+    float t = 0;
+    cudaEventElapsedTime(&t, a, z);
+    cudaEventDestroy(a);
+    cudaEventDestroy(z);
+    if (e != cudaSuccess) return cuda_check(e, "autotune trial");
+    if (e1 != cudaSuccess) return cuda_check(e1, "cudaEventRecord");
+    if (e2 != cudaSuccess) return cuda_check(e2, "cudaEventSynchronize");
+    *ms = t;
+    return MCLBM_OK;
+}
+
+std::vector<LaunchConfig> candidates(int precision, int N)
+{
+    std::vector<LaunchConfig> v;
+    const int* vecs;
+    int nv;
+    if (precision == MCLBM_FP64) {
+        vecs = kVecF64;
+        nv = sizeof(kVecF64) / sizeof(int);
+    } else if (precision == MCLBM_FP32) {
+        vecs = kVecF32;
+        nv = sizeof(kVecF32) / sizeof(int);
+    } else {
+        vecs = kVecF16;
+        nv = sizeof(kVecF16) / sizeof(int);
+    }
+    for (int i = 0; i < nv; ++i)
+        for (int blk : kBlocks)
+            if (N % vecs[i] == 0) v.push_back(LaunchConfig{vecs[i], blk});
+    return v;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mclbm_set_launch(mclbm_ctx* ctx, int32_t vec, int32_t block)
+{
+    if (!ctx) return set_error(MCLBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (!vec_supported(ctx->cfg.precision, vec) || (block != 128 && block != 256) || ctx->N % vec)
+        return set_error(MCLBM_ERR_INVALID_ARG, "unsupported launch shape (vec " + std::to_string(vec) + ", block " +
+                                                    std::to_string(block) + ")");
+    ctx->launch = LaunchConfig{vec, block};
+    return MCLBM_OK;
+}
+
+int mclbm_get_launch(const mclbm_ctx* ctx, int32_t* vec, int32_t* block)
+{
+    if (!ctx) return set_error(MCLBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (vec) *vec = ctx->launch.vec;
+    if (block) *block = ctx->launch.block;
+    return MCLBM_OK;
+}
+
+int mclbm_autotune(mclbm_ctx* ctx, int32_t trial_steps, int32_t* vec, int32_t* block, double* best_ms)
+{
+    if (!ctx || trial_steps < 1) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    if (ctx->steps != 0) return set_error(MCLBM_ERR_INVALID_ARG, "autotune must directly follow an initialisation");
+    double best = 1e300;
+    LaunchConfig bestc = ctx->launch;
+    for (const LaunchConfig& c : candidates(ctx->cfg.precision, ctx->N)) {
+        MCLBM_CUDA(launch_step_with(ctx, c));  // warm-up (first use also sizes the grid)
+        double ms = 0;
+        int st = time_ms(
+            ctx->stream,
+            [&]() {
+                for (int s = 0; s < trial_steps; ++s) {
+                    cudaError_t e = launch_step_with(ctx, c);
+                    if (e != cudaSuccess) return e;
+                }
+                return cudaSuccess;
+            },
+            &ms);
+        if (st != MCLBM_OK) return st;
+        if (ms < best) {
+            best = ms;
+            bestc = c;
+        }
+    }
+    ctx->launch = bestc;
+    int st = reinit_ctx(ctx);
+    if (st != MCLBM_OK) return st;
+    if (vec) *vec = bestc.vec;
+    if (block) *block = bestc.block;
+    if (best_ms) *best_ms = best / trial_steps;
+    return MCLBM_OK;
+}
+
+int mclbm_batch_create(mclbm_ctx* const* levels, int32_t nlev, const int32_t* substeps, mclbm_batch** out)
+{
+    if (!levels || !substeps || !out || nlev < 1 || nlev > kMaxLevels)
+        return set_error(MCLBM_ERR_INVALID_ARG, "need 1.." + std::to_string(kMaxLevels) + " levels");
+    *out = nullptr;
+    int S = 1;
+    for (int l = 0; l < nlev; ++l) {
+        if (!levels[l] || substeps[l] < 1 || substeps[l] > 4096) return set_error(MCLBM_ERR_INVALID_ARG, "bad level");
+        if (substeps[l] > S) S = substeps[l];
+        if (levels[l]->cfg.precision != levels[0]->cfg.precision || levels[l]->cfg.pattern != levels[0]->cfg.pattern)
+            return set_error(MCLBM_ERR_INVALID_ARG, "levels of a batch share precision and streaming pattern");
+        if (levels[l]->stream != levels[0]->stream || levels[l]->device != levels[0]->device)
+            return set_error(MCLBM_ERR_INVALID_ARG, "levels of a batch share device and stream");
+        for (int k = 0; k < l; ++k)
+            if (levels[k] == levels[l]) return set_error(MCLBM_ERR_INVALID_ARG, "a level appears twice");
+    }
+    int odd = 0;
+    for (int l = 0; l < nlev; ++l) {
+        if (S % substeps[l]) return set_error(MCLBM_ERR_INVALID_ARG, "every substeps[l] must divide the largest");
+        odd |= substeps[l] & 1;
+    }
+    mclbm_batch* b = new mclbm_batch();
+    b->lev.assign(levels, levels + nlev);
+    b->sub.assign(substeps, substeps + nlev);
+    b->S = S;
+    b->period = odd ? 2 : 1;
+    b->stream = levels[0]->stream;
+    b->launch = levels[0]->launch;
+    b->use_graph = b->stream != nullptr;
+    b->warmed = false;
+    b->macro_steps = 0;
+    *out = b;
+    return MCLBM_OK;
+}
+
+void mclbm_batch_destroy(mclbm_batch* b)
+{
+    if (!b) return;
+    clear_graphs(b);
+    delete b;
+}
+
+int mclbm_batch_set_graph(mclbm_batch* b, int32_t enable)
+{
+    if (!b) return set_error(MCLBM_ERR_INVALID_ARG, "batch is NULL");
+    if (enable && b->stream == nullptr)
+        return set_error(MCLBM_ERR_INVALID_ARG, "graph capture needs a non-default stream");
+    b->use_graph = enable != 0;
+    return MCLBM_OK;
+}
+
+int mclbm_batch_set_launch(mclbm_batch* b, int32_t vec, int32_t block)
+{
+    if (!b) return set_error(MCLBM_ERR_INVALID_ARG, "batch is NULL");
+    for (auto* c : b->lev)
+        if (!vec_supported(c->cfg.precision, vec) || c->N % vec || (block != 128 && block != 256))
+            return set_error(MCLBM_ERR_INVALID_ARG, "unsupported launch shape");
+    b->launch = LaunchConfig{vec, block};
+    clear_graphs(b);
+    b->warmed = false;
+    return MCLBM_OK;
+}
+
+int mclbm_batch_step(mclbm_batch* b, int64_t macro_steps)
+{
+    if (!b || macro_steps < 0) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    while (macro_steps > 0) {
+        if (b->use_graph && b->warmed && macro_steps >= b->period) {
+            const auto sig = signature(b);
+            auto it = b->graphs.find(sig);
+            if (it == b->graphs.end()) {
+                cudaGraphExec_t g = nullptr;
+                int st = capture(b, &g);
+                if (st != MCLBM_OK) return st;
+                it = b->graphs.emplace(sig, g).first;
+            }
+            MCLBM_CUDA(cudaGraphLaunch(it->second, b->stream));
+            for (size_t l = 0; l < b->lev.size(); ++l) b->lev[l]->steps += (int64_t)b->period * b->sub[l];
+            b->macro_steps += b->period;
+            macro_steps -= b->period;
+        } else {
+            MCLBM_CUDA(macro_direct(b, b->launch));
+            b->warmed = true;
+            b->macro_steps += 1;
+            macro_steps -= 1;
+        }
+    }
+    return MCLBM_OK;
+}
+
+int mclbm_batch_autotune(mclbm_batch* b, int32_t trials, int32_t* vec, int32_t* block, double* best_ms)
+{
+    if (!b || trials < 1) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    for (auto* c : b->lev)
+        if (c->steps != 0) return set_error(MCLBM_ERR_INVALID_ARG, "autotune must directly follow an initialisation");
+    int prec = b->lev[0]->cfg.precision, Nmin = 1 << 30;
+    for (auto* c : b->lev) Nmin = c->N < Nmin ? c->N : Nmin;
+    double best = 1e300;
+    LaunchConfig bestc = b->launch;
+    for (const LaunchConfig& c : candidates(prec, Nmin)) {
+        bool ok = true;
+        for (auto* l : b->lev) ok = ok && (l->N % c.vec == 0);
+        if (!ok) continue;
+        MCLBM_CUDA(macro_direct(b, c));
+        double ms = 0;
+        int st = time_ms(
+            b->stream,
+            [&]() {
+                for (int t = 0; t < trials; ++t) {
+                    cudaError_t e = macro_direct(b, c);
+                    if (e != cudaSuccess) return e;
+                }
+                return cudaSuccess;
+            },
+            &ms);
+        if (st != MCLBM_OK) return st;
+        if (ms < best) {
+            best = ms;
+            bestc = c;
+        }
+    }
+    b->launch = bestc;
+    clear_graphs(b);
+    b->warmed = false;
+    for (auto* c : b->lev) {
+        int st = reinit_ctx(c);
+        if (st != MCLBM_OK) return st;
+    }
+    b->macro_steps = 0;
+    if (vec) *vec = bestc.vec;
+    if (block) *block = bestc.block;
+    if (best_ms) *best_ms = best / trials;
+    return MCLBM_OK;
+}
+
+int64_t mclbm_batch_macro_steps(const mclbm_batch* b) { return b ? b->macro_steps : -1; }
+
+}  // extern "C"

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/mclbm.h"
+#include "launch.h"
 
 namespace mclbm {
 
@@ -20,6 +21,7 @@ struct WorkLayout {
     size_t cplx;      // complex FFT buffer [n] double2
     size_t real;      // power spectrum / autocorrelation [n] double
     size_t twiddle;   // [N/2] double2
+    size_t trig;      // [N][4] double: sin, cos of x_n and 2 x_n
     size_t bins;      // shell sums [2][N/2+1] double x M
     size_t total;
 };
@@ -46,6 +48,8 @@ struct mclbm_ctx {
     std::vector<double> params;  // host copy [M][24]
     size_t elem_bytes;
     bool twiddles_ready;  // FFT twiddle table computed in the work buffer
+    mclbm::LaunchConfig launch;  // stepper variant (autotuned or default)
+    int num_sms;
 };
 
 namespace mclbm {
@@ -66,7 +70,12 @@ void* lattice_ptr(const mclbm_ctx* c, int which);
 
 // kernels (launchers return cudaError_t of the launch)
 cudaError_t launch_init(const mclbm_ctx* c, const double* d_params);
-cudaError_t launch_step(mclbm_ctx* c);  // one step, flips state
+cudaError_t launch_step(mclbm_ctx* c);  // one step of one context; updates cur and steps
+cudaError_t launch_step_with(mclbm_ctx* c, const LaunchConfig& cfg);
+// one step of several levels in one launch; updates each level's cur and steps
+cudaError_t launch_levels(mclbm_ctx* const* levels, int nlev, const LaunchConfig& cfg, cudaStream_t s, int* occ);
+bool vec_supported(int precision, int vec);
+LaunchConfig default_launch(int precision);
 cudaError_t launch_get_populations(const mclbm_ctx* c, int sample, double* d_out);
 cudaError_t launch_set_populations(mclbm_ctx* c, int sample, const double* d_in);
 cudaError_t launch_moments(const mclbm_ctx* c, int sample, double* d_rho, double* d_u);

@@ -1,0 +1,39 @@
+// Launch configuration of the stepper kernel variants (chosen by the autotuner).
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+
+namespace mclbm {
+
+constexpr int kMaxLevels = 8;  // levels of one batched launch
+
+struct LaunchConfig {
+    int vec;    // nodes per thread along x
+    int block;  // threads per block (128 or 256)
+};
+
+// Variants compiled per element type (nodes per thread; VEC * sizeof(E) <= 16 bytes).
+constexpr int kVecF64[] = {1, 2};
+constexpr int kVecF32[] = {1, 2, 4};
+constexpr int kVecF16[] = {2, 4, 8};
+constexpr int kBlocks[] = {128, 256};
+
+template <class E>
+struct BatchArgs;
+
+// Launchers defined in stepper_<type>_<pattern>.cu.  grid_cap: SM count (the grid is
+// grid_cap times the variant's resident blocks per SM, or less for small batches).
+#define MCLBM_DECLARE_LAUNCH(T, E)                                                                              \
+    cudaError_t launch_batch_##T##_pull(const BatchArgs<E>& a, const LaunchConfig& c, int grid_cap, cudaStream_t s, \
+                                        int* occ);                                                               \
+    cudaError_t launch_batch_##T##_aa(const BatchArgs<E>& a, const LaunchConfig& c, int grid_cap, cudaStream_t s,   \
+                                      int* occ);
+MCLBM_DECLARE_LAUNCH(f64, double)
+MCLBM_DECLARE_LAUNCH(f32, float)
+MCLBM_DECLARE_LAUNCH(f16, __half)
+#undef MCLBM_DECLARE_LAUNCH
+
+}  // namespace mclbm

@@ -19,7 +19,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMaxP = 8;
-constexpr int kBlocks = 152 * 2;
+constexpr int kSfBlocks = 152 * 2;
 
 __global__ void __launch_bounds__(kThreads) k_sf_axes(const double* __restrict__ u, int N, int logN, int pmax,
                                                       double* __restrict__ partial)
@@ -109,7 +109,7 @@ size_t sf_axes_smem(int N)
     return a > b ? a : b;
 }
 
-size_t sf_axes_partial_bytes(int N) { return (size_t)kBlocks * (N / 2) * (kMaxP - 1) * sizeof(double); }
+size_t sf_axes_partial_bytes(int N) { return (size_t)kSfBlocks * (N / 2) * (kMaxP - 1) * sizeof(double); }
 
 cudaError_t launch_sf_axes(mclbm_ctx* c, int pmax, double* h_S)
 {
@@ -123,8 +123,8 @@ cudaError_t launch_sf_axes(mclbm_ctx* c, int pmax, double* h_S)
     const double scale = 1.0 / (3.0 * (double)c->n);
     for (int m = 0; m < c->M; ++m) {
         if ((e = launch_field(c, m, field)) != cudaSuccess) return e;
-        k_sf_axes<<<kBlocks, kThreads, smem, c->stream>>>(field, N, c->logN, pmax, partial);
-        k_sf_reduce<<<8, 256, 0, c->stream>>>(partial, kBlocks, halfN, pmax, scale,
+        k_sf_axes<<<kSfBlocks, kThreads, smem, c->stream>>>(field, N, c->logN, pmax, partial);
+        k_sf_reduce<<<8, 256, 0, c->stream>>>(partial, kSfBlocks, halfN, pmax, scale,
                                                out + (int64_t)m * (pmax - 1) * halfN);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

@@ -1,22 +1,11 @@
-// Ensemble initialisation and the fused stream + KBC collide kernels.
-//
-// One thread updates one lattice node of one sample per step.  The grid spans
-// every node of every sample of the ensemble (the sample index is the slowest
-// part of the linear node index), so a whole ensemble advances in one launch.
-//
-// Streaming (Eq. (lbIteration), f_i(x + c_i, t + 1) = f*_i(x, t)) is fused with
-// the collision in two patterns:
-//   pull: read f_i(x, t) = S_i(x - c_i) from lattice A, write f*_i(x, t) to
-//         slot i of node x in lattice B (A and B swap every step);
-//   AA:   one lattice, in place.  Even t: read slot i of x, write f*_i to slot
-//         opp(i) of x.  Odd t: read slot opp(i) of x - c_i, write f*_i to slot i
-//         of x + c_i.  Each node reads and writes the same 19 slots, so no two
-//         threads touch the same element within a step.
+// Ensemble initialisation, population gather/scatter, and the host side of the
+// batched stream + collide launch (the kernels live in stepper_impl.cuh and are
+// compiled per element type and pattern in stepper_<type>_<pattern>.cu).
 #include <cuda_fp16.h>
 
-#include "collide.cuh"
 #include "internal.h"
-#include "storage.cuh"
+#include "launch.h"
+#include "stepper_impl.cuh"
 
 namespace mclbm {
 
@@ -33,49 +22,51 @@ __device__ __forceinline__ void decode(const Geom& g, int64_t idx, int& m, int& 
     z = (int)(node >> (2 * g.logN));
 }
 
-template <class E>
-__device__ __forceinline__ void collide_node(typename Storage<E>::compute (&v)[Q], typename Storage<E>::compute omega)
+// Per-axis trigonometric tables of the initial condition: for n < N,
+// t[4n + 0..3] = sin(x_n), cos(x_n), sin(2 x_n), cos(2 x_n), x_n = 2 pi n / N.
+__global__ void k_trig_tables(double* t, int N)
 {
-    if constexpr (Storage<E>::shifted)
-        kbc_shifted(v, omega);
-    else
-        kbc_raw(v, omega);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+        double s, c, s2, c2;
+        sincospi(2.0 * k / N, &s, &c);
+        sincospi(4.0 * k / N, &s2, &c2);
+        t[4 * k + 0] = s;
+        t[4 * k + 1] = c;
+        t[4 * k + 2] = s2;
+        t[4 * k + 3] = c2;
+    }
 }
 
-// ---------------------------------------------------------------- init ----
-// u_0 = (U_lat / U_c) (u_det + s(X_m)) at node x_n = 2 pi n / N, f_0 = f^eq(rho_0, u_0),
+// u_0 = (U_lat / U_c)(u_det + s(X_m)) at node x_n = 2 pi n / N, f_0 = f^eq(rho_0, u_0):
 // Eqs. (tgv_init_velo), (alpha_perturbation), (initialRTGV), (initialPopulations).
+// u_0 and rho_0 in FP64; the equilibrium in the storage's arithmetic (FP64 for raw
+// storage, FP32 for the shifted deviations h = f^eq / w - 1).
 template <class E>
 __global__ void __launch_bounds__(kBlock) k_init(E* __restrict__ lat, Geom g, int64_t total, const double* __restrict__ X,
-                                                 double uc, double ulat, int density_mode, int pattern)
+                                                 const double* __restrict__ trig, double uc, double ulat, int density_mode,
+                                                 int pattern)
 {
+    using C = typename Storage<E>::compute;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         int m, x, y, z;
         decode(g, idx, m, x, y, z);
-        const double invN = 1.0 / g.N;
-        double sx, cxx, sy, cyy, sz, czz, s2x, c2x, s2y, c2y, s2z, c2z;
-        sincospi(2.0 * x * invN, &sx, &cxx);
-        sincospi(2.0 * y * invN, &sy, &cyy);
-        sincospi(2.0 * z * invN, &sz, &czz);
-        sincospi(4.0 * x * invN, &s2x, &c2x);
-        sincospi(4.0 * y * invN, &s2y, &c2y);
-        sincospi(4.0 * z * invN, &s2z, &c2z);
+        const double sx = trig[4 * x], cxx = trig[4 * x + 1], s2x = trig[4 * x + 2], c2x = trig[4 * x + 3];
+        const double sy = trig[4 * y], cyy = trig[4 * y + 1], s2y = trig[4 * y + 2], c2y = trig[4 * y + 3];
+        const double sz = trig[4 * z], czz = trig[4 * z + 1], s2z = trig[4 * z + 2], c2z = trig[4 * z + 3];
         double u[3] = {uc * sx * cyy * czz, -uc * cxx * sy * czz, 0.0};
-        if (X) {
-            const double* Xm = X + 24 * (int64_t)m;
-            const double ax[2] = {s2x, c2x}, ay[2] = {s2y, c2y}, az[2] = {s2z, c2z};
+        const double* Xm = X + 24 * (int64_t)m;
+        const double ax[2] = {s2x, c2x}, ay[2] = {s2y, c2y}, az[2] = {s2z, c2z};
 #pragma unroll
-            for (int al = 0; al < 3; ++al) {
-                double s = 0.0;
+        for (int al = 0; al < 3; ++al) {
+            double s = 0.0;
 #pragma unroll
-                for (int i = 0; i < 2; ++i)
+            for (int i = 0; i < 2; ++i)
 #pragma unroll
-                    for (int j = 0; j < 2; ++j)
+                for (int j = 0; j < 2; ++j)
 #pragma unroll
-                        for (int k = 0; k < 2; ++k) s += Xm[8 * al + 4 * i + 2 * j + k] * (ax[i] * ay[j] * az[k]);
-                u[al] += s * 0.125;
-            }
+                    for (int k = 0; k < 2; ++k) s += Xm[8 * al + 4 * i + 2 * j + k] * (ax[i] * ay[j] * az[k]);
+            u[al] += s * 0.125;
         }
         const double sc = ulat / uc;
         u[0] *= sc;
@@ -83,82 +74,32 @@ __global__ void __launch_bounds__(kBlock) k_init(E* __restrict__ lat, Geom g, in
         u[2] *= sc;
         double drho = 0.0;
         if (density_mode == 1) drho = 3.0 * (ulat * ulat / 16.0) * (c2x + c2y) * (c2z + 2.0);
-        const double rho = 1.0 + drho;
-        const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
         E* base = lat + (int64_t)m * Q * g.n;
+        if constexpr (Storage<E>::shifted) {
+            const C ux = (C)u[0], uy = (C)u[1], uz = (C)u[2], dr = (C)drho, rho = C(1) + dr;
+            const C uu = ux * ux + uy * uy + uz * uz;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const double cu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
-            const double heq = drho + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);  // f^eq / w - 1
-            E* p = base + pre_loc(g, pattern, 0, i, x, y, z);
-            if constexpr (Storage<E>::shifted) {
-                if constexpr (sizeof(E) == 4)
-                    *p = (float)heq;
-                else
-                    *p = __double2half(heq);
-            } else {
-                *p = rho * weight<double>(i) * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+            for (int i = 0; i < Q; ++i) {
+                C cu = 0;
+                MCLBM_SIGNED_ADD(cu, cx(i), ux);
+                MCLBM_SIGNED_ADD(cu, cy(i), uy);
+                MCLBM_SIGNED_ADD(cu, cz(i), uz);
+                const C heq = dr + rho * (C(3) * cu + C(4.5) * cu * cu - C(1.5) * uu);
+                base[pre_loc(g, pattern, 0, i, x, y, z)] = from_c<E>(heq);
+            }
+        } else {
+            const double rho = 1.0 + drho;
+            const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const double cu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
+                base[pre_loc(g, pattern, 0, i, x, y, z)] =
+                    rho * weight<double>(i) * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
             }
         }
     }
 }
 
-// ------------------------------------------------------ fused step: pull ----
-template <class E>
-__global__ void __launch_bounds__(kBlock) k_step_pull(const E* __restrict__ src, E* __restrict__ dst, Geom g,
-                                                      int64_t total, typename Storage<E>::compute omega)
-{
-    using C = typename Storage<E>::compute;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        int m, x, y, z;
-        decode(g, idx, m, x, y, z);
-        const int64_t base = (int64_t)m * Q * g.n;
-        C v[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i)
-            v[i] = Storage<E>::load(src + base + (int64_t)i * g.n +
-                                    g.node(g.wrap(x - cx(i)), g.wrap(y - cy(i)), g.wrap(z - cz(i))));
-        collide_node<E>(v, omega);
-        const int64_t node = g.node(x, y, z);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) Storage<E>::store(dst + base + (int64_t)i * g.n + node, v[i]);
-    }
-}
-
-// -------------------------------------------------------- fused step: AA ----
-template <class E, int Parity>
-__global__ void __launch_bounds__(kBlock) k_step_aa(E* lat, Geom g, int64_t total, typename Storage<E>::compute omega)
-{
-    using C = typename Storage<E>::compute;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        int m, x, y, z;
-        decode(g, idx, m, x, y, z);
-        E* base = lat + (int64_t)m * Q * g.n;
-        C v[Q];
-        if (Parity == 0) {
-            const int64_t node = g.node(x, y, z);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) v[i] = Storage<E>::load(base + (int64_t)i * g.n + node);
-            collide_node<E>(v, omega);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) Storage<E>::store(base + (int64_t)opp(i) * g.n + node, v[i]);
-        } else {
-#pragma unroll
-            for (int i = 0; i < Q; ++i)
-                v[i] = Storage<E>::load(base + (int64_t)opp(i) * g.n +
-                                        g.node(g.wrap(x - cx(i)), g.wrap(y - cy(i)), g.wrap(z - cz(i))));
-            collide_node<E>(v, omega);
-#pragma unroll
-            for (int i = 0; i < Q; ++i)
-                Storage<E>::store(base + (int64_t)i * g.n + g.node(g.wrap(x + cx(i)), g.wrap(y + cy(i)), g.wrap(z + cz(i))),
-                                  v[i]);
-        }
-    }
-}
-
-// ------------------------------------------------ population gather/scatter ----
 template <class E>
 __global__ void k_get_pops(const E* __restrict__ lat, Geom g, int pattern, int parity, int sample, double* __restrict__ out)
 {
@@ -190,41 +131,24 @@ int grid_for(int64_t total)
 }
 
 Geom geom_of(const mclbm_ctx* c) { return Geom{c->N, c->logN, c->n}; }
+int parity_of(const mclbm_ctx* c) { return c->cfg.pattern == MCLBM_AA ? (int)(c->steps & 1) : 0; }
 
 template <class E>
-cudaError_t init_t(const mclbm_ctx* c, const double* d_params)
+cudaError_t init_t(const mclbm_ctx* c, const double* d_params, double* d_trig)
 {
+    k_trig_tables<<<(c->N + 127) / 128, 128, 0, c->stream>>>(d_trig, c->N);
     const int64_t total = (int64_t)c->M * c->n;
-    k_init<E><<<grid_for(total), kBlock, 0, c->stream>>>((E*)lattice_ptr(c, c->cur), geom_of(c), total, d_params,
+    k_init<E><<<grid_for(total), kBlock, 0, c->stream>>>((E*)lattice_ptr(c, c->cur), geom_of(c), total, d_params, d_trig,
                                                          c->cfg.U_c, c->units.U_lat, c->cfg.init_density,
                                                          c->cfg.pattern);
     return cudaGetLastError();
 }
 
 template <class E>
-cudaError_t step_t(mclbm_ctx* c)
-{
-    using C = typename Storage<E>::compute;
-    const int64_t total = (int64_t)c->M * c->n;
-    const C omega = (C)c->units.omega;
-    if (c->cfg.pattern == MCLBM_PULL) {
-        k_step_pull<E><<<grid_for(total), kBlock, 0, c->stream>>>((const E*)lattice_ptr(c, c->cur),
-                                                                  (E*)lattice_ptr(c, 1 - c->cur), geom_of(c), total,
-                                                                  omega);
-        c->cur ^= 1;
-    } else if ((c->steps & 1) == 0) {
-        k_step_aa<E, 0><<<grid_for(total), kBlock, 0, c->stream>>>((E*)lattice_ptr(c, 0), geom_of(c), total, omega);
-    } else {
-        k_step_aa<E, 1><<<grid_for(total), kBlock, 0, c->stream>>>((E*)lattice_ptr(c, 0), geom_of(c), total, omega);
-    }
-    return cudaGetLastError();
-}
-
-template <class E>
 cudaError_t get_t(const mclbm_ctx* c, int sample, double* d_out)
 {
-    k_get_pops<E><<<grid_for(c->n), kBlock, 0, c->stream>>>((const E*)lattice_ptr(c, c->cur), geom_of(c),
-                                                            c->cfg.pattern, (int)(c->steps & 1), sample, d_out);
+    k_get_pops<E><<<grid_for(c->n), kBlock, 0, c->stream>>>((const E*)lattice_ptr(c, c->cur), geom_of(c), c->cfg.pattern,
+                                                            parity_of(c), sample, d_out);
     return cudaGetLastError();
 }
 
@@ -232,28 +156,106 @@ template <class E>
 cudaError_t set_t(mclbm_ctx* c, int sample, const double* d_in)
 {
     k_set_pops<E><<<grid_for(c->n), kBlock, 0, c->stream>>>((E*)lattice_ptr(c, c->cur), geom_of(c), c->cfg.pattern,
-                                                            (int)(c->steps & 1), sample, d_in);
+                                                            parity_of(c), sample, d_in);
     return cudaGetLastError();
+}
+
+template <class E>
+void fill_level(LevelArgs<E>& L, const mclbm_ctx* c)
+{
+    if (c->cfg.pattern == MCLBM_PULL) {
+        L.src = (const E*)lattice_ptr(c, c->cur);
+        L.dst = (E*)lattice_ptr(c, 1 - c->cur);
+    } else {
+        L.src = (const E*)lattice_ptr(c, 0);
+        L.dst = (E*)lattice_ptr(c, 0);
+    }
+    L.g = geom_of(c);
+    L.M = c->M;
+    L.parity = parity_of(c);
+    L.omega32 = (float)c->units.omega;
+    L.omega64 = c->units.omega;
+}
+
+template <class E>
+cudaError_t levels_t(mclbm_ctx* const* lv, int nlev, const LaunchConfig& cfg, int grid_cap, cudaStream_t s, int* occ)
+{
+    BatchArgs<E> a;
+    memset(&a, 0, sizeof(a));
+    a.nlev = nlev;
+    a.prefix[0] = 0;
+    for (int k = 0; k < nlev; ++k) {
+        fill_level<E>(a.lev[k], lv[k]);
+        a.prefix[k + 1] = a.prefix[k] + (int64_t)lv[k]->M * lv[k]->n / cfg.vec;
+    }
+    const bool pull = lv[0]->cfg.pattern == MCLBM_PULL;
+    if constexpr (std::is_same<E, double>::value)
+        return pull ? launch_batch_f64_pull(a, cfg, grid_cap, s, occ) : launch_batch_f64_aa(a, cfg, grid_cap, s, occ);
+    else if constexpr (std::is_same<E, float>::value)
+        return pull ? launch_batch_f32_pull(a, cfg, grid_cap, s, occ) : launch_batch_f32_aa(a, cfg, grid_cap, s, occ);
+    else
+        return pull ? launch_batch_f16_pull(a, cfg, grid_cap, s, occ) : launch_batch_f16_aa(a, cfg, grid_cap, s, occ);
 }
 
 }  // namespace
 
-#define MCLBM_DISPATCH(c, fn, ...)                                  \
-    switch ((c)->cfg.precision) {                                   \
-        case MCLBM_FP64: return fn<double>(__VA_ARGS__);            \
-        case MCLBM_FP32: return fn<float>(__VA_ARGS__);             \
-        default: return fn<__half>(__VA_ARGS__);                    \
+#define MCLBM_DISPATCH(prec, fn, ...)                    \
+    switch (prec) {                                      \
+        case MCLBM_FP64: return fn<double>(__VA_ARGS__); \
+        case MCLBM_FP32: return fn<float>(__VA_ARGS__);  \
+        default: return fn<__half>(__VA_ARGS__);         \
     }
 
-cudaError_t launch_init(const mclbm_ctx* c, const double* d_params) { MCLBM_DISPATCH(c, init_t, c, d_params); }
-cudaError_t launch_step(mclbm_ctx* c) { MCLBM_DISPATCH(c, step_t, c); }
+cudaError_t launch_init(const mclbm_ctx* c, const double* d_params)
+{
+    double* trig = (double*)(c->work + c->wl.trig);
+    MCLBM_DISPATCH(c->cfg.precision, init_t, c, d_params, trig);
+}
 cudaError_t launch_get_populations(const mclbm_ctx* c, int sample, double* d_out)
 {
-    MCLBM_DISPATCH(c, get_t, c, sample, d_out);
+    MCLBM_DISPATCH(c->cfg.precision, get_t, c, sample, d_out);
 }
 cudaError_t launch_set_populations(mclbm_ctx* c, int sample, const double* d_in)
 {
-    MCLBM_DISPATCH(c, set_t, c, sample, d_in);
+    MCLBM_DISPATCH(c->cfg.precision, set_t, c, sample, d_in);
+}
+
+bool vec_supported(int precision, int vec)
+{
+    auto in = [vec](const int* a, int n) {
+        for (int k = 0; k < n; ++k)
+            if (a[k] == vec) return true;
+        return false;
+    };
+    if (precision == MCLBM_FP64) return in(kVecF64, sizeof(kVecF64) / sizeof(int));
+    if (precision == MCLBM_FP32) return in(kVecF32, sizeof(kVecF32) / sizeof(int));
+    return in(kVecF16, sizeof(kVecF16) / sizeof(int));
+}
+
+cudaError_t launch_levels(mclbm_ctx* const* lv, int nlev, const LaunchConfig& cfg, cudaStream_t s, int* occ)
+{
+    if (nlev < 1 || nlev > kMaxLevels) return cudaErrorInvalidValue;
+    const int grid_cap = lv[0]->num_sms;
+    cudaError_t e;
+    switch (lv[0]->cfg.precision) {
+        case MCLBM_FP64: e = levels_t<double>(lv, nlev, cfg, grid_cap, s, occ); break;
+        case MCLBM_FP32: e = levels_t<float>(lv, nlev, cfg, grid_cap, s, occ); break;
+        default: e = levels_t<__half>(lv, nlev, cfg, grid_cap, s, occ); break;
+    }
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < nlev; ++k) {
+        if (lv[k]->cfg.pattern == MCLBM_PULL) lv[k]->cur ^= 1;
+        lv[k]->steps += 1;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_step(mclbm_ctx* c) { return launch_step_with(c, c->launch); }
+
+cudaError_t launch_step_with(mclbm_ctx* c, const LaunchConfig& cfg)
+{
+    mclbm_ctx* one[1] = {c};
+    return launch_levels(one, 1, cfg, c->stream, nullptr);
 }
 
 }  // namespace mclbm

@@ -1,0 +1,11 @@
+// Stepper variants: element type __half, aa streaming.
+#include "stepper_launch.cuh"
+
+namespace mclbm {
+
+cudaError_t launch_batch_f16_aa(const BatchArgs<__half>& a, const LaunchConfig& c, int grid_cap, cudaStream_t s, int* occ)
+{
+    return launch_vec_block<__half, 1, 2, 4, 8>(a, c, grid_cap, s, occ);
+}
+
+}  // namespace mclbm

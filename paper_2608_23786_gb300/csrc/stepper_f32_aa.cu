@@ -1,0 +1,11 @@
+// Stepper variants: element type float, aa streaming.
+#include "stepper_launch.cuh"
+
+namespace mclbm {
+
+cudaError_t launch_batch_f32_aa(const BatchArgs<float>& a, const LaunchConfig& c, int grid_cap, cudaStream_t s, int* occ)
+{
+    return launch_vec_block<float, 1, 1, 2, 4>(a, c, grid_cap, s, occ);
+}
+
+}  // namespace mclbm

@@ -1,0 +1,11 @@
+// Stepper variants: element type double, pull streaming.
+#include "stepper_launch.cuh"
+
+namespace mclbm {
+
+cudaError_t launch_batch_f64_pull(const BatchArgs<double>& a, const LaunchConfig& c, int grid_cap, cudaStream_t s, int* occ)
+{
+    return launch_vec_block<double, 0, 1, 2>(a, c, grid_cap, s, occ);
+}
+
+}  // namespace mclbm

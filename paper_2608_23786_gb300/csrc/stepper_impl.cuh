@@ -1,0 +1,313 @@
+// Fused stream + KBC collide kernel (Eq. (lbIteration) with Eqs. (kbcCollision),
+// (entropyControl)) over a batch of levels, each an ensemble of samples.
+//
+// Thread mapping.  One thread updates VEC consecutive nodes along x of one row of
+// one sample; consecutive threads take consecutive runs of a row, so a warp reads
+// and writes 32 * VEC consecutive elements of each population array with VEC-wide
+// (up to 16-byte) loads and stores.  The threads of all levels of a launch form one
+// linear index space (levels concatenated, samples slowest within a level); every
+// level contributes a multiple of 32 threads, so a warp never spans two levels.  The
+// grid is persistent: each thread strides over that space.
+//
+// x-shifts.  A population with c_x = +1 is gathered from x - 1: a thread loads its
+// own aligned run and takes the element before it from the previous lane with a
+// warp shuffle; only the first lane of a warp and the thread at the start of a row
+// (periodic wrap) load that element directly.  c_x = -1 mirrors this with the next
+// lane.  y- and z-shifts only move the row, so those loads stay aligned.
+//
+// Patterns.  pull: read f_i(x) = S_i(x - c_i) from one lattice, write f*_i(x) to
+// slot i of x in the other.  AA (in place, parity per level): even steps read slot i
+// and write slot opp(i) of the own node; odd steps read slot opp(i) of x - c_i and
+// write slot i of x + c_i.  In the odd step a node's outgoing value for c_x = +-1
+// lands in the neighbour's run: it travels by warp shuffle to the lane that owns the
+// destination run, which stores a full aligned vector; where the destination run
+// belongs to a lane that cannot receive it (first lane of a warp or start of a row),
+// the owner stores that single element itself and the receiver stores the rest of
+// its run element by element.  Every slot is written exactly once, and a slot read
+// by one lane is written by another only after the shuffle that depends on the
+// reader's loaded data.
+#pragma once
+#include <cuda_fp16.h>
+
+#include <cstring>
+
+#include "collide.cuh"
+#include "launch.h"
+#include "storage.cuh"
+
+namespace mclbm {
+
+
+
+template <class E>
+struct LevelArgs {
+    const E* src;   // pull: current lattice; AA: the lattice
+    E* dst;         // pull: next lattice; AA: same as src
+    Geom g;
+    int M;
+    int parity;     // AA: steps taken & 1
+    float omega32;
+    double omega64;
+};
+
+template <class E>
+struct BatchArgs {
+    int nlev;
+    int64_t prefix[kMaxLevels + 1];  // thread offsets of the levels (multiples of 32)
+    LevelArgs<E> lev[kMaxLevels];
+};
+
+template <int BYTES>
+struct RawOf;
+template <>
+struct RawOf<2> {
+    using type = unsigned short;
+};
+template <>
+struct RawOf<4> {
+    using type = unsigned int;
+};
+template <>
+struct RawOf<8> {
+    using type = uint2;
+};
+template <>
+struct RawOf<16> {
+    using type = uint4;
+};
+
+template <class E, int VEC>
+__device__ __forceinline__ void vload(const E* p, E (&out)[VEC])
+{
+    using R = typename RawOf<VEC * sizeof(E)>::type;
+    const R r = __ldg(reinterpret_cast<const R*>(p));
+    memcpy(out, &r, sizeof(R));
+}
+
+template <class E, int VEC>
+__device__ __forceinline__ void vstore(E* p, const E (&in)[VEC])
+{
+    using R = typename RawOf<VEC * sizeof(E)>::type;
+    R r;
+    memcpy(&r, in, sizeof(R));
+    *reinterpret_cast<R*>(p) = r;
+}
+
+template <class E>
+__device__ __forceinline__ E sload(const E* p)
+{
+    return __ldg(p);
+}
+template <>
+__device__ __forceinline__ __half sload<__half>(const __half* p)
+{
+    return __ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p)));
+}
+
+template <class E>
+__device__ __forceinline__ typename Storage<E>::compute to_c(E v)
+{
+    return (typename Storage<E>::compute)v;
+}
+template <>
+__device__ __forceinline__ float to_c<__half>(__half v)
+{
+    return __half2float(v);
+}
+template <class E>
+__device__ __forceinline__ E from_c(typename Storage<E>::compute v)
+{
+    return (E)v;
+}
+template <>
+__device__ __forceinline__ __half from_c<__half>(float v)
+{
+    return __float2half_rn(v);
+}
+
+template <class E>
+__device__ __forceinline__ typename Storage<E>::compute omega_of(const LevelArgs<E>& L);
+template <>
+__device__ __forceinline__ double omega_of<double>(const LevelArgs<double>& L) { return L.omega64; }
+template <>
+__device__ __forceinline__ float omega_of<float>(const LevelArgs<float>& L) { return L.omega32; }
+template <>
+__device__ __forceinline__ float omega_of<__half>(const LevelArgs<__half>& L) { return L.omega32; }
+
+// Gather the VEC values x0 - cxi .. x0 + VEC - 1 - cxi of one row (periodic in x).
+template <class E, int VEC, int CXI>
+__device__ __forceinline__ void gather_row(const E* row, int x0, int N, int lane, typename Storage<E>::compute (&v)[VEC])
+{
+    E w[VEC];
+    vload<E, VEC>(row + x0, w);
+    if constexpr (CXI == 0) {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) v[k] = to_c<E>(w[k]);
+    } else if constexpr (CXI > 0) {  // source x - 1
+        E prev = __shfl_up_sync(0xffffffffu, w[VEC - 1], 1);
+        if (lane == 0 || x0 == 0) prev = sload<E>(row + ((x0 - 1) & (N - 1)));
+        v[0] = to_c<E>(prev);
+#pragma unroll
+        for (int k = 1; k < VEC; ++k) v[k] = to_c<E>(w[k - 1]);
+    } else {  // source x + 1
+        E next = __shfl_down_sync(0xffffffffu, w[0], 1);
+        if (lane == 31 || x0 + VEC == N) next = sload<E>(row + ((x0 + VEC) & (N - 1)));
+#pragma unroll
+        for (int k = 0; k < VEC - 1; ++k) v[k] = to_c<E>(w[k + 1]);
+        v[VEC - 1] = to_c<E>(next);
+    }
+}
+
+// Scatter the VEC values of nodes x0..x0+VEC-1 to positions shifted by CXI in x.
+template <class E, int VEC, int CXI>
+__device__ __forceinline__ void scatter_row(E* row, int x0, int N, int lane, const typename Storage<E>::compute (&v)[VEC])
+{
+    E w[VEC];
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) w[k] = from_c<E>(v[k]);
+    if constexpr (CXI == 0) {
+        vstore<E, VEC>(row + x0, w);
+    } else if constexpr (CXI > 0) {  // node x goes to x + 1
+        const E prev = __shfl_up_sync(0xffffffffu, w[VEC - 1], 1);
+        const bool can_receive = lane != 0 && x0 != 0;
+        if (lane == 31 || x0 + VEC == N) row[(x0 + VEC) & (N - 1)] = w[VEC - 1];
+        if (can_receive) {
+            E o[VEC];
+            o[0] = prev;
+#pragma unroll
+            for (int k = 1; k < VEC; ++k) o[k] = w[k - 1];
+            vstore<E, VEC>(row + x0, o);
+        } else {
+#pragma unroll
+            for (int k = 1; k < VEC; ++k) row[x0 + k] = w[k - 1];
+        }
+    } else {  // node x goes to x - 1
+        const E next = __shfl_down_sync(0xffffffffu, w[0], 1);
+        const bool can_receive = lane != 31 && x0 + VEC != N;
+        if (lane == 0 || x0 == 0) row[(x0 - 1) & (N - 1)] = w[0];
+        if (can_receive) {
+            E o[VEC];
+#pragma unroll
+            for (int k = 0; k < VEC - 1; ++k) o[k] = w[k + 1];
+            o[VEC - 1] = next;
+            vstore<E, VEC>(row + x0, o);
+        } else {
+#pragma unroll
+            for (int k = 0; k < VEC - 1; ++k) row[x0 + k] = w[k + 1];
+        }
+    }
+}
+
+template <class E, int VEC>
+__device__ __forceinline__ void collide_run(typename Storage<E>::compute (&v)[Q][VEC], typename Storage<E>::compute omega)
+{
+    using C = typename Storage<E>::compute;
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+        C t[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) t[i] = v[i][k];
+        if constexpr (Storage<E>::shifted)
+            kbc_shifted(t, omega);
+        else
+            kbc_raw(t, omega);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) v[i][k] = t[i];
+    }
+}
+
+template <int I>
+struct Dir {
+    static constexpr int x = cx(I), y = cy(I), z = cz(I), o = opp(I);
+};
+
+// Load all Q populations of a run: slot SLOT(i) of the row shifted by -c_i.
+template <class E, int VEC, bool OPP_SLOT, int I = 0>
+__device__ __forceinline__ void gather_all(const E* base, const Geom& g, int x0, int y, int z, int lane,
+                                           typename Storage<E>::compute (&v)[Q][VEC])
+{
+    if constexpr (I < Q) {
+        constexpr int slot = OPP_SLOT ? Dir<I>::o : I;
+        const E* row = base + (int64_t)slot * g.n + g.node(0, g.wrap(y - Dir<I>::y), g.wrap(z - Dir<I>::z));
+        gather_row<E, VEC, Dir<I>::x>(row, x0, g.N, lane, v[I]);
+        gather_all<E, VEC, OPP_SLOT, I + 1>(base, g, x0, y, z, lane, v);
+    }
+}
+
+// Store all Q post-collision populations: slot I of the row shifted by SIGN * c_i.
+template <class E, int VEC, int SIGN, int I = 0>
+__device__ __forceinline__ void scatter_all(E* base, const Geom& g, int x0, int y, int z, int lane,
+                                            const typename Storage<E>::compute (&v)[Q][VEC])
+{
+    if constexpr (I < Q) {
+        E* row = base + (int64_t)I * g.n + g.node(0, g.wrap(y + SIGN * Dir<I>::y), g.wrap(z + SIGN * Dir<I>::z));
+        scatter_row<E, VEC, SIGN * Dir<I>::x>(row, x0, g.N, lane, v[I]);
+        scatter_all<E, VEC, SIGN, I + 1>(base, g, x0, y, z, lane, v);
+    }
+}
+
+// Own-node aligned access with slot permutation (AA even step).
+template <class E, int VEC>
+__device__ __forceinline__ void load_own(const E* base, const Geom& g, int64_t node, typename Storage<E>::compute (&v)[Q][VEC])
+{
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        E w[VEC];
+        vload<E, VEC>(base + (int64_t)i * g.n + node, w);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) v[i][k] = to_c<E>(w[k]);
+    }
+}
+template <class E, int VEC>
+__device__ __forceinline__ void store_own_opp(E* base, const Geom& g, int64_t node, const typename Storage<E>::compute (&v)[Q][VEC])
+{
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        E w[VEC];
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) w[k] = from_c<E>(v[i][k]);
+        vstore<E, VEC>(base + (int64_t)opp(i) * g.n + node, w);
+    }
+}
+
+// PATTERN: 0 pull, 1 AA.
+template <class E, int VEC, int PATTERN, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_step_batch(const BatchArgs<E> args)
+{
+    using C = typename Storage<E>::compute;
+    const int lane = threadIdx.x & 31;
+    const int64_t total = args.prefix[args.nlev];
+    for (int64_t t = blockIdx.x * (int64_t)BLOCK + threadIdx.x; t < total; t += (int64_t)gridDim.x * BLOCK) {
+        int l = 0;
+#pragma unroll 1
+        while (l + 1 < args.nlev && t >= args.prefix[l + 1]) ++l;
+        const LevelArgs<E>& L = args.lev[l];
+        const Geom g = L.g;
+        const int64_t first = (t - args.prefix[l]) * VEC;  // first node, ensemble-linear
+        const int m = (int)(first >> (3 * g.logN));
+        const int64_t node = first & (g.n - 1);
+        const int x0 = (int)(node & (g.N - 1));
+        const int y = (int)((node >> g.logN) & (g.N - 1));
+        const int z = (int)(node >> (2 * g.logN));
+        const C omega = omega_of<E>(L);
+        C v[Q][VEC];
+        if constexpr (PATTERN == 0) {
+            gather_all<E, VEC, false>(L.src + (int64_t)m * Q * g.n, g, x0, y, z, lane, v);
+            collide_run<E, VEC>(v, omega);
+            scatter_all<E, VEC, 0>(L.dst + (int64_t)m * Q * g.n, g, x0, y, z, lane, v);
+        } else {
+            E* base = L.dst + (int64_t)m * Q * g.n;
+            if (L.parity == 0) {
+                load_own<E, VEC>(base, g, node, v);
+                collide_run<E, VEC>(v, omega);
+                store_own_opp<E, VEC>(base, g, node, v);
+            } else {
+                gather_all<E, VEC, true>(base, g, x0, y, z, lane, v);
+                collide_run<E, VEC>(v, omega);
+                scatter_all<E, VEC, 1>(base, g, x0, y, z, lane, v);
+            }
+        }
+    }
+}
+
+}  // namespace mclbm

@@ -78,6 +78,16 @@ _SIGNATURES = {
     "mclbm_w1_work_bytes": (_c.c_size_t, [_c.c_int32, _c.c_int32, _c.c_int32]),
     "mclbm_w1_restricted": (_c.c_int, [_vp, _c.c_int32, _vp, _c.c_int32, _c.c_int32, _vp, _c.c_size_t, _vp, _dp, _dp]),
     "mclbm_check_finite": (_c.c_int, [_ctx_p]),
+    "mclbm_set_launch": (_c.c_int, [_ctx_p, _c.c_int32, _c.c_int32]),
+    "mclbm_get_launch": (_c.c_int, [_ctx_p, _i32p, _i32p]),
+    "mclbm_autotune": (_c.c_int, [_ctx_p, _c.c_int32, _i32p, _i32p, _dp]),
+    "mclbm_batch_create": (_c.c_int, [_c.POINTER(_ctx_p), _c.c_int32, _i32p, _c.POINTER(_vp)]),
+    "mclbm_batch_destroy": (None, [_vp]),
+    "mclbm_batch_set_graph": (_c.c_int, [_vp, _c.c_int32]),
+    "mclbm_batch_set_launch": (_c.c_int, [_vp, _c.c_int32, _c.c_int32]),
+    "mclbm_batch_step": (_c.c_int, [_vp, _c.c_int64]),
+    "mclbm_batch_macro_steps": (_c.c_int64, [_vp]),
+    "mclbm_batch_autotune": (_c.c_int, [_vp, _c.c_int32, _i32p, _i32p, _dp]),
 }
 
 _lib = None
@@ -260,3 +270,54 @@ def mclbm_w1_restricted(d_a, MA, d_b, MB, G, d_work, work_bytes, stream=0, per_p
 
 def mclbm_check_finite(ctx):
     _check(load().mclbm_check_finite(ctx))
+
+
+def mclbm_set_launch(ctx, vec, block):
+    _check(load().mclbm_set_launch(ctx, int(vec), int(block)))
+
+
+def mclbm_get_launch(ctx):
+    v, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().mclbm_get_launch(ctx, ctypes.byref(v), ctypes.byref(b)))
+    return v.value, b.value
+
+
+def mclbm_autotune(ctx, trial_steps=5):
+    v, b, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _check(load().mclbm_autotune(ctx, int(trial_steps), ctypes.byref(v), ctypes.byref(b), ctypes.byref(ms)))
+    return v.value, b.value, ms.value
+
+
+def mclbm_batch_create(ctxs, substeps):
+    n = len(ctxs)
+    arr = (_ctx_p * n)(*[c.value if isinstance(c, _ctx_p) else c for c in ctxs])
+    sub = (ctypes.c_int32 * n)(*[int(s) for s in substeps])
+    out = _vp()
+    _check(load().mclbm_batch_create(arr, n, sub, ctypes.byref(out)))
+    return out
+
+
+def mclbm_batch_destroy(b):
+    load().mclbm_batch_destroy(b)
+
+
+def mclbm_batch_set_graph(b, enable):
+    _check(load().mclbm_batch_set_graph(b, int(bool(enable))))
+
+
+def mclbm_batch_set_launch(b, vec, block):
+    _check(load().mclbm_batch_set_launch(b, int(vec), int(block)))
+
+
+def mclbm_batch_step(b, macro_steps):
+    _check(load().mclbm_batch_step(b, int(macro_steps)))
+
+
+def mclbm_batch_macro_steps(b):
+    return load().mclbm_batch_macro_steps(b)
+
+
+def mclbm_batch_autotune(b, trials=2):
+    v, blk, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _check(load().mclbm_batch_autotune(b, int(trials), ctypes.byref(v), ctypes.byref(blk), ctypes.byref(ms)))
+    return v.value, blk.value, ms.value

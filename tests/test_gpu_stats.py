@@ -111,7 +111,9 @@ def test_sf_axes(N, pmax):
 
 def test_restrict():
     ens, u = _pair(N=16, M=3)
-    np.testing.assert_allclose(ens.restrict(8).cpu().numpy(), stats.restrict(u, 8), rtol=1e-13, atol=1e-16)
+    ref = stats.restrict(u, 8)
+    # components near zero come from sums of +-f ~ 0.03: compare against the velocity scale
+    np.testing.assert_allclose(ens.restrict(8).cpu().numpy(), ref, rtol=0, atol=1e-13 * np.abs(ref).max())
 
 
 @pytest.mark.parametrize("MA,MB", [(4, 4), (3, 7)])

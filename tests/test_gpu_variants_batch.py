@@ -1,0 +1,117 @@
+"""Launch-shape variants, the autotuner, and the batched multi-level launch with CUDA-graph
+replay: all must give bit-identical states to the plain single-level path (every variant
+does the same per-node arithmetic), which the oracle parity tests pin."""
+import numpy as np
+import pytest
+import torch
+
+import ensemble_inputs as gen
+from paper_2608_23786_gb300 import Ensemble, mclbm
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = {"fp64": [1, 2], "fp32": [1, 2, 4], "fp16": [2, 4, 8]}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    mclbm.load(build_if_missing=True)
+
+
+def _states(ens):
+    return [ens.populations(m) for m in range(ens.M)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
+@pytest.mark.parametrize("pattern", ["pull", "aa"])
+@pytest.mark.parametrize("N,steps", [(8, 3), (32, 5), (64, 2)])
+def test_every_launch_shape_gives_identical_states(precision, pattern, N, steps):
+    """N = 8 (a row is one or a few threads: every lane is a row start), 32 and 64 (rows
+    span part of a warp, a full warp, or several)."""
+    X = gen.draw_params(31, 2)
+    ref = None
+    for vec in VARIANTS[precision]:
+        if N % vec:
+            continue
+        for block in (128, 256):
+            ens = Ensemble(N, 2, Re=300.0, Ma=0.1, precision=precision, pattern=pattern).init(X)
+            mclbm.mclbm_set_launch(ens.ctx, vec, block)
+            ens.step(steps)
+            got = _states(ens)
+            if ref is None:
+                ref = got
+            else:
+                for a, b in zip(ref, got):
+                    assert torch.equal(a, b), (vec, block)
+    # and AA equals pull for the default shape
+    other = Ensemble(N, 2, Re=300.0, Ma=0.1, precision=precision,
+                     pattern="pull" if pattern == "aa" else "aa").init(X).step(steps)
+    for a, b in zip(ref, _states(other)):
+        assert torch.equal(a, b)
+
+
+def test_autotune_picks_a_supported_shape_and_restores_the_initial_state():
+    ens = Ensemble(32, 4, Re=400.0, Ma=0.05, precision="fp32", seed=9).init()
+    before = _states(ens)
+    vec, block, ms = mclbm.mclbm_autotune(ens.ctx, 2)
+    assert vec in VARIANTS["fp32"] and block in (128, 256) and ms > 0
+    assert mclbm.mclbm_get_launch(ens.ctx) == (vec, block)
+    assert ens.steps_taken == 0
+    for a, b in zip(before, _states(ens)):
+        assert torch.equal(a, b)
+    ens.step(1)
+    with pytest.raises(mclbm.MclbmError):
+        mclbm.mclbm_autotune(ens.ctx, 1)
+
+
+def _levels(precision, pattern, stream, sizes=((16, 3), (32, 2), (64, 1)), seeds=(1, 2, 3)):
+    res = (400.0, 1600.0, 3200.0)
+    mas = (0.1, 0.05, 0.025)
+    out = []
+    for (N, M), Re, Ma, s in zip(sizes, res, mas, seeds):
+        out.append(Ensemble(N, M, Re=Re, Ma=Ma, precision=precision, pattern=pattern, seed=s,
+                            stream=stream).init())
+    return out
+
+
+@pytest.mark.parametrize("precision,pattern", [("fp32", "pull"), ("fp32", "aa"), ("fp16", "aa"), ("fp64", "pull")])
+@pytest.mark.parametrize("substeps,graph,macro", [((1, 4, 16), True, 3), ((1, 4, 16), False, 2), ((2, 4, 8), True, 4),
+                                                   ((1, 2, 4), True, 5)])
+def test_batch_equals_separate_levels(precision, pattern, substeps, graph, macro):
+    """One persistent launch per sub-step over all levels (and its graph replay) equals
+    stepping each level on its own by macro * substeps[l] steps, bit for bit; includes odd
+    per-level step counts (graph period of two macro steps) and a macro count that is not a
+    multiple of the period."""
+    stream = torch.cuda.Stream()
+    lv = _levels(precision, pattern, stream)
+    ref = _levels(precision, pattern, stream)
+    b = mclbm.mclbm_batch_create([e.ctx for e in lv], substeps)
+    try:
+        mclbm.mclbm_batch_set_graph(b, graph)
+        mclbm.mclbm_batch_step(b, macro)
+        assert mclbm.mclbm_batch_macro_steps(b) == macro
+        stream.synchronize()
+        for e, r, s in zip(lv, ref, substeps):
+            r.step(macro * s)
+            assert e.steps_taken == macro * s
+            for a, c in zip(_states(e), _states(r)):
+                assert torch.equal(a, c)
+    finally:
+        mclbm.mclbm_batch_destroy(b)
+
+
+def test_batch_autotune_and_validation():
+    stream = torch.cuda.Stream()
+    lv = _levels("fp32", "pull", stream)
+    b = mclbm.mclbm_batch_create([e.ctx for e in lv], (1, 4, 16))
+    try:
+        vec, block, ms = mclbm.mclbm_batch_autotune(b, 1)
+        assert vec in VARIANTS["fp32"] and ms > 0
+        assert all(e.steps_taken == 0 for e in lv)
+    finally:
+        mclbm.mclbm_batch_destroy(b)
+    with pytest.raises(mclbm.MclbmError):
+        mclbm.mclbm_batch_create([e.ctx for e in lv], (1, 3, 16))  # 3 does not divide 16
+    other = Ensemble(16, 1, Re=100.0, Ma=0.1, precision="fp16", stream=stream).init()
+    with pytest.raises(mclbm.MclbmError):
+        mclbm.mclbm_batch_create([lv[0].ctx, other.ctx], (1, 4))  # mixed precision
