@@ -202,6 +202,8 @@ def main():
     X = gen.draw_params(wl["seed"], wl["M"], first_sample=rank * wl["M"])
     ens = Ensemble(wl["N"], wl["M"], Re=wl["Re"], Ma=wl["Ma"], precision=wl["precision"], pattern=wl["pattern"],
                    seed=wl["seed"], device=dev, stream=stream).init(X)
+    # launch shape picked by the library's autotuner on this ensemble (restores the initial state)
+    tuned = mclbm.mclbm_autotune(ens.ctx, 3)
     mean = torch.empty((3,) + (wl["N"],) * 3, dtype=torch.float64, device=dev)
     var = torch.empty_like(mean)
     E = np.zeros(wl["M"])
@@ -309,8 +311,10 @@ def main():
         ("f16-storage/f32" if wl["precision"] == "fp16" else "f64"), "data": "synthetic",
         "config": {"workload": wl["name"], "N": wl["N"], "M_per_gpu": wl["M"], "Re": wl["Re"], "Ma": wl["Ma"],
                    "storage": wl["precision"], "streaming": wl["pattern"], "updates_per_step": S,
-                   "reductions_per_step": ["E_m(t)", "mean/var fields"], "l2": "inputs (2.55 GB) larger than L2"},
-        "roofline": {"kernel": "k_step_pull<float>" if wl["pattern"] == "pull" else "k_step_aa<float>",
+                   "reductions_per_step": ["E_m(t)", "mean/var fields"], "l2": "inputs (2.55 GB) larger than L2",
+                   "launch": {"kind": ["direct", "staged"][tuned[0]], "vec": tuned[1], "block": tuned[2]}},
+        "roofline": {"kernel": ("k_step_staged" if tuned[0] == 1 else "k_step_batch") +
+                     f"<{wl['precision']},{wl['pattern']},vec={tuned[1]}" + (f",block={tuned[2]}>" if tuned[0] == 0 else ">"),
                      "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "peak_kind": peak_kind,
                      "traffic": traffic, "algorithmic_bytes_per_launch": bpl,
@@ -323,6 +327,7 @@ def main():
         "clocks": clk.summary(),
         "stepper_sources_sha256": digest,
     }
+    mclbm.mclbm_device_status(ens.ctx)
     print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()

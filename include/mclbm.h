@@ -216,19 +216,24 @@ MCLBM_API int mclbm_w1_restricted(const double* d_a, int32_t MA, const double* d
                         size_t work_bytes, void* cuda_stream, double* W, double* per_point);
 
 /* ---- launch shape and autotuning ------------------------------------------
- * The stepper kernel updates `vec` consecutive nodes along x per thread (vec-wide
- * loads and stores, warp shuffles for the x-shifts) in blocks of `block` threads on a
- * persistent grid.  Supported: vec in {1, 2} (FP64), {1, 2, 4} (FP32), {2, 4, 8}
- * (FP16), dividing N; block in {128, 256}.  Results do not depend on the shape. */
-MCLBM_API int mclbm_set_launch(mclbm_ctx* ctx, int32_t vec, int32_t block);
-MCLBM_API int mclbm_get_launch(const mclbm_ctx* ctx, int32_t* vec, int32_t* block);
+ * kind 0: the direct stepper kernel updates `vec` consecutive nodes along x per
+ * thread (vec-wide loads and stores, warp shuffles for the x-shifts) in blocks of
+ * `block` threads on a persistent grid; vec in {1, 2} (FP64), {1, 2, 4} (FP32),
+ * {2, 4, 8} (FP16), dividing N; block in {128, 256}.
+ * kind 1: the staged kernel (one producer warp stages each tile's source rows in
+ * shared memory with bulk asynchronous copies; eight consumer warps collide `vec`
+ * in {1, 2} nodes per thread); `block` is ignored.
+ * Results do not depend on the shape (same arithmetic per node). */
+MCLBM_API int mclbm_set_launch(mclbm_ctx* ctx, int32_t kind, int32_t vec, int32_t block);
+MCLBM_API int mclbm_get_launch(const mclbm_ctx* ctx, int32_t* kind, int32_t* vec, int32_t* block);
 
 /* Time every supported shape on this context for trial_steps steps each (CUDA events
  * on the context's stream), keep the fastest, and restore the initial state by
  * re-running the initialisation from the stored parameters.  Must directly follow
  * mclbm_init_ensemble / mclbm_init_tgv (INVALID_ARG otherwise).  Outputs may be NULL;
  * best_ms is the time per step.  Synchronises. */
-MCLBM_API int mclbm_autotune(mclbm_ctx* ctx, int32_t trial_steps, int32_t* vec, int32_t* block, double* best_ms);
+MCLBM_API int mclbm_autotune(mclbm_ctx* ctx, int32_t trial_steps, int32_t* kind, int32_t* vec, int32_t* block,
+                             double* best_ms);
 
 /* ---- batched levels of the viscosity sequence --------------------------------
  * Levels (contexts sharing device, stream, precision and pattern) advanced
@@ -242,13 +247,40 @@ typedef struct mclbm_batch mclbm_batch;
 MCLBM_API int mclbm_batch_create(mclbm_ctx* const* levels, int32_t nlev, const int32_t* substeps, mclbm_batch** out);
 MCLBM_API void mclbm_batch_destroy(mclbm_batch* b);
 MCLBM_API int mclbm_batch_set_graph(mclbm_batch* b, int32_t enable);
-MCLBM_API int mclbm_batch_set_launch(mclbm_batch* b, int32_t vec, int32_t block);
+MCLBM_API int mclbm_batch_set_launch(mclbm_batch* b, int32_t kind, int32_t vec, int32_t block);
 /* Enqueue macro_steps macro steps.  Enqueued only. */
 MCLBM_API int mclbm_batch_step(mclbm_batch* b, int64_t macro_steps);
 MCLBM_API int64_t mclbm_batch_macro_steps(const mclbm_batch* b);
 /* Autotune the batch's launch shape (one macro step per trial, trials trials per
  * shape), then re-initialise every level.  Must directly follow initialisation. */
-MCLBM_API int mclbm_batch_autotune(mclbm_batch* b, int32_t trials, int32_t* vec, int32_t* block, double* best_ms);
+MCLBM_API int mclbm_batch_autotune(mclbm_batch* b, int32_t trials, int32_t* kind, int32_t* vec, int32_t* block,
+                                   double* best_ms);
+
+/* ---- adjoint (gradients w.r.t. the 24 parameters) ------------------------------
+ * Discrete adjoint of the time stepping: for J_m = E_m(T) (objective 0, kinetic
+ * energy) or Z_m(T) (objective 1, enstrophy) of every sample m after nsteps steps,
+ * dJ_m/dX_m [M][24] with X_m the sample's parameters (Eq. (alpha_perturbation)).
+ * The reverse sweep applies the transpose of streaming and the hand-written
+ * transpose of the KBC collision Jacobian, including the derivative of the closed-form
+ * gamma of Eq. (entropyControl); states are checkpointed every ckpt_every steps and
+ * each segment is recomputed from its checkpoint.  Pull streaming only.  The context
+ * must directly follow an initialisation; on return it holds the state at step nsteps.
+ * d_buf: caller device buffer of mclbm_grad_required_bytes() bytes (256-aligned).
+ * J [M], dJdX [M][24]: host.  Synchronises.  Errors: INVALID_ARG, OOM, CUDA. */
+MCLBM_API int mclbm_grad_required_bytes(const mclbm_ctx* ctx, int64_t nsteps, int32_t ckpt_every, size_t* bytes);
+MCLBM_API int mclbm_grad(mclbm_ctx* ctx, int32_t objective, int64_t nsteps, int32_t ckpt_every, void* d_buf,
+                         size_t buf_bytes, double* J, double* dJdX);
+
+/* One transposed step on caller data, for checking the adjoint: given pre-collision
+ * populations f^t (raw, FP64) and lambda^{t+1} = dJ/df^{t+1}, writes
+ * lambda^t = dJ/df^t (all FP64 device [M][19][N][N][N], library velocity order),
+ * computed in the context's arithmetic (FP64 or FP32).  Enqueued only. */
+MCLBM_API int mclbm_adjoint_step(const mclbm_ctx* ctx, const double* d_f, const double* d_lambda_next, double* d_lambda);
+
+/* Synchronise the context's stream and report a bounded device wait that gave up
+ * since the last initialisation (MCLBM_ERR_TIMEOUT; the staged stepper's producer and
+ * consumer waits are bounded and set this instead of hanging). */
+MCLBM_API int mclbm_device_status(mclbm_ctx* ctx);
 
 /* Scan every stored population for NaN/Inf.  Returns MCLBM_OK or
  * MCLBM_ERR_NONFINITE.  Synchronises. */

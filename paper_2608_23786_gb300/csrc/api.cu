@@ -271,6 +271,7 @@ static int do_init(mclbm_ctx* c)
     MCLBM_CUDA(cudaMemcpyAsync(d_params, c->params.data(), sizeof(double) * 24 * c->M, cudaMemcpyHostToDevice, c->stream));
     c->cur = 0;
     c->steps = 0;
+    MCLBM_CUDA(cudaMemsetAsync(c->work + c->wl.flag, 0, 16 * sizeof(int), c->stream));
     MCLBM_CUDA(launch_init(c, d_params));
     return MCLBM_OK;
 }
@@ -431,6 +432,17 @@ int mclbm_w1_1pt(mclbm_ctx* A, const mclbm_ctx* B, int32_t Qd, double* W, double
     MCLBM_CUDA(launch_restrict(A, Qd, ra));
     MCLBM_CUDA(launch_restrict(&Bv, Qd, rb));
     MCLBM_CUDA(launch_w1(ra, A->M, rb, B->M, G, scratch, w1_work_bytes(A->M, B->M, G), A->stream, W, per_point));
+    return MCLBM_OK;
+}
+
+int mclbm_device_status(mclbm_ctx* ctx)
+{
+    if (!ctx) return set_error(MCLBM_ERR_INVALID_ARG, "ctx is NULL");
+    int flags[2] = {0, 0};
+    MCLBM_CUDA(cudaMemcpyAsync(flags, ctx->work + ctx->wl.flag, sizeof(flags), cudaMemcpyDeviceToHost, ctx->stream));
+    MCLBM_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (flags[1] == MCLBM_ERR_TIMEOUT)
+        return set_error(MCLBM_ERR_TIMEOUT, "a bounded device wait of the staged stepper gave up");
     return MCLBM_OK;
 }
 

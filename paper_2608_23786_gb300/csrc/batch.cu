@@ -149,7 +149,9 @@ std::vector<LaunchConfig> candidates(int precision, int N)
     }
     for (int i = 0; i < nv; ++i)
         for (int blk : kBlocks)
-            if (N % vecs[i] == 0) v.push_back(LaunchConfig{vecs[i], blk});
+            if (N % vecs[i] == 0) v.push_back(LaunchConfig{vecs[i], blk, 0});
+    for (int vs : kVecStaged)
+        if (N % vs == 0) v.push_back(LaunchConfig{vs, 0, 1});
     return v;
 }
 
@@ -157,25 +159,27 @@ std::vector<LaunchConfig> candidates(int precision, int N)
 
 extern "C" {
 
-int mclbm_set_launch(mclbm_ctx* ctx, int32_t vec, int32_t block)
+int mclbm_set_launch(mclbm_ctx* ctx, int32_t kind, int32_t vec, int32_t block)
 {
     if (!ctx) return set_error(MCLBM_ERR_INVALID_ARG, "ctx is NULL");
-    if (!vec_supported(ctx->cfg.precision, vec) || (block != 128 && block != 256) || ctx->N % vec)
-        return set_error(MCLBM_ERR_INVALID_ARG, "unsupported launch shape (vec " + std::to_string(vec) + ", block " +
-                                                    std::to_string(block) + ")");
-    ctx->launch = LaunchConfig{vec, block};
+    const LaunchConfig c{vec, kind == 1 ? 0 : block, kind};
+    if (!launch_supported(ctx->cfg.precision, c) || vec < 1 || ctx->N % vec)
+        return set_error(MCLBM_ERR_INVALID_ARG, "unsupported launch shape (kind " + std::to_string(kind) + ", vec " +
+                                                    std::to_string(vec) + ", block " + std::to_string(block) + ")");
+    ctx->launch = c;
     return MCLBM_OK;
 }
 
-int mclbm_get_launch(const mclbm_ctx* ctx, int32_t* vec, int32_t* block)
+int mclbm_get_launch(const mclbm_ctx* ctx, int32_t* kind, int32_t* vec, int32_t* block)
 {
     if (!ctx) return set_error(MCLBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (kind) *kind = ctx->launch.kind;
     if (vec) *vec = ctx->launch.vec;
     if (block) *block = ctx->launch.block;
     return MCLBM_OK;
 }
 
-int mclbm_autotune(mclbm_ctx* ctx, int32_t trial_steps, int32_t* vec, int32_t* block, double* best_ms)
+int mclbm_autotune(mclbm_ctx* ctx, int32_t trial_steps, int32_t* kind, int32_t* vec, int32_t* block, double* best_ms)
 {
     if (!ctx || trial_steps < 1) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
     if (ctx->steps != 0) return set_error(MCLBM_ERR_INVALID_ARG, "autotune must directly follow an initialisation");
@@ -203,6 +207,7 @@ int mclbm_autotune(mclbm_ctx* ctx, int32_t trial_steps, int32_t* vec, int32_t* b
     ctx->launch = bestc;
     int st = reinit_ctx(ctx);
     if (st != MCLBM_OK) return st;
+    if (kind) *kind = bestc.kind;
     if (vec) *vec = bestc.vec;
     if (block) *block = bestc.block;
     if (best_ms) *best_ms = best / trial_steps;
@@ -260,13 +265,14 @@ int mclbm_batch_set_graph(mclbm_batch* b, int32_t enable)
     return MCLBM_OK;
 }
 
-int mclbm_batch_set_launch(mclbm_batch* b, int32_t vec, int32_t block)
+int mclbm_batch_set_launch(mclbm_batch* b, int32_t kind, int32_t vec, int32_t block)
 {
     if (!b) return set_error(MCLBM_ERR_INVALID_ARG, "batch is NULL");
+    const LaunchConfig lc{vec, kind == 1 ? 0 : block, kind};
     for (auto* c : b->lev)
-        if (!vec_supported(c->cfg.precision, vec) || c->N % vec || (block != 128 && block != 256))
+        if (!launch_supported(c->cfg.precision, lc) || vec < 1 || c->N % vec)
             return set_error(MCLBM_ERR_INVALID_ARG, "unsupported launch shape");
-    b->launch = LaunchConfig{vec, block};
+    b->launch = lc;
     clear_graphs(b);
     b->warmed = false;
     return MCLBM_OK;
@@ -299,7 +305,7 @@ int mclbm_batch_step(mclbm_batch* b, int64_t macro_steps)
     return MCLBM_OK;
 }
 
-int mclbm_batch_autotune(mclbm_batch* b, int32_t trials, int32_t* vec, int32_t* block, double* best_ms)
+int mclbm_batch_autotune(mclbm_batch* b, int32_t trials, int32_t* kind, int32_t* vec, int32_t* block, double* best_ms)
 {
     if (!b || trials < 1) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
     for (auto* c : b->lev)
@@ -338,6 +344,7 @@ int mclbm_batch_autotune(mclbm_batch* b, int32_t trials, int32_t* vec, int32_t* 
         if (st != MCLBM_OK) return st;
     }
     b->macro_steps = 0;
+    if (kind) *kind = bestc.kind;
     if (vec) *vec = bestc.vec;
     if (block) *block = bestc.block;
     if (best_ms) *best_ms = best / trials;

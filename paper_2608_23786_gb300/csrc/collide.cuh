@@ -95,8 +95,11 @@ __host__ __device__ __forceinline__ T kbc_raw(T (&f)[Q], T omega)
 // this the higher-order non-equilibrium is at rounding level).
 constexpr float kHHGuard = 1e-30f;
 
-// KBC on normalised deviations h_i = f_i / w_i - 1 (in place), FP32.
-__device__ __forceinline__ float kbc_shifted(float (&h)[Q], float omega)
+// KBC on normalised deviations h_i = f_i / w_i - 1 (in place), FP32.  a = 2/omega and
+// b = 2 - 2/omega are passed in (computed once on the host); the reciprocals 1/rho and
+// w_i / (1 + heq_i) and the quotient sh/hh use the fast approximate division (a few ulp,
+// below the FP32 rounding already present in the sums).
+__device__ __forceinline__ float kbc_shifted(float (&h)[Q], float omega, float a, float b)
 {
     constexpr float w0 = 1.0f / 3.0f, w1 = 1.0f / 18.0f, w2 = 1.0f / 36.0f;
     // density deviation and momentum: sum w h, sum w c h
@@ -110,7 +113,7 @@ __device__ __forceinline__ float kbc_shifted(float (&h)[Q], float omega)
     const float jx = w1 * (h[1] - h[2]) + w2 * ((h[7] - h[8]) + (h[9] - h[10]) + (h[11] - h[12]) + (h[13] - h[14]));
     const float jy = w1 * (h[3] - h[4]) + w2 * ((h[7] - h[8]) - (h[9] - h[10]) + (h[15] - h[16]) + (h[17] - h[18]));
     const float jz = w1 * (h[5] - h[6]) + w2 * ((h[11] - h[12]) - (h[13] - h[14]) + (h[15] - h[16]) - (h[17] - h[18]));
-    const float rinv = __frcp_rn(rho);
+    const float rinv = __fdividef(1.0f, rho);
     const float ux = jx * rinv, uy = jy * rinv, uz = jz * rinv;
     const float uu = ux * ux + uy * uy + uz * uz;
     float heq[Q], n[Q];
@@ -123,8 +126,8 @@ __device__ __forceinline__ float kbc_shifted(float (&h)[Q], float omega)
         heq[i] = drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
         n[i] = h[i] - heq[i];
     }
-    // second moments of f^neq / (normalised): P_ab = sum w c_a c_b n
-    const float ex = n[7] + n[8] + n[9] + n[10];   // xy edges
+    // second moments of f^neq (normalised): P_ab = sum w c_a c_b n
+    const float ex = n[7] + n[8] + n[9] + n[10];      // xy edges
     const float exz = n[11] + n[12] + n[13] + n[14];  // xz edges
     const float eyz = n[15] + n[16] + n[17] + n[18];  // yz edges
     const float pxx = w1 * (n[1] + n[2]) + w2 * (ex + exz);
@@ -151,12 +154,11 @@ __device__ __forceinline__ float kbc_shifted(float (&h)[Q], float omega)
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const float k = n[i] - s[i];
-        const float wr = weight<float>(i) * __frcp_rn(1.0f + heq[i]);
+        const float wr = __fdividef(weight<float>(i), 1.0f + heq[i]);
         sh += wr * s[i] * k;
         hh += wr * k * k;
     }
-    const float two_over = 2.0f / omega;
-    const float gamma = (hh <= kHHGuard) ? 2.0f : two_over - (2.0f - two_over) * __fdiv_rn(sh, hh);
+    const float gamma = (hh <= kHHGuard) ? 2.0f : a - b * __fdividef(sh, hh);
     const float bo = 0.5f * omega * gamma;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {

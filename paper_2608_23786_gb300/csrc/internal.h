@@ -75,6 +75,7 @@ cudaError_t launch_step_with(mclbm_ctx* c, const LaunchConfig& cfg);
 // one step of several levels in one launch; updates each level's cur and steps
 cudaError_t launch_levels(mclbm_ctx* const* levels, int nlev, const LaunchConfig& cfg, cudaStream_t s, int* occ);
 bool vec_supported(int precision, int vec);
+bool launch_supported(int precision, const LaunchConfig& c);
 LaunchConfig default_launch(int precision);
 cudaError_t launch_get_populations(const mclbm_ctx* c, int sample, double* d_out);
 cudaError_t launch_set_populations(mclbm_ctx* c, int sample, const double* d_in);

@@ -11,8 +11,9 @@ namespace mclbm {
 constexpr int kMaxLevels = 8;  // levels of one batched launch
 
 struct LaunchConfig {
-    int vec;    // nodes per thread along x
-    int block;  // threads per block (128 or 256)
+    int vec;       // nodes per thread along x
+    int block;     // threads per block (128 or 256); the staged kernel always uses 288
+    int kind = 0;  // 0: direct loads (stepper_impl.cuh), 1: shared-memory staging (stepper_staged.cuh)
 };
 
 // Variants compiled per element type (nodes per thread; VEC * sizeof(E) <= 16 bytes).
@@ -23,6 +24,10 @@ constexpr int kBlocks[] = {128, 256};
 
 template <class E>
 struct BatchArgs;
+template <class E>
+struct StagedArgs;
+
+constexpr int kVecStaged[] = {1, 2};  // nodes per consumer thread of the staged kernel
 
 // Launchers defined in stepper_<type>_<pattern>.cu.  grid_cap: SM count (the grid is
 // grid_cap times the variant's resident blocks per SM, or less for small batches).
@@ -30,7 +35,9 @@ struct BatchArgs;
     cudaError_t launch_batch_##T##_pull(const BatchArgs<E>& a, const LaunchConfig& c, int grid_cap, cudaStream_t s, \
                                         int* occ);                                                               \
     cudaError_t launch_batch_##T##_aa(const BatchArgs<E>& a, const LaunchConfig& c, int grid_cap, cudaStream_t s,   \
-                                      int* occ);
+                                      int* occ);                                                                 \
+    cudaError_t launch_staged_##T##_pull(StagedArgs<E>& a, const LaunchConfig& c, int grid_cap, cudaStream_t s);    \
+    cudaError_t launch_staged_##T##_aa(StagedArgs<E>& a, const LaunchConfig& c, int grid_cap, cudaStream_t s);
 MCLBM_DECLARE_LAUNCH(f64, double)
 MCLBM_DECLARE_LAUNCH(f32, float)
 MCLBM_DECLARE_LAUNCH(f16, __half)

@@ -6,6 +6,7 @@
 #include "internal.h"
 #include "launch.h"
 #include "stepper_impl.cuh"
+#include "stepper_staged.cuh"
 
 namespace mclbm {
 
@@ -175,11 +176,43 @@ void fill_level(LevelArgs<E>& L, const mclbm_ctx* c)
     L.parity = parity_of(c);
     L.omega32 = (float)c->units.omega;
     L.omega64 = c->units.omega;
+    L.a32 = (float)(2.0 / c->units.omega);
+    L.b32 = (float)(2.0 - 2.0 / c->units.omega);
+}
+
+template <class E>
+cudaError_t staged_t(mclbm_ctx* const* lv, int nlev, const LaunchConfig& cfg, int grid_cap, cudaStream_t s)
+{
+    StagedArgs<E> a;
+    memset(&a, 0, sizeof(a));
+    a.nlev = nlev;
+    a.tile_prefix[0] = 0;
+    const int target = kConsumerWarps * 32 * cfg.vec;  // nodes per tile
+    int max_nodes = 0;
+    for (int k = 0; k < nlev; ++k) {
+        const int N = lv[k]->N;
+        int ty = target / N;
+        ty = ty < 1 ? 1 : (ty > N ? N : ty);
+        a.ty[k] = ty;
+        if (ty * N > max_nodes) max_nodes = ty * N;
+        fill_level<E>(a.lev[k], lv[k]);
+        a.tile_prefix[k + 1] = a.tile_prefix[k] + (int64_t)lv[k]->M * N * (N / ty);
+    }
+    a.stage_elems = Q * max_nodes;
+    a.err = (int*)(lv[0]->work + lv[0]->wl.flag) + 1;
+    const bool pull = lv[0]->cfg.pattern == MCLBM_PULL;
+    if constexpr (std::is_same<E, double>::value)
+        return pull ? launch_staged_f64_pull(a, cfg, grid_cap, s) : launch_staged_f64_aa(a, cfg, grid_cap, s);
+    else if constexpr (std::is_same<E, float>::value)
+        return pull ? launch_staged_f32_pull(a, cfg, grid_cap, s) : launch_staged_f32_aa(a, cfg, grid_cap, s);
+    else
+        return pull ? launch_staged_f16_pull(a, cfg, grid_cap, s) : launch_staged_f16_aa(a, cfg, grid_cap, s);
 }
 
 template <class E>
 cudaError_t levels_t(mclbm_ctx* const* lv, int nlev, const LaunchConfig& cfg, int grid_cap, cudaStream_t s, int* occ)
 {
+    if (cfg.kind == 1) return staged_t<E>(lv, nlev, cfg, grid_cap, s);
     BatchArgs<E> a;
     memset(&a, 0, sizeof(a));
     a.nlev = nlev;
@@ -220,6 +253,13 @@ cudaError_t launch_set_populations(mclbm_ctx* c, int sample, const double* d_in)
     MCLBM_DISPATCH(c->cfg.precision, set_t, c, sample, d_in);
 }
 
+bool launch_supported(int precision, const LaunchConfig& c)
+{
+    if (c.kind == 1) return c.vec == 1 || c.vec == 2;
+    if (c.kind != 0 || (c.block != 128 && c.block != 256)) return false;
+    return vec_supported(precision, c.vec);
+}
+
 bool vec_supported(int precision, int vec)
 {
     auto in = [vec](const int* a, int n) {
@@ -251,6 +291,45 @@ cudaError_t launch_levels(mclbm_ctx* const* lv, int nlev, const LaunchConfig& cf
 }
 
 cudaError_t launch_step(mclbm_ctx* c) { return launch_step_with(c, c->launch); }
+
+// One pull step from an explicit source lattice to an explicit destination lattice (both
+// pull layout, same shape as the context's); the context's own state is not touched.
+cudaError_t launch_pull_explicit(mclbm_ctx* c, const void* src, void* dst)
+{
+    const LaunchConfig cfg = default_launch(c->cfg.precision);
+    switch (c->cfg.precision) {
+        case MCLBM_FP64: {
+            BatchArgs<double> a;
+            memset(&a, 0, sizeof(a));
+            a.nlev = 1;
+            fill_level<double>(a.lev[0], c);
+            a.lev[0].src = (const double*)src;
+            a.lev[0].dst = (double*)dst;
+            a.prefix[1] = (int64_t)c->M * c->n / cfg.vec;
+            return launch_batch_f64_pull(a, cfg, c->num_sms, c->stream, nullptr);
+        }
+        case MCLBM_FP32: {
+            BatchArgs<float> a;
+            memset(&a, 0, sizeof(a));
+            a.nlev = 1;
+            fill_level<float>(a.lev[0], c);
+            a.lev[0].src = (const float*)src;
+            a.lev[0].dst = (float*)dst;
+            a.prefix[1] = (int64_t)c->M * c->n / cfg.vec;
+            return launch_batch_f32_pull(a, cfg, c->num_sms, c->stream, nullptr);
+        }
+        default: {
+            BatchArgs<__half> a;
+            memset(&a, 0, sizeof(a));
+            a.nlev = 1;
+            fill_level<__half>(a.lev[0], c);
+            a.lev[0].src = (const __half*)src;
+            a.lev[0].dst = (__half*)dst;
+            a.prefix[1] = (int64_t)c->M * c->n / cfg.vec;
+            return launch_batch_f16_pull(a, cfg, c->num_sms, c->stream, nullptr);
+        }
+    }
+}
 
 cudaError_t launch_step_with(mclbm_ctx* c, const LaunchConfig& cfg)
 {

@@ -8,4 +8,9 @@ cudaError_t launch_batch_f32_pull(const BatchArgs<float>& a, const LaunchConfig&
     return launch_vec_block<float, 0, 1, 2, 4>(a, c, grid_cap, s, occ);
 }
 
+cudaError_t launch_staged_f32_pull(StagedArgs<float>& a, const LaunchConfig& c, int grid_cap, cudaStream_t s)
+{
+    return launch_staged_vec<float, 0>(a, c, grid_cap, s);
+}
+
 }  // namespace mclbm

@@ -48,6 +48,7 @@ struct LevelArgs {
     int parity;     // AA: steps taken & 1
     float omega32;
     double omega64;
+    float a32, b32;  // 2/omega and 2 - 2/omega of Eq. (entropyControl)
 };
 
 template <class E>
@@ -199,8 +200,9 @@ __device__ __forceinline__ void scatter_row(E* row, int x0, int N, int lane, con
 }
 
 template <class E, int VEC>
-__device__ __forceinline__ void collide_run(typename Storage<E>::compute (&v)[Q][VEC], typename Storage<E>::compute omega)
+__device__ __forceinline__ void collide_run(typename Storage<E>::compute (&v)[Q][VEC], const LevelArgs<E>& L)
 {
+    const typename Storage<E>::compute omega = omega_of<E>(L);
     using C = typename Storage<E>::compute;
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
@@ -208,7 +210,7 @@ __device__ __forceinline__ void collide_run(typename Storage<E>::compute (&v)[Q]
 #pragma unroll
         for (int i = 0; i < Q; ++i) t[i] = v[i][k];
         if constexpr (Storage<E>::shifted)
-            kbc_shifted(t, omega);
+            kbc_shifted(t, omega, L.a32, L.b32);
         else
             kbc_raw(t, omega);
 #pragma unroll
@@ -293,17 +295,17 @@ __global__ void __launch_bounds__(BLOCK) k_step_batch(const BatchArgs<E> args)
         C v[Q][VEC];
         if constexpr (PATTERN == 0) {
             gather_all<E, VEC, false>(L.src + (int64_t)m * Q * g.n, g, x0, y, z, lane, v);
-            collide_run<E, VEC>(v, omega);
+            collide_run<E, VEC>(v, L);
             scatter_all<E, VEC, 0>(L.dst + (int64_t)m * Q * g.n, g, x0, y, z, lane, v);
         } else {
             E* base = L.dst + (int64_t)m * Q * g.n;
             if (L.parity == 0) {
                 load_own<E, VEC>(base, g, node, v);
-                collide_run<E, VEC>(v, omega);
+                collide_run<E, VEC>(v, L);
                 store_own_opp<E, VEC>(base, g, node, v);
             } else {
                 gather_all<E, VEC, true>(base, g, x0, y, z, lane, v);
-                collide_run<E, VEC>(v, omega);
+                collide_run<E, VEC>(v, L);
                 scatter_all<E, VEC, 1>(base, g, x0, y, z, lane, v);
             }
         }

@@ -4,6 +4,7 @@
 #pragma once
 #include "launch.h"
 #include "stepper_impl.cuh"
+#include "stepper_staged.cuh"
 
 namespace mclbm {
 
@@ -46,6 +47,44 @@ cudaError_t launch_vec_block(const BatchArgs<E>& a, const LaunchConfig& cfg, int
     };
     (try_one(std::integral_constant<int, VECS>{}), ...);
     return e;
+}
+
+// Staged kernel: pick the number of stages so that two blocks fit on an SM, size the
+// dynamic shared memory, and launch a persistent grid (SM count x resident blocks).
+template <class E, int PATTERN, int VEC>
+cudaError_t launch_staged_variant(StagedArgs<E>& a, int grid_cap, cudaStream_t s)
+{
+    auto kern = k_step_staged<E, PATTERN, VEC>;
+    const size_t stage_bytes = (size_t)a.stage_elems * sizeof(E);
+    int stages = (int)((size_t)(110 * 1024) / stage_bytes);
+    stages = stages < 2 ? 2 : (stages > 4 ? 4 : stages);
+    a.stages = stages;
+    const size_t smem = 256 + (size_t)stages * stage_bytes;
+    static size_t configured = 0;
+    cudaError_t e;
+    if (smem > configured) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kStagedThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int64_t total = a.tile_prefix[a.nlev];
+    int64_t blocks = (int64_t)grid_cap * occ;
+    if (blocks > total) blocks = total;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, kStagedThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <class E, int PATTERN>
+cudaError_t launch_staged_vec(StagedArgs<E>& a, const LaunchConfig& cfg, int grid_cap, cudaStream_t s)
+{
+    if (cfg.vec == 1) return launch_staged_variant<E, PATTERN, 1>(a, grid_cap, s);
+    if (cfg.vec == 2) return launch_staged_variant<E, PATTERN, 2>(a, grid_cap, s);
+    return cudaErrorInvalidConfiguration;
 }
 
 }  // namespace mclbm

@@ -35,6 +35,11 @@ class Ensemble:
         with torch.cuda.device(self.device):
             self.pop = torch.empty(pop_bytes + 256, dtype=torch.uint8, device=self.device)
             self.work = torch.empty(work_bytes + 256, dtype=torch.uint8, device=self.device)
+        cur = torch.cuda.current_stream(self.device)
+        if cur != self.stream:  # buffers are allocated on the current stream, used on self.stream
+            self.stream.wait_stream(cur)
+            self.pop.record_stream(self.stream)
+            self.work.record_stream(self.stream)
         self._pop_ptr = (self.pop.data_ptr() + 255) // 256 * 256
         self._work_ptr = (self.work.data_ptr() + 255) // 256 * 256
         with torch.cuda.device(self.device):
@@ -51,6 +56,22 @@ class Ensemble:
     @property
     def n(self):
         return self.N**3
+
+    # ---- stream ordering between torch's current stream and the ensemble's stream ----
+    def _enter(self, *tensors):
+        """Make the ensemble's stream wait for work queued on torch's current stream (e.g. the
+        allocation or filling of `tensors`) and mark the tensors as used on that stream."""
+        cur = torch.cuda.current_stream(self.device)
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
+            for t in tensors:
+                t.record_stream(self.stream)
+
+    def _exit(self):
+        """Make torch's current stream wait for the ensemble's queued work."""
+        cur = torch.cuda.current_stream(self.device)
+        if cur != self.stream:
+            cur.wait_stream(self.stream)
 
     # ---- evolution -------------------------------------------------------------
     def init(self, params=None):
@@ -79,20 +100,25 @@ class Ensemble:
     def populations(self, sample=0):
         """Pre-collision f [19][N][N][N] (FP64, library velocity order) as a CUDA tensor."""
         out = torch.empty((19, self.N, self.N, self.N), dtype=torch.float64, device=self.device)
+        self._enter(out)
         _m.mclbm_get_populations(self.ctx, sample, out.data_ptr())
+        self._exit()
         return out
 
     def set_populations(self, f, sample=0):
         f = f.to(device=self.device, dtype=torch.float64).contiguous()
+        self._enter(f)
         _m.mclbm_set_populations(self.ctx, sample, f.data_ptr())
-        self.stream.synchronize()
+        self._exit()
         return self
 
     def moments(self, sample=0):
         """(rho [N][N][N], u [3][N][N][N] physical) FP64 CUDA tensors."""
         rho = torch.empty((self.N,) * 3, dtype=torch.float64, device=self.device)
         u = torch.empty((3,) + (self.N,) * 3, dtype=torch.float64, device=self.device)
+        self._enter(rho, u)
         _m.mclbm_moments(self.ctx, sample, rho.data_ptr(), u.data_ptr())
+        self._exit()
         return rho, u
 
     def energy(self, enstrophy=False):
@@ -104,7 +130,9 @@ class Ensemble:
     def mean_var(self):
         mean = torch.empty((3,) + (self.N,) * 3, dtype=torch.float64, device=self.device)
         var = torch.empty_like(mean)
+        self._enter(mean, var)
         _m.mclbm_mean_var(self.ctx, mean.data_ptr(), var.data_ptr())
+        self._exit()
         return mean, var
 
     def spectrum(self):
@@ -124,7 +152,9 @@ class Ensemble:
 
     def restrict(self, Q=8):
         out = torch.empty((self.M, Q**3, 3), dtype=torch.float64, device=self.device)
+        self._enter(out)
         _m.mclbm_restrict(self.ctx, Q, out.data_ptr())
+        self._exit()
         return out
 
     def w1(self, other, Q=8, per_point=False):

@@ -78,16 +78,20 @@ _SIGNATURES = {
     "mclbm_w1_work_bytes": (_c.c_size_t, [_c.c_int32, _c.c_int32, _c.c_int32]),
     "mclbm_w1_restricted": (_c.c_int, [_vp, _c.c_int32, _vp, _c.c_int32, _c.c_int32, _vp, _c.c_size_t, _vp, _dp, _dp]),
     "mclbm_check_finite": (_c.c_int, [_ctx_p]),
-    "mclbm_set_launch": (_c.c_int, [_ctx_p, _c.c_int32, _c.c_int32]),
-    "mclbm_get_launch": (_c.c_int, [_ctx_p, _i32p, _i32p]),
-    "mclbm_autotune": (_c.c_int, [_ctx_p, _c.c_int32, _i32p, _i32p, _dp]),
+    "mclbm_set_launch": (_c.c_int, [_ctx_p, _c.c_int32, _c.c_int32, _c.c_int32]),
+    "mclbm_get_launch": (_c.c_int, [_ctx_p, _i32p, _i32p, _i32p]),
+    "mclbm_autotune": (_c.c_int, [_ctx_p, _c.c_int32, _i32p, _i32p, _i32p, _dp]),
+    "mclbm_device_status": (_c.c_int, [_ctx_p]),
+    "mclbm_grad_required_bytes": (_c.c_int, [_ctx_p, _c.c_int64, _c.c_int32, _size_p]),
+    "mclbm_grad": (_c.c_int, [_ctx_p, _c.c_int32, _c.c_int64, _c.c_int32, _vp, _c.c_size_t, _dp, _dp]),
+    "mclbm_adjoint_step": (_c.c_int, [_ctx_p, _vp, _vp, _vp]),
     "mclbm_batch_create": (_c.c_int, [_c.POINTER(_ctx_p), _c.c_int32, _i32p, _c.POINTER(_vp)]),
     "mclbm_batch_destroy": (None, [_vp]),
     "mclbm_batch_set_graph": (_c.c_int, [_vp, _c.c_int32]),
-    "mclbm_batch_set_launch": (_c.c_int, [_vp, _c.c_int32, _c.c_int32]),
+    "mclbm_batch_set_launch": (_c.c_int, [_vp, _c.c_int32, _c.c_int32, _c.c_int32]),
     "mclbm_batch_step": (_c.c_int, [_vp, _c.c_int64]),
     "mclbm_batch_macro_steps": (_c.c_int64, [_vp]),
-    "mclbm_batch_autotune": (_c.c_int, [_vp, _c.c_int32, _i32p, _i32p, _dp]),
+    "mclbm_batch_autotune": (_c.c_int, [_vp, _c.c_int32, _i32p, _i32p, _i32p, _dp]),
 }
 
 _lib = None
@@ -272,20 +276,27 @@ def mclbm_check_finite(ctx):
     _check(load().mclbm_check_finite(ctx))
 
 
-def mclbm_set_launch(ctx, vec, block):
-    _check(load().mclbm_set_launch(ctx, int(vec), int(block)))
+def mclbm_set_launch(ctx, vec, block=256, kind=0):
+    _check(load().mclbm_set_launch(ctx, int(kind), int(vec), int(block)))
 
 
 def mclbm_get_launch(ctx):
-    v, b = ctypes.c_int32(), ctypes.c_int32()
-    _check(load().mclbm_get_launch(ctx, ctypes.byref(v), ctypes.byref(b)))
-    return v.value, b.value
+    """(kind, vec, block) of the context's stepper launch."""
+    k, v, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().mclbm_get_launch(ctx, ctypes.byref(k), ctypes.byref(v), ctypes.byref(b)))
+    return k.value, v.value, b.value
 
 
 def mclbm_autotune(ctx, trial_steps=5):
-    v, b, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
-    _check(load().mclbm_autotune(ctx, int(trial_steps), ctypes.byref(v), ctypes.byref(b), ctypes.byref(ms)))
-    return v.value, b.value, ms.value
+    """Returns (kind, vec, block, ms per step) of the fastest shape."""
+    k, v, b, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _check(load().mclbm_autotune(ctx, int(trial_steps), ctypes.byref(k), ctypes.byref(v), ctypes.byref(b),
+                                 ctypes.byref(ms)))
+    return k.value, v.value, b.value, ms.value
+
+
+def mclbm_device_status(ctx):
+    _check(load().mclbm_device_status(ctx))
 
 
 def mclbm_batch_create(ctxs, substeps):
@@ -305,8 +316,8 @@ def mclbm_batch_set_graph(b, enable):
     _check(load().mclbm_batch_set_graph(b, int(bool(enable))))
 
 
-def mclbm_batch_set_launch(b, vec, block):
-    _check(load().mclbm_batch_set_launch(b, int(vec), int(block)))
+def mclbm_batch_set_launch(b, vec, block=256, kind=0):
+    _check(load().mclbm_batch_set_launch(b, int(kind), int(vec), int(block)))
 
 
 def mclbm_batch_step(b, macro_steps):
@@ -318,6 +329,27 @@ def mclbm_batch_macro_steps(b):
 
 
 def mclbm_batch_autotune(b, trials=2):
-    v, blk, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
-    _check(load().mclbm_batch_autotune(b, int(trials), ctypes.byref(v), ctypes.byref(blk), ctypes.byref(ms)))
-    return v.value, blk.value, ms.value
+    """Returns (kind, vec, block, ms per macro step) of the fastest shape."""
+    k, v, blk, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _check(load().mclbm_batch_autotune(b, int(trials), ctypes.byref(k), ctypes.byref(v), ctypes.byref(blk),
+                                       ctypes.byref(ms)))
+    return k.value, v.value, blk.value, ms.value
+
+
+def mclbm_grad_required_bytes(ctx, nsteps, ckpt_every):
+    b = ctypes.c_size_t()
+    _check(load().mclbm_grad_required_bytes(ctx, int(nsteps), int(ckpt_every), ctypes.byref(b)))
+    return b.value
+
+
+def mclbm_grad(ctx, objective, nsteps, ckpt_every, d_buf, buf_bytes, M):
+    """Returns (J [M], dJ/dX [M][24]) as numpy arrays."""
+    import numpy as np
+    J = np.zeros(M)
+    G = np.zeros((M, 24))
+    _check(load().mclbm_grad(ctx, int(objective), int(nsteps), int(ckpt_every), d_buf, buf_bytes, _darr(J), _darr(G)))
+    return J, G
+
+
+def mclbm_adjoint_step(ctx, d_f, d_lambda_next, d_lambda):
+    _check(load().mclbm_adjoint_step(ctx, d_f, d_lambda_next, d_lambda))

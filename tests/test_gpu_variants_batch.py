@@ -11,6 +11,14 @@ from paper_2608_23786_gb300 import Ensemble, mclbm
 pytestmark = pytest.mark.gpu
 
 VARIANTS = {"fp64": [1, 2], "fp32": [1, 2, 4], "fp16": [2, 4, 8]}
+STAGED = [1, 2]
+
+
+def _shapes(precision, N):
+    """(kind, vec, block) of every launch shape that applies to a lattice of side N."""
+    out = [(0, v, b) for v in VARIANTS[precision] if N % v == 0 for b in (128, 256)]
+    out += [(1, v, 0) for v in STAGED if N % v == 0]
+    return out
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -30,19 +38,17 @@ def test_every_launch_shape_gives_identical_states(precision, pattern, N, steps)
     span part of a warp, a full warp, or several)."""
     X = gen.draw_params(31, 2)
     ref = None
-    for vec in VARIANTS[precision]:
-        if N % vec:
-            continue
-        for block in (128, 256):
-            ens = Ensemble(N, 2, Re=300.0, Ma=0.1, precision=precision, pattern=pattern).init(X)
-            mclbm.mclbm_set_launch(ens.ctx, vec, block)
-            ens.step(steps)
-            got = _states(ens)
-            if ref is None:
-                ref = got
-            else:
-                for a, b in zip(ref, got):
-                    assert torch.equal(a, b), (vec, block)
+    for kind, vec, block in _shapes(precision, N):
+        ens = Ensemble(N, 2, Re=300.0, Ma=0.1, precision=precision, pattern=pattern).init(X)
+        mclbm.mclbm_set_launch(ens.ctx, vec, block, kind)
+        ens.step(steps)
+        mclbm.mclbm_device_status(ens.ctx)
+        got = _states(ens)
+        if ref is None:
+            ref = got
+        else:
+            for a, b in zip(ref, got):
+                assert torch.equal(a, b), (kind, vec, block)
     # and AA equals pull for the default shape
     other = Ensemble(N, 2, Re=300.0, Ma=0.1, precision=precision,
                      pattern="pull" if pattern == "aa" else "aa").init(X).step(steps)
@@ -53,9 +59,9 @@ def test_every_launch_shape_gives_identical_states(precision, pattern, N, steps)
 def test_autotune_picks_a_supported_shape_and_restores_the_initial_state():
     ens = Ensemble(32, 4, Re=400.0, Ma=0.05, precision="fp32", seed=9).init()
     before = _states(ens)
-    vec, block, ms = mclbm.mclbm_autotune(ens.ctx, 2)
-    assert vec in VARIANTS["fp32"] and block in (128, 256) and ms > 0
-    assert mclbm.mclbm_get_launch(ens.ctx) == (vec, block)
+    kind, vec, block, ms = mclbm.mclbm_autotune(ens.ctx, 2)
+    assert (kind, vec, block) in _shapes("fp32", 32) and ms > 0
+    assert mclbm.mclbm_get_launch(ens.ctx) == (kind, vec, block)
     assert ens.steps_taken == 0
     for a, b in zip(before, _states(ens)):
         assert torch.equal(a, b)
@@ -77,7 +83,8 @@ def _levels(precision, pattern, stream, sizes=((16, 3), (32, 2), (64, 1)), seeds
 @pytest.mark.parametrize("precision,pattern", [("fp32", "pull"), ("fp32", "aa"), ("fp16", "aa"), ("fp64", "pull")])
 @pytest.mark.parametrize("substeps,graph,macro", [((1, 4, 16), True, 3), ((1, 4, 16), False, 2), ((2, 4, 8), True, 4),
                                                    ((1, 2, 4), True, 5)])
-def test_batch_equals_separate_levels(precision, pattern, substeps, graph, macro):
+@pytest.mark.parametrize("kind", [0, 1])
+def test_batch_equals_separate_levels(precision, pattern, substeps, graph, macro, kind):
     """One persistent launch per sub-step over all levels (and its graph replay) equals
     stepping each level on its own by macro * substeps[l] steps, bit for bit; includes odd
     per-level step counts (graph period of two macro steps) and a macro count that is not a
@@ -88,12 +95,15 @@ def test_batch_equals_separate_levels(precision, pattern, substeps, graph, macro
     b = mclbm.mclbm_batch_create([e.ctx for e in lv], substeps)
     try:
         mclbm.mclbm_batch_set_graph(b, graph)
+        if kind == 1:
+            mclbm.mclbm_batch_set_launch(b, 1, 0, kind=1)
         mclbm.mclbm_batch_step(b, macro)
         assert mclbm.mclbm_batch_macro_steps(b) == macro
         stream.synchronize()
         for e, r, s in zip(lv, ref, substeps):
             r.step(macro * s)
             assert e.steps_taken == macro * s
+            mclbm.mclbm_device_status(e.ctx)
             for a, c in zip(_states(e), _states(r)):
                 assert torch.equal(a, c)
     finally:
@@ -105,8 +115,8 @@ def test_batch_autotune_and_validation():
     lv = _levels("fp32", "pull", stream)
     b = mclbm.mclbm_batch_create([e.ctx for e in lv], (1, 4, 16))
     try:
-        vec, block, ms = mclbm.mclbm_batch_autotune(b, 1)
-        assert vec in VARIANTS["fp32"] and ms > 0
+        kind, vec, block, ms = mclbm.mclbm_batch_autotune(b, 1)
+        assert (kind, vec, block) in _shapes("fp32", 16) and ms > 0
         assert all(e.steps_taken == 0 for e in lv)
     finally:
         mclbm.mclbm_batch_destroy(b)
