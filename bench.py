@@ -171,8 +171,16 @@ def main():
     ap.add_argument("--precision", default=None, choices=["fp32", "fp16", "fp64"])
     ap.add_argument("--pattern", default=None, choices=["pull", "aa"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end and plain-FP64 legs (profiling)")
+    ap.add_argument("--N", type=int, default=None, help="override the lattice size (profiling of small cases)")
+    ap.add_argument("--M", type=int, default=None, help="override the number of samples (profiling of small cases)")
+    ap.add_argument("--launch", default=None, help="kind,vec,block instead of the autotuner (e.g. 0,2,128)")
     args = ap.parse_args()
     wl = dict(WORKLOAD)
+    if args.N or args.M:
+        wl["N"] = args.N or wl["N"]
+        wl["M"] = args.M or wl["M"]
+        wl["name"] = f"rtgv_{wl['N']}cube_x{wl['M']}_{wl['precision']}_{wl['pattern']}"
     if args.precision:
         wl["precision"] = args.precision
     if args.pattern:
@@ -203,7 +211,12 @@ def main():
     ens = Ensemble(wl["N"], wl["M"], Re=wl["Re"], Ma=wl["Ma"], precision=wl["precision"], pattern=wl["pattern"],
                    seed=wl["seed"], device=dev, stream=stream).init(X)
     # launch shape picked by the library's autotuner on this ensemble (restores the initial state)
-    tuned = mclbm.mclbm_autotune(ens.ctx, 3)
+    if args.launch:
+        kind, vec, block = (int(v) for v in args.launch.split(","))
+        mclbm.mclbm_set_launch(ens.ctx, vec, block, kind)
+        tuned = (kind, vec, block, None)
+    else:
+        tuned = mclbm.mclbm_autotune(ens.ctx, 3)
     mean = torch.empty((3,) + (wl["N"],) * 3, dtype=torch.float64, device=dev)
     var = torch.empty_like(mean)
     E = np.zeros(wl["M"])
@@ -264,13 +277,16 @@ def main():
         stream.synchronize()
 
     e2e_steps = max(2, args.steps // 4)
-    e2e_step()
+    if args.no_e2e:
+        e2e_steps = 0
+    else:
+        e2e_step()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_dt = time.perf_counter() - t0
+    e2e_dt = max(time.perf_counter() - t0, 1e-9)
     if world > 1:
         t = torch.tensor([e2e_dt], dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -279,17 +295,19 @@ def main():
 
     # ---- plain FP64 single-sample GPU stepper on the same GPU (the method without the ensemble
     # batching or shifted storage), 64^3 x 1
-    plain = Ensemble(wl["N"], 1, Re=wl["Re"], Ma=wl["Ma"], precision="fp64", pattern="pull", device=dev,
-                     stream=stream).init(X[:1])
-    plain.step(5)
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    plain.step(40)
-    b.record(stream)
-    torch.cuda.synchronize()
-    plain_glups = wl["N"] ** 3 * 40 / (a.elapsed_time(b) / 1e3) / 1e9
-    del plain
+    plain_glups = None
+    if not args.no_e2e:
+        plain = Ensemble(wl["N"], 1, Re=wl["Re"], Ma=wl["Ma"], precision="fp64", pattern="pull", device=dev,
+                         stream=stream).init(X[:1])
+        plain.step(5)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plain.step(40)
+        b.record(stream)
+        torch.cuda.synchronize()
+        plain_glups = wl["N"] ** 3 * 40 / (a.elapsed_time(b) / 1e3) / 1e9
+        del plain
 
     if rank != 0:
         if world > 1:
@@ -311,7 +329,8 @@ def main():
         ("f16-storage/f32" if wl["precision"] == "fp16" else "f64"), "data": "synthetic",
         "config": {"workload": wl["name"], "N": wl["N"], "M_per_gpu": wl["M"], "Re": wl["Re"], "Ma": wl["Ma"],
                    "storage": wl["precision"], "streaming": wl["pattern"], "updates_per_step": S,
-                   "reductions_per_step": ["E_m(t)", "mean/var fields"], "l2": "inputs (2.55 GB) larger than L2",
+                   "reductions_per_step": ["E_m(t)", "mean/var fields"], "l2": f"inputs ({BYTES_PER_LU[wl['precision']] * wl['M'] * wl['N'] ** 3 / 1e9:.2f} GB moved per update) "
+                         "larger than the 129 MB L2: no flush",
                    "launch": {"kind": ["direct", "staged"][tuned[0]], "vec": tuned[1], "block": tuned[2]}},
         "roofline": {"kernel": ("k_step_staged" if tuned[0] == 1 else "k_step_batch") +
                      f"<{wl['precision']},{wl['pattern']},vec={tuned[1]}" + (f",block={tuned[2]}>" if tuned[0] == 0 else ">"),
@@ -320,8 +339,9 @@ def main():
                      "traffic": traffic, "algorithmic_bytes_per_launch": bpl,
                      "avg_launch_ms": stepper_s * 1e3, "stepper_glups": wl["M"] * wl["N"] ** 3 / stepper_s / 1e9},
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": "GLUPS", "h2d_bytes_per_step": int(params_h.numel() * 8),
-                "d2h_bytes_per_step": int(E_h.numel() * 8 + mv_h.numel() * 8)},
+        "e2e": None if args.no_e2e else {"value": e2e_value, "unit": "GLUPS",
+                                         "h2d_bytes_per_step": int(params_h.numel() * 8),
+                                         "d2h_bytes_per_step": int(E_h.numel() * 8 + mv_h.numel() * 8)},
         "gpu_launches": kernels_per_step * args.steps,
         "fp64_plain_single_sample": {"value": plain_glups, "unit": "GLUPS", "N": wl["N"], "M": 1},
         "clocks": clk.summary(),

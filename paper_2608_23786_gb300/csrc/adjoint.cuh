@@ -15,6 +15,9 @@
 // so dJ = mu.df + g_s.dDs + g_h.dDh + g_eq.dfeq with
 //   g_s = -omega mu + Gam A1 k/e,   g_h = -beta mu + Gam (A1 s + 2 A2 k)/e,
 //   g_eq = -Gam (A1 s k + A2 k^2)/e^2.
+// With R1 = (mu.Dh)/hh and R2 = sh/hh (c = omega b / 2): Gam A1 = c R1, Gam A2 = -c R1 R2,
+// so every term is a product of the two ratios with components of k and s; no 1/hh^2
+// is formed (it underflows in FP32 where Dh is small).
 // Ds = A f^neq with the fixed shear projection A and Dh = (I - A) f^neq, f^neq = f - f^eq:
 //   r = A^T (g_s - g_h) + g_h,  q = g_eq - r,  dJ = (mu + r).df + q.dfeq,
 // and f^eq(rho, u) with drho = sum df, du = (dj - u drho)/rho, dj = sum c df gives
@@ -89,19 +92,20 @@ __host__ __device__ __forceinline__ void kbc_vjp(const T (&h)[Q], const T (&mu)[
     }
     const T a = T(2) / omega, b = T(2) - T(2) / omega;
     const bool active = hh > hh_guard;
-    const T gamma = active ? a - b * sh / hh : T(2);
+    const T R2 = active ? sh / hh : T(0);
+    const T R1 = active ? mk / hh : T(0);
+    const T gamma = active ? a - b * R2 : T(2);
     const T beta = T(0.5) * omega * gamma;
-    const T Gam = active ? -T(0.5) * omega * mk : T(0);
-    const T A1 = active ? -b / hh : T(0);
-    const T A2 = active ? b * sh / (hh * hh) : T(0);
+    const T c1 = T(0.5) * omega * b * R1;  // Gam A1
+    const T c2 = -c1 * R2;                 // Gam A2
     // ---- coefficient vectors (raw units)
     T gs[Q], gh[Q], geq[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const T k = n[i] - s[i];
-        gs[i] = -omega * mu[i] + Gam * A1 * k / e[i];
-        gh[i] = -beta * mu[i] + Gam * (A1 * s[i] + T(2) * A2 * k) / e[i];
-        geq[i] = -Gam * (A1 * s[i] * k + A2 * k * k) / (e[i] * e[i]);
+        gs[i] = -omega * mu[i] + c1 * k / e[i];
+        gh[i] = -beta * mu[i] + (c1 * s[i] + T(2) * c2 * k) / e[i];
+        geq[i] = -(c1 * s[i] * k + c2 * k * k) / (e[i] * e[i]);
     }
     // ---- r = A^T (gs - gh) + gh via adjoint second moments
     T d[Q];

@@ -119,11 +119,16 @@ __device__ __forceinline__ float kbc_shifted(float (&h)[Q], float omega, float a
     float heq[Q], n[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        float cu = 0.f;
+        // rho (c.u) is written c.j: the equilibrium then carries exactly the node's momentum,
+        // whatever the rounding of 1/rho (which enters only the second-order terms)
+        float cj = 0.f, cu = 0.f;
+        MCLBM_SIGNED_ADD(cj, cx(i), jx);
+        MCLBM_SIGNED_ADD(cj, cy(i), jy);
+        MCLBM_SIGNED_ADD(cj, cz(i), jz);
         MCLBM_SIGNED_ADD(cu, cx(i), ux);
         MCLBM_SIGNED_ADD(cu, cy(i), uy);
         MCLBM_SIGNED_ADD(cu, cz(i), uz);
-        heq[i] = drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
+        heq[i] = drho + 3.0f * cj + rho * (4.5f * cu * cu - 1.5f * uu);
         n[i] = h[i] - heq[i];
     }
     // second moments of f^neq (normalised): P_ab = sum w c_a c_b n

@@ -31,7 +31,7 @@ namespace mclbm {
 
 constexpr int kConsumerWarps = 8;
 constexpr int kStagedThreads = (kConsumerWarps + 1) * 32;
-constexpr long kSpinLimit = 1L << 21;  // polls of ~1 us hint each: a few seconds at most
+constexpr long kSpinLimit = 1L << 26;  // polls (each may block for a system-defined time): seconds at most
 constexpr int kTimeoutCode = -6;       // MCLBM_ERR_TIMEOUT
 
 template <class E>
@@ -66,11 +66,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     asm volatile(
         "{\n"
         " .reg .pred p;\n"
-        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         " selp.u32 %0, 1, 0, p;\n"
         "}\n"
         : "=r"(ok)
-        : "r"(bar), "r"(parity), "r"(1000)
+        : "r"(bar), "r"(parity)
         : "memory");
     return ok != 0;
 }
@@ -109,36 +109,37 @@ __device__ __forceinline__ TileCoord tile_coord(const StagedArgs<E>& a, int64_t 
     return c;
 }
 
-// Producer: copy the source rows of tile `tc` into stage buffer `buf` (element pointer).
+// Producer warp: copy the source rows of tile `tc` into stage buffer `buf`.  Lane 0 arms
+// the stage's barrier with the tile's byte count; then lane i < 19 issues the one or two
+// row-block copies of population i.
 template <class E, int PATTERN>
-__device__ __forceinline__ void issue_tile(const StagedArgs<E>& a, const TileCoord& tc, E* buf, uint32_t full_bar)
+__device__ __forceinline__ void issue_tile(const StagedArgs<E>& a, const TileCoord& tc, E* buf, uint32_t full_bar, int lane)
 {
     const LevelArgs<E>& L = a.lev[tc.l];
     const Geom g = L.g;
     const int N = g.N, ty = tc.ty;
     const int64_t row_bytes = (int64_t)N * sizeof(E);
-    const uint32_t tile_bytes = (uint32_t)(Q * ty * row_bytes);
-    mbar_arrive_expect_tx(full_bar, tile_bytes);
+    if (lane == 0) mbar_arrive_expect_tx(full_bar, (uint32_t)(Q * ty * row_bytes));
+    __syncwarp();
+    if (lane >= Q) return;
+    const int i = lane;
     const E* sample = L.src + (int64_t)tc.m * Q * g.n;
     const bool aa_odd = PATTERN == 1 && L.parity == 1;
     const bool shift = PATTERN == 0 || aa_odd;
-#pragma unroll 1
-    for (int i = 0; i < Q; ++i) {
-        const int sl = aa_odd ? opp(i) : i;
-        const int dy = shift ? cy(i) : 0, dz = shift ? cz(i) : 0;
-        const E* plane = sample + (int64_t)sl * g.n + (int64_t)g.wrap(tc.z - dz) * N * N;
-        const uint32_t dst = smem_u32(buf + (int64_t)i * ty * N);
-        const int first = tc.y0 - dy;  // first source row (may be -1 or run past N - 1)
-        if (first >= 0 && first + ty <= N) {
-            bulk_g2s(dst, plane + (int64_t)first * N, (uint32_t)(ty * row_bytes), full_bar);
-        } else if (first < 0) {  // rows N-1, 0, 1, ..., ty-2
-            bulk_g2s(dst, plane + (int64_t)(N - 1) * N, (uint32_t)row_bytes, full_bar);
-            if (ty > 1) bulk_g2s(dst + (uint32_t)row_bytes, plane, (uint32_t)((ty - 1) * row_bytes), full_bar);
-        } else {  // rows first .. N-1, then 0
-            const int head = N - first;
-            if (head > 0) bulk_g2s(dst, plane + (int64_t)first * N, (uint32_t)(head * row_bytes), full_bar);
-            bulk_g2s(dst + (uint32_t)(head * row_bytes), plane, (uint32_t)((ty - head) * row_bytes), full_bar);
-        }
+    const int sl = aa_odd ? opp(i) : i;
+    const int dy = shift ? cy(i) : 0, dz = shift ? cz(i) : 0;
+    const E* plane = sample + (int64_t)sl * g.n + (int64_t)g.wrap(tc.z - dz) * N * N;
+    const uint32_t dst = smem_u32(buf + (int64_t)i * ty * N);
+    const int first = tc.y0 - dy;  // first source row (may be -1 or run past N - 1)
+    if (first >= 0 && first + ty <= N) {
+        bulk_g2s(dst, plane + (int64_t)first * N, (uint32_t)(ty * row_bytes), full_bar);
+    } else if (first < 0) {  // rows N-1, 0, 1, ..., ty-2
+        bulk_g2s(dst, plane + (int64_t)(N - 1) * N, (uint32_t)row_bytes, full_bar);
+        if (ty > 1) bulk_g2s(dst + (uint32_t)row_bytes, plane, (uint32_t)((ty - 1) * row_bytes), full_bar);
+    } else {  // rows first .. N-1, then 0
+        const int head = N - first;
+        if (head > 0) bulk_g2s(dst, plane + (int64_t)first * N, (uint32_t)(head * row_bytes), full_bar);
+        bulk_g2s(dst + (uint32_t)(head * row_bytes), plane, (uint32_t)((ty - head) * row_bytes), full_bar);
     }
 }
 
@@ -208,27 +209,29 @@ __global__ void __launch_bounds__(kStagedThreads) k_step_staged(const StagedArgs
     __syncthreads();
     const int64_t total = a.tile_prefix[a.nlev];
     if (warp == kConsumerWarps) {
-        if (lane != 0) return;
         int64_t k = 0;
-        bool ok = true;
         for (int64_t t = blockIdx.x; t < total; t += gridDim.x, ++k) {
             const int s = (int)(k % S);
             const uint32_t ph = (uint32_t)((k / S) & 1);
-            if (!mbar_wait_bounded(smem_u32(&bars[S + s]), ph ^ 1u)) {
-                atomicExch(a.err, kTimeoutCode);
-                ok = false;
-                break;
+            int ok = 1;
+            if (lane == 0) {
+                ok = mbar_wait_bounded(smem_u32(&bars[S + s]), ph ^ 1u) ? 1 : 0;
+                if (!ok) atomicExch(a.err, kTimeoutCode);
+                if (*(volatile int*)a.err != 0) ok = 0;
             }
-            if (*(volatile int*)a.err != 0) break;
-            issue_tile<E, PATTERN>(a, tile_coord(a, t), stage0 + (int64_t)s * a.stage_elems, smem_u32(&bars[s]));
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            issue_tile<E, PATTERN>(a, tile_coord(a, t), stage0 + (int64_t)s * a.stage_elems, smem_u32(&bars[s]), lane);
+            __syncwarp();
         }
         // drain: the last phase armed on every stage must have completed
-        const int64_t armed = k;
-        for (int s = 0; s < S && s < armed; ++s) {
-            const int64_t last = armed - 1 - ((armed - 1 - s) % S);  // last iteration that used stage s
-            if (!mbar_wait_bounded(smem_u32(&bars[s]), (uint32_t)((last / S) & 1))) atomicExch(a.err, kTimeoutCode);
+        if (lane == 0) {
+            const int64_t armed = k;
+            for (int s = 0; s < S && s < armed; ++s) {
+                const int64_t last = armed - 1 - ((armed - 1 - s) % S);  // last iteration that used stage s
+                if (!mbar_wait_bounded(smem_u32(&bars[s]), (uint32_t)((last / S) & 1))) atomicExch(a.err, kTimeoutCode);
+            }
         }
-        (void)ok;
         return;
     }
     const int ctid = threadIdx.x;  // 0 .. consumers*32 - 1
