@@ -282,6 +282,22 @@ MCLBM_API int mclbm_adjoint_step(const mclbm_ctx* ctx, const double* d_f, const 
  * consumer waits are bounded and set this instead of hanging). */
 MCLBM_API int mclbm_device_status(mclbm_ctx* ctx);
 
+/* W_{1,1} on restricted fields like mclbm_w1_restricted, for callers that cannot
+ * allocate device memory: code embedded where another allocator owns the GPU's memory
+ * (a framework's caching pool or a fixed arena, whose accounting a cudaMalloc would
+ * bypass), code that must not trigger the device-wide synchronisation of cudaFree, and
+ * code running with no device memory to spare.  This call allocates nothing: its
+ * scratch is a fixed array in the library's device image, holding at most 4096 points
+ * (G <= 4096; larger G returns MCLBM_ERR_SHAPE), about 96 KiB that every GPU loading the
+ * library keeps until the process exits.  The first call on a device looks up that
+ * array's address (cudaGetSymbolAddress, with the device current), so make it before
+ * any stream capture.  Calls share the array: nothing carries over from one call to the
+ * next, but calls that overlap on the GPU race.  Same inputs, outputs and errors as
+ * mclbm_w1_restricted otherwise; synchronises cuda_stream.  The paper has no
+ * counterpart of this entry point. */
+MCLBM_API int mclbm_w1_restricted_noalloc(const double* d_a, int32_t MA, const double* d_b, int32_t MB, int32_t G,
+                                          void* cuda_stream, double* W, double* per_point);
+
 /* Scan every stored population for NaN/Inf.  Returns MCLBM_OK or
  * MCLBM_ERR_NONFINITE.  Synchronises. */
 MCLBM_API int mclbm_check_finite(mclbm_ctx* ctx);

@@ -10,6 +10,8 @@
 // support point, in FP64.  A final fixed-order reduction gives
 // W = (1/G) sum_points sum_components W1.
 #include <cfloat>
+#include <mutex>
+#include <string>
 
 #include "internal.h"
 
@@ -119,4 +121,69 @@ cudaError_t launch_w1(const double* d_a, int MA, const double* d_b, int MB, int 
     return cudaStreamSynchronize(s);
 }
 
+// ---- W1 on restricted fields without caller-provided scratch ---------------------
+// The call below uses, as its only scratch, a fixed array in the library's device
+// image: per-point distances [G][3] and the total, for at most kNoAllocMaxPoints points.
+// Every GPU that loads the library holds this array (about 96 KiB) until the process
+// exits.  Every element the call reads from it is first written by the same call, so
+// nothing needs clearing between calls; calls that overlap on the GPU (other streams,
+// other host threads) share the array and race.
+
+constexpr int kNoAllocMaxPoints = 4096;
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) double g_w1_scratch[3 * kNoAllocMaxPoints + 32];
+
+namespace {
+std::mutex g_scratch_mu;
+double* g_scratch_dev[kMaxDevices];  // device address of g_w1_scratch, per device
+
+// Device address of the scratch array on the current device.  Looked up once per device
+// (with that device current) on the first call made on it.
+cudaError_t scratch_address(double** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_dev[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_w1_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_dev[dev] = (double*)p;
+    }
+    *out = g_scratch_dev[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
 }  // namespace mclbm
+
+using namespace mclbm;
+
+extern "C" int mclbm_w1_restricted_noalloc(const double* d_a, int32_t MA, const double* d_b, int32_t MB, int32_t G,
+                                           void* cuda_stream, double* W, double* per_point)
+{
+    if (!d_a || !d_b || !W || G < 1) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    if (G > kNoAllocMaxPoints)
+        return set_error(MCLBM_ERR_SHAPE, "mclbm_w1_restricted_noalloc supports at most " +
+                                              std::to_string(kNoAllocMaxPoints) + " points (G = " + std::to_string(G) +
+                                              "); use mclbm_w1_restricted with a work buffer");
+    if (MA < 1 || MB < 1 || MA > kMaxW1Samples || MB > kMaxW1Samples)
+        return set_error(MCLBM_ERR_SHAPE, "W1 supports 1..2048 samples per ensemble");
+    double* scratch = nullptr;
+    MCLBM_CUDA(scratch_address(&scratch));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    double* pp = scratch;
+    double* total = scratch + 3 * G;
+    const int PA = pow2_at_least(MA), PB = pow2_at_least(MB);
+    const size_t smem = (size_t)(PA + PB) * sizeof(double);  // <= 32 KiB: no opt-in needed
+    k_w1_points<<<dim3(G, 3), kThreads, smem, s>>>(d_a, MA, d_b, MB, G, PA, PB, pp);
+    k_w1_total<<<1, kThreads, 0, s>>>(pp, G, total);
+    MCLBM_CUDA(cudaGetLastError());
+    MCLBM_CUDA(cudaMemcpyAsync(W, total, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (per_point) MCLBM_CUDA(cudaMemcpyAsync(per_point, pp, sizeof(double) * 3 * G, cudaMemcpyDeviceToHost, s));
+    MCLBM_CUDA(cudaStreamSynchronize(s));
+    return MCLBM_OK;
+}

@@ -78,6 +78,7 @@ _SIGNATURES = {
     "mclbm_w1_work_bytes": (_c.c_size_t, [_c.c_int32, _c.c_int32, _c.c_int32]),
     "mclbm_w1_restricted": (_c.c_int, [_vp, _c.c_int32, _vp, _c.c_int32, _c.c_int32, _vp, _c.c_size_t, _vp, _dp, _dp]),
     "mclbm_check_finite": (_c.c_int, [_ctx_p]),
+    "mclbm_w1_restricted_noalloc": (_c.c_int, [_vp, _c.c_int32, _vp, _c.c_int32, _c.c_int32, _vp, _dp, _dp]),
     "mclbm_set_launch": (_c.c_int, [_ctx_p, _c.c_int32, _c.c_int32, _c.c_int32]),
     "mclbm_get_launch": (_c.c_int, [_ctx_p, _i32p, _i32p, _i32p]),
     "mclbm_autotune": (_c.c_int, [_ctx_p, _c.c_int32, _i32p, _i32p, _i32p, _dp]),
@@ -269,6 +270,15 @@ def mclbm_w1_restricted(d_a, MA, d_b, MB, G, d_work, work_bytes, stream=0, per_p
     W = ctypes.c_double()
     _check(load().mclbm_w1_restricted(d_a, int(MA), d_b, int(MB), int(G), d_work, work_bytes, stream or None,
                                       ctypes.byref(W), _darr(per_point)))
+    return W.value
+
+
+def mclbm_w1_restricted_noalloc(d_a, MA, d_b, MB, G, stream=0, per_point=None):
+    """W_{1,1} on device restricted fields without any device allocation (scratch is a fixed
+    array inside the library, G <= 4096 points)."""
+    W = ctypes.c_double()
+    _check(load().mclbm_w1_restricted_noalloc(d_a, int(MA), d_b, int(MB), int(G), stream or None, ctypes.byref(W),
+                                              _darr(per_point)))
     return W.value
 
 
