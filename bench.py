@@ -28,12 +28,18 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(name="rtgv_64cube_x64_fp32_pull", N=64, M=64, Re=800.0, Ma=0.025, precision="fp32",
                 pattern="pull", updates_per_step=50, seed=1)
+KINDS = ["direct", "staged", "prefetch"]
+KERNEL_NAMES = ["k_step_batch", "k_step_staged", "k_step_prefetch"]
 BYTES_PER_LU = {"fp64": 2 * 19 * 8, "fp32": 2 * 19 * 4, "fp16": 2 * 19 * 2}
 STEPPER_SOURCES = ["paper_2608_23786_gb300/csrc/stepper.cu", "paper_2608_23786_gb300/csrc/collide.cuh",
-                   "paper_2608_23786_gb300/csrc/storage.cuh", "paper_2608_23786_gb300/csrc/lattice.cuh"]
-# DRAM bytes (read + write) per launch of the stepper on this workload from one ncu capture of the
-# kernel built from sources with this digest; reported as null when the sources differ.
-NCU_TRAFFIC = {"sha256": None, "bytes_per_launch": None}
+                   "paper_2608_23786_gb300/csrc/storage.cuh", "paper_2608_23786_gb300/csrc/lattice.cuh",
+                   "paper_2608_23786_gb300/csrc/stepper_impl.cuh", "paper_2608_23786_gb300/csrc/stepper_launch.cuh",
+                   "paper_2608_23786_gb300/csrc/stepper_staged.cuh", "paper_2608_23786_gb300/csrc/stepper_f32_pull.cu"]
+# DRAM bytes (read + write) per launch of the stepper on this workload, from one ncu capture of the
+# kernel built from sources with this digest and launched with this shape (kind, vec, block); the
+# capture ran 16 of the 64 samples (318.8 MB read + 272.2 MB written) and is scaled by 64/16.
+# Reported as null when the sources or the tuned shape differ.
+NCU_TRAFFIC = {"sha256": "1a76ad01e47b085b", "launch": (2, 2, 128), "bytes_per_launch": 4 * (318.848512e6 + 272.242688e6)}
 
 
 def stepper_digest():
@@ -162,6 +168,120 @@ def run_reference(args, wl):
     }))
 
 
+def run_levels(args, precision):
+    """Uneven batch of the diffusive-scaling viscosity sequence in one graph-captured launch per
+    sub-step: 64^3 x 64, 128^3 x 32, 256^3 x 8 at Re 400 / 1600 / 3200, Ma 0.025 / 0.0125 / 0.00625,
+    1 : 4 : 16 sub-steps per macro step.  One bench step = one macro step.  The statistics the
+    levels feed (shell spectra, S_2 / S_3 along axes, W1 between consecutive levels) are timed
+    once after the timed region and reported separately."""
+    import torch
+    from paper_2608_23786_gb300 import Ensemble, mclbm
+    import ensemble_inputs as gen
+    mclbm.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    pattern = "aa" if precision == "fp16" else "pull"
+    spec = [(64, 64, 400.0, 0.025, 1, 1), (128, 32, 1600.0, 0.0125, 4, 2), (256, 8, 3200.0, 0.00625, 16, 3)]
+    levels = [Ensemble(N, M, Re=Re, Ma=Ma, precision=precision, pattern=pattern, seed=seed, device=dev,
+                       stream=stream).init(gen.draw_params(seed, M)) for N, M, Re, Ma, _, seed in spec]
+    subs = [sp[4] for sp in spec]
+    b = mclbm.mclbm_batch_create([e.ctx for e in levels], subs)
+    tuned = mclbm.mclbm_batch_autotune(b, 1)
+    for _ in range(max(3, args.warmup)):
+        mclbm.mclbm_batch_step(b, 1)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        ev0.record(stream)
+        mclbm.mclbm_batch_step(b, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    sec = ev0.elapsed_time(ev1) / 1e3
+    lu = sum(M * N**3 * sub for (N, M, _, _, sub, _) in spec) * args.steps
+    for e in levels:
+        mclbm.mclbm_device_status(e.ctx)
+    bpl = BYTES_PER_LU[precision]
+    peaks, peak_kind = measured_peaks()
+    achieved = bpl * lu / sec / 1e9
+    # statistics fed by the levels
+    t0 = time.perf_counter()
+    spectra = [e.spectrum() for e in levels]
+    sfa = [e.sf_axes(3) for e in levels]
+    w1 = [levels[k].w1(levels[k + 1]) for k in range(2)]
+    stats_s = time.perf_counter() - t0
+    out = {
+        "metric": "ensemble_glups", "value": lu / sec / 1e9, "unit": "GLUPS", "n_gpus": 1, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": sec / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if precision == "fp32" else "f16-storage/f32",
+        "data": "synthetic",
+        "config": {"workload": f"levels_64x64_128x32_256x8_{precision}_{pattern}", "substeps": subs,
+                   "launch": {"kind": KINDS[tuned[0]], "vec": tuned[1], "block": tuned[2]}, "graph": True,
+                   "l2": "inputs larger than L2"},
+        "roofline": {"kernel": KERNEL_NAMES[tuned[0]], "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "peak_kind": peak_kind, "traffic": None},
+        "stats_once_s": stats_s, "w1_consecutive_levels": w1,
+        "spectrum_finite": bool(all(np.all(np.isfinite(x)) for x in spectra + sfa)),
+        "clocks": clk.summary(),
+    }
+    mclbm.mclbm_batch_destroy(b)
+    print(json.dumps(out))
+
+
+def run_large(args):
+    """512^3 x 4 samples, Re = 6400, Ma = 0.003125, FP16 shifted storage, in-place AA streaming;
+    one bench step = 10 updates.  E(k), S_p (p = 2..6) and W1 against a 256^3 x 8 level are timed
+    once after the timed region."""
+    import torch
+    from paper_2608_23786_gb300 import Ensemble, mclbm
+    import ensemble_inputs as gen
+    mclbm.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    S = 10
+    ens = Ensemble(512, 4, Re=6400.0, Ma=0.003125, precision="fp16", pattern="aa", seed=5, device=dev,
+                   stream=stream).init(gen.draw_params(5, 4))
+    tuned = mclbm.mclbm_autotune(ens.ctx, 2)
+    for _ in range(max(3, args.warmup)):
+        ens.step(S)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        ev0.record(stream)
+        ens.step(S * args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    sec = ev0.elapsed_time(ev1) / 1e3
+    mclbm.mclbm_device_status(ens.ctx)
+    lu = 4 * 512**3 * S * args.steps
+    peaks, peak_kind = measured_peaks()
+    achieved = BYTES_PER_LU["fp16"] * lu / sec / 1e9
+    ref = Ensemble(256, 8, Re=3200.0, Ma=0.00625, precision="fp16", pattern="aa", seed=6, device=dev,
+                   stream=stream).init(gen.draw_params(6, 8)).step(4 * S)
+    t0 = time.perf_counter()
+    E = ens.spectrum()
+    t1 = time.perf_counter()
+    Sp = ens.sf_axes(6)
+    t2 = time.perf_counter()
+    W = ens.w1(ref)
+    t3 = time.perf_counter()
+    out = {
+        "metric": "ensemble_glups", "value": lu / sec / 1e9, "unit": "GLUPS", "n_gpus": 1, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": sec / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16-storage/f32", "data": "synthetic",
+        "config": {"workload": "rtgv_512cube_x4_fp16_aa", "updates_per_step": S, "footprint_gb": 38 * 512**3 * 4 / 1e9,
+                   "launch": {"kind": KINDS[tuned[0]], "vec": tuned[1], "block": tuned[2]},
+                   "l2": "inputs larger than L2"},
+        "roofline": {"kernel": KERNEL_NAMES[tuned[0]], "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "peak_kind": peak_kind, "traffic": None},
+        "stats_s": {"spectrum": t1 - t0, "sf_axes_p2_6": t2 - t1, "w1_vs_256": t3 - t2}, "w1": W,
+        "stats_finite": bool(np.all(np.isfinite(E)) and np.all(np.isfinite(Sp))),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -175,7 +295,13 @@ def main():
     ap.add_argument("--N", type=int, default=None, help="override the lattice size (profiling of small cases)")
     ap.add_argument("--M", type=int, default=None, help="override the number of samples (profiling of small cases)")
     ap.add_argument("--launch", default=None, help="kind,vec,block instead of the autotuner (e.g. 0,2,128)")
+    ap.add_argument("--workload", default="ensemble64", choices=["ensemble64", "levels_fp32", "levels_fp16", "large"],
+                    help="ensemble64 (default): 64^3 x 64 FP32; levels_*: 3-level batch; large: 512^3 x 4 FP16 AA")
     args = ap.parse_args()
+    if args.workload.startswith("levels"):
+        return run_levels(args, args.workload.split("_")[1])
+    if args.workload == "large":
+        return run_large(args)
     wl = dict(WORKLOAD)
     if args.N or args.M:
         wl["N"] = args.N or wl["N"]
@@ -309,6 +435,35 @@ def main():
         plain_glups = wl["N"] ** 3 * 40 / (a.elapsed_time(b) / 1e3) / 1e9
         del plain
 
+    # ---- adjoint: gradients of E(T) w.r.t. the 24 parameters of 16 samples at 64^3 after 500 FP32
+    # steps, checkpoint every 50 (forward, segment recomputation, reverse sweep, reduction)
+    adjoint = None
+    if not args.no_e2e:
+        T4, K4, M4 = 500, 50, 16
+        ens4 = Ensemble(64, M4, Re=wl["Re"], Ma=wl["Ma"], precision="fp32", pattern="pull", device=dev,
+                        stream=stream).init(X[:M4])
+        need = mclbm.mclbm_grad_required_bytes(ens4.ctx, T4, K4)
+        gbuf = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+        gptr = (gbuf.data_ptr() + 255) // 256 * 256
+        mclbm.mclbm_grad(ens4.ctx, 0, T4, K4, gptr, need, M4)  # warm-up
+        ens4.init(X[:M4])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J4, G4 = mclbm.mclbm_grad(ens4.ctx, 0, T4, K4, gptr, need, M4)
+        grad_s = time.perf_counter() - t0
+        ph = mclbm.mclbm_grad_timing(ens4.ctx)
+        lu4 = M4 * 64**3 * T4
+        adj_bytes = 3 * 19 * 4 * lu4  # read state + read lambda + write lambda per update
+        adjoint = {"workload": "rtgv_64cube_x16_fp32_500steps_ckpt50", "objective": "E(T)",
+                   "value": lu4 / grad_s / 1e9, "unit": "GLUPS (whole gradient: forward + recompute + reverse)",
+                   "phases_ms": {"forward": ph[0], "recompute": ph[1], "reverse": ph[2], "reduction": ph[3]},
+                   "reverse_glups": lu4 / (ph[2] / 1e3) / 1e9,
+                   "reverse_achieved_gbs": adj_bytes / (ph[2] / 1e3) / 1e9,
+                   "reverse_frac_of_hbm": adj_bytes / (ph[2] / 1e3) / 1e9 / measured_peaks()[0]["hbm_gbs"],
+                   "algorithmic_bytes_per_lu_reverse": 3 * 19 * 4,
+                   "grad_finite": bool(np.all(np.isfinite(G4)))}
+        del gbuf, ens4
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -317,7 +472,9 @@ def main():
     bpl = BYTES_PER_LU[wl["precision"]] * wl["M"] * wl["N"] ** 3
     achieved = bpl / stepper_s / 1e9
     digest = stepper_digest()
-    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sha256"] == digest else None
+    traffic = (NCU_TRAFFIC["bytes_per_launch"]
+               if NCU_TRAFFIC["sha256"] == digest and tuple(tuned[:3]) == NCU_TRAFFIC["launch"] and wl["M"] == 64
+               and wl["N"] == 64 and wl["precision"] == "fp32" and wl["pattern"] == "pull" else None)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         v, desc, cores = oracle_sample(wl)
@@ -331,8 +488,8 @@ def main():
                    "storage": wl["precision"], "streaming": wl["pattern"], "updates_per_step": S,
                    "reductions_per_step": ["E_m(t)", "mean/var fields"], "l2": f"inputs ({BYTES_PER_LU[wl['precision']] * wl['M'] * wl['N'] ** 3 / 1e9:.2f} GB moved per update) "
                          "larger than the 129 MB L2: no flush",
-                   "launch": {"kind": ["direct", "staged"][tuned[0]], "vec": tuned[1], "block": tuned[2]}},
-        "roofline": {"kernel": ("k_step_staged" if tuned[0] == 1 else "k_step_batch") +
+                   "launch": {"kind": KINDS[tuned[0]], "vec": tuned[1], "block": tuned[2]}},
+        "roofline": {"kernel": KERNEL_NAMES[tuned[0]] +
                      f"<{wl['precision']},{wl['pattern']},vec={tuned[1]}" + (f",block={tuned[2]}>" if tuned[0] == 0 else ">"),
                      "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "peak_kind": peak_kind,
@@ -344,6 +501,7 @@ def main():
                                          "d2h_bytes_per_step": int(E_h.numel() * 8 + mv_h.numel() * 8)},
         "gpu_launches": kernels_per_step * args.steps,
         "fp64_plain_single_sample": {"value": plain_glups, "unit": "GLUPS", "N": wl["N"], "M": 1},
+        "adjoint": adjoint,
         "clocks": clk.summary(),
         "stepper_sources_sha256": digest,
     }

@@ -223,6 +223,8 @@ MCLBM_API int mclbm_w1_restricted(const double* d_a, int32_t MA, const double* d
  * kind 1: the staged kernel (one producer warp stages each tile's source rows in
  * shared memory with bulk asynchronous copies; eight consumer warps collide `vec`
  * in {1, 2} nodes per thread); `block` is ignored.
+ * kind 2: the direct kernel with the next run's loads issued before the current
+ * run's arithmetic (same vec and block values as kind 0).
  * Results do not depend on the shape (same arithmetic per node). */
 MCLBM_API int mclbm_set_launch(mclbm_ctx* ctx, int32_t kind, int32_t vec, int32_t block);
 MCLBM_API int mclbm_get_launch(const mclbm_ctx* ctx, int32_t* kind, int32_t* vec, int32_t* block);
@@ -271,6 +273,11 @@ MCLBM_API int mclbm_grad_required_bytes(const mclbm_ctx* ctx, int64_t nsteps, in
 MCLBM_API int mclbm_grad(mclbm_ctx* ctx, int32_t objective, int64_t nsteps, int32_t ckpt_every, void* d_buf,
                          size_t buf_bytes, double* J, double* dJdX);
 
+/* Device time (CUDA events on the context's stream) of the phases of the last
+ * mclbm_grad on this context, ms[4]: forward with checkpoints, recomputation of the
+ * segments, reverse sweep (adjoint kernels), parameter reduction.  Host array. */
+MCLBM_API int mclbm_grad_timing(const mclbm_ctx* ctx, double* ms);
+
 /* One transposed step on caller data, for checking the adjoint: given pre-collision
  * populations f^t (raw, FP64) and lambda^{t+1} = dJ/df^{t+1}, writes
  * lambda^t = dJ/df^t (all FP64 device [M][19][N][N][N], library velocity order),
@@ -297,6 +304,19 @@ MCLBM_API int mclbm_device_status(mclbm_ctx* ctx);
  * counterpart of this entry point. */
 MCLBM_API int mclbm_w1_restricted_noalloc(const double* d_a, int32_t MA, const double* d_b, int32_t MB, int32_t G,
                                           void* cuda_stream, double* W, double* per_point);
+
+/* Failure-path self-test: runs one bounded wait on a barrier that nothing completes, so
+ * the wait runs out and records MCLBM_ERR_TIMEOUT exactly as a stepper wait would; the
+ * next mclbm_device_status reports it and the next initialisation clears it.  No GPU
+ * fault, trap or hang is involved.  Enqueued only. */
+MCLBM_API int mclbm_selftest_timeout(mclbm_ctx* ctx);
+
+/* Checkpoint of the current state: configuration, step count, parameters and the
+ * stored populations, to a host file (written after synchronising the stream).
+ * mclbm_load restores it into a context of the same N, M, precision and pattern.
+ * Errors: IO (cannot open, truncated, not a checkpoint), SHAPE, CUDA. */
+MCLBM_API int mclbm_save(const mclbm_ctx* ctx, const char* path);
+MCLBM_API int mclbm_load(mclbm_ctx* ctx, const char* path);
 
 /* Scan every stored population for NaN/Inf.  Returns MCLBM_OK or
  * MCLBM_ERR_NONFINITE.  Synchronises. */

@@ -27,7 +27,7 @@ cudaError_t launch_pull_explicit(mclbm_ctx* c, const void* src, void* dst);  // 
 
 namespace {
 
-constexpr int kBlock = 256;
+constexpr int kBlock = 128;
 constexpr int kGradChunks = 64;  // blocks per sample in the parameter reduction
 
 __device__ __forceinline__ void xyz(const Geom& g, int64_t node, int& x, int& y, int& z)
@@ -305,10 +305,33 @@ cudaError_t param_grad_t(mclbm_ctx* c, const void* state0, const void* lam0, dou
 
 size_t grad_required_bytes(const mclbm_ctx* c, int64_t nsteps, int K) { return grad_layout(c, nsteps, K).total; }
 
+// CUDA events bracketing the phases of one gradient computation (for mclbm_grad_timing)
+struct PhaseEvents {
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool ok = true;
+    PhaseEvents()
+    {
+        for (auto& e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) ok = false;
+    }
+    ~PhaseEvents()
+    {
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    void mark(int k, cudaStream_t s)
+    {
+        if (ok) cudaEventRecord(ev[k], s);
+    }
+};
+
 int run_grad(mclbm_ctx* c, int objective, int64_t nsteps, int K, char* buf, size_t bytes, double* h_J, double* h_dJdX)
 {
     const GradLayout L = grad_layout(c, nsteps, K);
     if (bytes < L.total) return set_error(MCLBM_ERR_OOM, "gradient buffer needs " + std::to_string(L.total) + " bytes");
+    PhaseEvents pe;
+    double recompute_ms = 0, adjoint_ms = 0;
+    pe.mark(0, c->stream);
     // ---- forward with checkpoints every K steps
     for (int64_t t = 0; t < nsteps; ++t) {
         if (t % K == 0)
@@ -318,6 +341,7 @@ int run_grad(mclbm_ctx* c, int objective, int64_t nsteps, int K, char* buf, size
     }
     if (nsteps == 0)
         MCLBM_CUDA(cudaMemcpyAsync(buf + L.ckpt, lattice_ptr(c, c->cur), L.lattice, cudaMemcpyDeviceToDevice, c->stream));
+    pe.mark(1, c->stream);
     // ---- objective and its derivative at T
     std::vector<double> E((size_t)c->M), Z((size_t)c->M);
     MCLBM_CUDA(launch_energy(c, objective == 1, E.data(), Z.data()));
@@ -339,15 +363,27 @@ int run_grad(mclbm_ctx* c, int objective, int64_t nsteps, int K, char* buf, size
         auto state_at = [&](int64_t t) -> const char* {
             return t == t0 ? ck : buf + L.seg + (size_t)(t - t0 - 1) * L.lattice;
         };
+        pe.mark(2, c->stream);
         for (int64_t t = t0 + 1; t < t1; ++t)
             MCLBM_CUDA(launch_pull_explicit(c, state_at(t - 1), (void*)state_at(t)));
+        pe.mark(3, c->stream);
         for (int64_t t = t1 - 1; t >= t0; --t) {
             MCLBM_CUDA(adjoint_step(c, state_at(t), lam_a, lam_b));
             char* tmp = lam_a;
             lam_a = lam_b;
             lam_b = tmp;
         }
+        pe.mark(4, c->stream);
+        if (pe.ok) {
+            float a = 0, b = 0;
+            MCLBM_CUDA(cudaEventSynchronize(pe.ev[4]));
+            cudaEventElapsedTime(&a, pe.ev[2], pe.ev[3]);
+            cudaEventElapsedTime(&b, pe.ev[3], pe.ev[4]);
+            recompute_ms += a;
+            adjoint_ms += b;
+        }
     }
+    pe.mark(2, c->stream);
     // ---- dJ/dX from lambda^0 and the initial state
     double* partial = (double*)(buf + L.partial);
     double* out = (double*)(buf + L.out);
@@ -357,8 +393,18 @@ int run_grad(mclbm_ctx* c, int objective, int64_t nsteps, int K, char* buf, size
         default: e = param_grad_t<__half>(c, buf + L.ckpt, lam_a, partial, out); break;
     }
     MCLBM_CUDA(e);
+    pe.mark(5, c->stream);
     MCLBM_CUDA(cudaMemcpyAsync(h_dJdX, out, sizeof(double) * 24 * c->M, cudaMemcpyDeviceToHost, c->stream));
     MCLBM_CUDA(cudaStreamSynchronize(c->stream));
+    if (pe.ok) {
+        float f = 0, p = 0;
+        cudaEventElapsedTime(&f, pe.ev[0], pe.ev[1]);
+        cudaEventElapsedTime(&p, pe.ev[2], pe.ev[5]);
+        c->grad_ms[0] = f;
+        c->grad_ms[1] = recompute_ms;
+        c->grad_ms[2] = adjoint_ms;
+        c->grad_ms[3] = p;
+    }
     return MCLBM_OK;
 }
 
@@ -421,6 +467,13 @@ int mclbm_grad(mclbm_ctx* ctx, int32_t objective, int64_t nsteps, int32_t ckpt_e
     if (ctx->steps != 0) return set_error(MCLBM_ERR_INVALID_ARG, "mclbm_grad must directly follow an initialisation");
     if ((uintptr_t)d_buf & 255) return set_error(MCLBM_ERR_INVALID_ARG, "gradient buffer must be 256-byte aligned");
     return run_grad(ctx, objective, nsteps, ckpt_every, (char*)d_buf, buf_bytes, J, dJdX);
+}
+
+int mclbm_grad_timing(const mclbm_ctx* ctx, double* ms)
+{
+    if (!ctx || !ms) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    for (int k = 0; k < 4; ++k) ms[k] = ctx->grad_ms[k];
+    return MCLBM_OK;
 }
 
 int mclbm_adjoint_step(const mclbm_ctx* ctx, const double* d_f, const double* d_lambda_next, double* d_lambda)

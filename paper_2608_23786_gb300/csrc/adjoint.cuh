@@ -31,8 +31,12 @@
 
 namespace mclbm {
 
+// 1/x: IEEE in FP64, the fast approximate division in FP32 (a few ulp)
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+
 template <class T>
-__host__ __device__ __forceinline__ void kbc_vjp(const T (&h)[Q], const T (&mu)[Q], T omega, T hh_guard, T (&lam)[Q])
+__device__ __forceinline__ void kbc_vjp(const T (&h)[Q], const T (&mu)[Q], T omega, T hh_guard, T (&lam)[Q])
 {
     // ---- forward quantities
     T drho = 0, jx = 0, jy = 0, jz = 0;
@@ -45,9 +49,10 @@ __host__ __device__ __forceinline__ void kbc_vjp(const T (&h)[Q], const T (&mu)[
         MCLBM_SIGNED_ADD(jz, cz(i), wh);
     }
     const T rho = T(1) + drho;
-    const T ux = jx / rho, uy = jy / rho, uz = jz / rho;
+    const T irho = recip(rho);
+    const T ux = jx * irho, uy = jy * irho, uz = jz * irho;
     const T uu = ux * ux + uy * uy + uz * uz;
-    T e[Q], n[Q];
+    T e[Q], ie[Q], n[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         T cu = 0;
@@ -56,6 +61,7 @@ __host__ __device__ __forceinline__ void kbc_vjp(const T (&h)[Q], const T (&mu)[
         MCLBM_SIGNED_ADD(cu, cz(i), uz);
         const T heq = drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
         e[i] = T(1) + heq;
+        ie[i] = recip(e[i]);
         n[i] = h[i] - heq;
     }
     T pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
@@ -69,7 +75,7 @@ __host__ __device__ __forceinline__ void kbc_vjp(const T (&h)[Q], const T (&mu)[
         MCLBM_SIGNED_ADD(pxz, cx(i) * cz(i), wn);
         MCLBM_SIGNED_ADD(pyz, cy(i) * cz(i), wn);
     }
-    const T tr3 = (pxx + pyy + pzz) / T(3);
+    const T tr3 = (pxx + pyy + pzz) * (T(1) / T(3));
     T s[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -86,14 +92,16 @@ __host__ __device__ __forceinline__ void kbc_vjp(const T (&h)[Q], const T (&mu)[
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const T k = n[i] - s[i];
-        sh += weight<T>(i) * s[i] * k / e[i];
-        hh += weight<T>(i) * k * k / e[i];
+        const T wk = weight<T>(i) * k * ie[i];
+        sh += wk * s[i];
+        hh += wk * k;
         mk += mu[i] * weight<T>(i) * k;  // mu . Dh
     }
     const T a = T(2) / omega, b = T(2) - T(2) / omega;
     const bool active = hh > hh_guard;
-    const T R2 = active ? sh / hh : T(0);
-    const T R1 = active ? mk / hh : T(0);
+    const T ihh = active ? recip(hh) : T(0);
+    const T R2 = sh * ihh;
+    const T R1 = mk * ihh;
     const T gamma = active ? a - b * R2 : T(2);
     const T beta = T(0.5) * omega * gamma;
     const T c1 = T(0.5) * omega * b * R1;  // Gam A1
@@ -103,9 +111,9 @@ __host__ __device__ __forceinline__ void kbc_vjp(const T (&h)[Q], const T (&mu)[
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const T k = n[i] - s[i];
-        gs[i] = -omega * mu[i] + c1 * k / e[i];
-        gh[i] = -beta * mu[i] + (c1 * s[i] + T(2) * c2 * k) / e[i];
-        geq[i] = -(c1 * s[i] * k + c2 * k * k) / (e[i] * e[i]);
+        gs[i] = -omega * mu[i] + c1 * k * ie[i];
+        gh[i] = -beta * mu[i] + (c1 * s[i] + T(2) * c2 * k) * ie[i];
+        geq[i] = -(c1 * s[i] * k + c2 * k * k) * (ie[i] * ie[i]);
     }
     // ---- r = A^T (gs - gh) + gh via adjoint second moments
     T d[Q];
@@ -114,9 +122,10 @@ __host__ __device__ __forceinline__ void kbc_vjp(const T (&h)[Q], const T (&mu)[
     T faces = 0;
 #pragma unroll
     for (int i = 1; i < 7; ++i) faces += d[i];
-    const T Pxx = T(0.5) * (d[1] + d[2]) - faces / T(6);
-    const T Pyy = T(0.5) * (d[3] + d[4]) - faces / T(6);
-    const T Pzz = T(0.5) * (d[5] + d[6]) - faces / T(6);
+    const T f6 = faces * (T(1) / T(6));
+    const T Pxx = T(0.5) * (d[1] + d[2]) - f6;
+    const T Pyy = T(0.5) * (d[3] + d[4]) - f6;
+    const T Pzz = T(0.5) * (d[5] + d[6]) - f6;
     const T Pxy = T(0.25) * ((d[7] + d[8]) - (d[9] + d[10]));
     const T Pxz = T(0.25) * ((d[11] + d[12]) - (d[13] + d[14]));
     const T Pyz = T(0.25) * ((d[15] + d[16]) - (d[17] + d[18]));
@@ -152,14 +161,15 @@ __host__ __device__ __forceinline__ void kbc_vjp(const T (&h)[Q], const T (&mu)[
         Qy += wq * rho * gy;
         Qz += wq * rho * gz;
     }
-    Qr /= rho;
-    const T base = Qr - (Qx * ux + Qy * uy + Qz * uz) / rho;
+    Qr *= irho;
+    const T qx = Qx * irho, qy = Qy * irho, qz = Qz * irho;
+    const T base = Qr - (qx * ux + qy * uy + qz * uz);
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         T v = mu[j] + r[j] + base;
-        MCLBM_SIGNED_ADD(v, cx(j), Qx / rho);
-        MCLBM_SIGNED_ADD(v, cy(j), Qy / rho);
-        MCLBM_SIGNED_ADD(v, cz(j), Qz / rho);
+        MCLBM_SIGNED_ADD(v, cx(j), qx);
+        MCLBM_SIGNED_ADD(v, cy(j), qy);
+        MCLBM_SIGNED_ADD(v, cz(j), qz);
         lam[j] = v;
     }
 }

@@ -446,6 +446,69 @@ int mclbm_device_status(mclbm_ctx* ctx)
     return MCLBM_OK;
 }
 
+int mclbm_selftest_timeout(mclbm_ctx* ctx)
+{
+    if (!ctx) return set_error(MCLBM_ERR_INVALID_ARG, "ctx is NULL");
+    MCLBM_CUDA(launch_wait_selftest(ctx));
+    return MCLBM_OK;
+}
+
+// ---- checkpoint file: magic, version, config, units, steps, cur, params, lattice bytes
+namespace {
+constexpr uint64_t kMagic = 0x4d434c424d434b31ull;  // "MCLBMCK1"
+}
+
+int mclbm_save(const mclbm_ctx* ctx, const char* path)
+{
+    if (!ctx || !path) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    const size_t bytes = ctx->elem_bytes * Q * (size_t)ctx->n * ctx->M;
+    std::vector<char> host(bytes);
+    MCLBM_CUDA(cudaMemcpyAsync(host.data(), lattice_ptr(ctx, ctx->cur), bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    MCLBM_CUDA(cudaStreamSynchronize(ctx->stream));
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return set_error(MCLBM_ERR_IO, std::string("cannot open ") + path + " for writing");
+    const uint64_t magic = kMagic, steps = (uint64_t)ctx->steps;
+    const int32_t cur = ctx->cur;
+    bool ok = std::fwrite(&magic, sizeof magic, 1, fp) == 1 && std::fwrite(&ctx->cfg, sizeof ctx->cfg, 1, fp) == 1 &&
+              std::fwrite(&steps, sizeof steps, 1, fp) == 1 && std::fwrite(&cur, sizeof cur, 1, fp) == 1 &&
+              std::fwrite(ctx->params.data(), sizeof(double), ctx->params.size(), fp) == ctx->params.size() &&
+              std::fwrite(host.data(), 1, bytes, fp) == bytes;
+    ok = (std::fclose(fp) == 0) && ok;
+    if (!ok) return set_error(MCLBM_ERR_IO, std::string("writing ") + path + " failed");
+    return MCLBM_OK;
+}
+
+int mclbm_load(mclbm_ctx* ctx, const char* path)
+{
+    if (!ctx || !path) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return set_error(MCLBM_ERR_IO, std::string("cannot open ") + path);
+    uint64_t magic = 0, steps = 0;
+    int32_t cur = 0;
+    mclbm_config cfg;
+    std::vector<double> params(ctx->params.size());
+    const size_t bytes = ctx->elem_bytes * Q * (size_t)ctx->n * ctx->M;
+    std::vector<char> host(bytes);
+    bool ok = std::fread(&magic, sizeof magic, 1, fp) == 1 && magic == kMagic &&
+              std::fread(&cfg, sizeof cfg, 1, fp) == 1 && std::fread(&steps, sizeof steps, 1, fp) == 1 &&
+              std::fread(&cur, sizeof cur, 1, fp) == 1 &&
+              std::fread(params.data(), sizeof(double), params.size(), fp) == params.size() &&
+              std::fread(host.data(), 1, bytes, fp) == bytes;
+    std::fclose(fp);
+    if (!ok) return set_error(MCLBM_ERR_IO, std::string("reading ") + path + " failed (truncated or not a checkpoint)");
+    if (cfg.N != ctx->cfg.N || cfg.M != ctx->cfg.M || cfg.precision != ctx->cfg.precision ||
+        cfg.pattern != ctx->cfg.pattern)
+        return set_error(MCLBM_ERR_SHAPE, "checkpoint shape (N, M, precision, pattern) differs from the context");
+    if (cur != 0 && cur != 1) return set_error(MCLBM_ERR_IO, "corrupt checkpoint");
+    ctx->cur = cur;
+    ctx->steps = (int64_t)steps;
+    ctx->params = params;
+    MCLBM_CUDA(cudaMemcpyAsync(lattice_ptr(ctx, ctx->cur), host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream));
+    MCLBM_CUDA(cudaMemsetAsync(ctx->work + ctx->wl.flag, 0, 16 * sizeof(int), ctx->stream));
+    MCLBM_CUDA(cudaStreamSynchronize(ctx->stream));
+    return MCLBM_OK;
+}
+
 int mclbm_check_finite(mclbm_ctx* ctx)
 {
     if (!ctx) return set_error(MCLBM_ERR_INVALID_ARG, "ctx is NULL");

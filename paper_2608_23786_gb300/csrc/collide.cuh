@@ -114,22 +114,25 @@ __device__ __forceinline__ float kbc_shifted(float (&h)[Q], float omega, float a
     const float jy = w1 * (h[3] - h[4]) + w2 * ((h[7] - h[8]) - (h[9] - h[10]) + (h[15] - h[16]) + (h[17] - h[18]));
     const float jz = w1 * (h[5] - h[6]) + w2 * ((h[11] - h[12]) - (h[13] - h[14]) + (h[15] - h[16]) - (h[17] - h[18]));
     const float rinv = __fdividef(1.0f, rho);
-    const float ux = jx * rinv, uy = jy * rinv, uz = jz * rinv;
-    const float uu = ux * ux + uy * uy + uz * uz;
+    const float jj = jx * jx + jy * jy + jz * jz;
+    // f^eq / w - 1 = (rho - 1) + 3 c.j + (4.5 (c.j)^2 - 1.5 |j|^2) / rho: the linear term in c.j
+    // carries exactly the node's momentum whatever the rounding of 1/rho.  Opposite velocities
+    // share the even part q and differ in the sign of 3 c.j.
     float heq[Q], n[Q];
+    heq[0] = drho - 1.5f * jj * rinv;
+    n[0] = h[0] - heq[0];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        // rho (c.u) is written c.j: the equilibrium then carries exactly the node's momentum,
-        // whatever the rounding of 1/rho (which enters only the second-order terms)
-        float cj = 0.f, cu = 0.f;
+    for (int p = 0; p < 9; ++p) {
+        const int i = 2 * p + 1;
+        float cj = 0.f;
         MCLBM_SIGNED_ADD(cj, cx(i), jx);
         MCLBM_SIGNED_ADD(cj, cy(i), jy);
         MCLBM_SIGNED_ADD(cj, cz(i), jz);
-        MCLBM_SIGNED_ADD(cu, cx(i), ux);
-        MCLBM_SIGNED_ADD(cu, cy(i), uy);
-        MCLBM_SIGNED_ADD(cu, cz(i), uz);
-        heq[i] = drho + 3.0f * cj + rho * (4.5f * cu * cu - 1.5f * uu);
+        const float q = drho + rinv * (4.5f * cj * cj - 1.5f * jj);
+        heq[i] = q + 3.0f * cj;
+        heq[i + 1] = q - 3.0f * cj;
         n[i] = h[i] - heq[i];
+        n[i + 1] = h[i + 1] - heq[i + 1];
     }
     // second moments of f^neq (normalised): P_ab = sum w c_a c_b n
     const float ex = n[7] + n[8] + n[9] + n[10];      // xy edges
@@ -142,33 +145,41 @@ __device__ __forceinline__ float kbc_shifted(float (&h)[Q], float omega, float a
     const float pxz = w2 * ((n[11] + n[12]) - (n[13] + n[14]));
     const float pyz = w2 * ((n[15] + n[16]) - (n[17] + n[18]));
     const float tr3 = (pxx + pyy + pzz) * (1.0f / 3.0f);
-    // shear part normalised by w: faces D_aa/2 / (1/18) = 9 D_aa, edges s l P_ab/4 / (1/36) = 9 s l P_ab
-    float s[Q];
-    s[0] = 0.f;
-    s[1] = s[2] = 9.0f * (pxx - tr3);
-    s[3] = s[4] = 9.0f * (pyy - tr3);
-    s[5] = s[6] = 9.0f * (pzz - tr3);
-    s[7] = s[8] = 9.0f * pxy;
-    s[9] = s[10] = -9.0f * pxy;
-    s[11] = s[12] = 9.0f * pxz;
-    s[13] = s[14] = -9.0f * pxz;
-    s[15] = s[16] = 9.0f * pyz;
-    s[17] = s[18] = -9.0f * pyz;
+    // shear part normalised by w (equal on opposite velocities): faces 9 D_aa, edges 9 s l P_ab
+    float sp[9];
+    sp[0] = 9.0f * (pxx - tr3);
+    sp[1] = 9.0f * (pyy - tr3);
+    sp[2] = 9.0f * (pzz - tr3);
+    sp[3] = 9.0f * pxy;
+    sp[4] = -9.0f * pxy;
+    sp[5] = 9.0f * pxz;
+    sp[6] = -9.0f * pxz;
+    sp[7] = 9.0f * pyz;
+    sp[8] = -9.0f * pyz;
     // <Ds|Dh> and <Dh|Dh> with 1/f^eq = 1/(w (1 + heq)): sum w s k / (1 + heq)
-    float sh = 0.f, hh = 0.f;
+    float k[Q];
+    k[0] = n[0];
+    float hh = __fdividef(w0, 1.0f + heq[0]) * k[0] * k[0];
+    float sh = 0.f;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const float k = n[i] - s[i];
-        const float wr = __fdividef(weight<float>(i), 1.0f + heq[i]);
-        sh += wr * s[i] * k;
-        hh += wr * k * k;
+    for (int p = 0; p < 9; ++p) {
+        const int i = 2 * p + 1;
+        k[i] = n[i] - sp[p];
+        k[i + 1] = n[i + 1] - sp[p];
+        const float wa = __fdividef(weight<float>(i), 1.0f + heq[i]);
+        const float wb = __fdividef(weight<float>(i), 1.0f + heq[i + 1]);
+        const float ka = wa * k[i], kb = wb * k[i + 1];
+        sh += sp[p] * (ka + kb);
+        hh += ka * k[i] + kb * k[i + 1];
     }
     const float gamma = (hh <= kHHGuard) ? 2.0f : a - b * __fdividef(sh, hh);
     const float bo = 0.5f * omega * gamma;
+    h[0] = h[0] - bo * k[0];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const float k = n[i] - s[i];
-        h[i] = h[i] - omega * s[i] - bo * k;
+    for (int p = 0; p < 9; ++p) {
+        const int i = 2 * p + 1;
+        h[i] = h[i] - omega * sp[p] - bo * k[i];
+        h[i + 1] = h[i + 1] - omega * sp[p] - bo * k[i + 1];
     }
     return gamma;
 }

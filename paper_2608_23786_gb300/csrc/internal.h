@@ -50,6 +50,7 @@ struct mclbm_ctx {
     bool twiddles_ready;  // FFT twiddle table computed in the work buffer
     mclbm::LaunchConfig launch;  // stepper variant (autotuned or default)
     int num_sms;
+    double grad_ms[4];  // last mclbm_grad: forward, recompute, reverse (adjoint kernels), parameter reduction
 };
 
 namespace mclbm {
@@ -72,6 +73,7 @@ void* lattice_ptr(const mclbm_ctx* c, int which);
 cudaError_t launch_init(const mclbm_ctx* c, const double* d_params);
 cudaError_t launch_step(mclbm_ctx* c);  // one step of one context; updates cur and steps
 cudaError_t launch_step_with(mclbm_ctx* c, const LaunchConfig& cfg);
+cudaError_t launch_wait_selftest(mclbm_ctx* c);
 // one step of several levels in one launch; updates each level's cur and steps
 cudaError_t launch_levels(mclbm_ctx* const* levels, int nlev, const LaunchConfig& cfg, cudaStream_t s, int* occ);
 bool vec_supported(int precision, int vec);

@@ -125,6 +125,19 @@ __global__ void k_set_pops(E* __restrict__ lat, Geom g, int pattern, int parity,
     }
 }
 
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing arrives at,
+// gives up after `limit` polls and records MCLBM_ERR_TIMEOUT in the error word, exactly
+// as the staged stepper does when a wait runs out.  No copy is in flight.
+__global__ void k_wait_selftest(int* err, long limit)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(smem_u32(&bar), 1);
+    mbar_fence_init();
+    if (!mbar_wait_bounded(smem_u32(&bar), 0u, limit)) atomicExch(err, kTimeoutCode);
+}
+
+
 int grid_for(int64_t total)
 {
     int64_t b = (total + kBlock - 1) / kBlock;
@@ -256,7 +269,7 @@ cudaError_t launch_set_populations(mclbm_ctx* c, int sample, const double* d_in)
 bool launch_supported(int precision, const LaunchConfig& c)
 {
     if (c.kind == 1) return c.vec == 1 || c.vec == 2;
-    if (c.kind != 0 || (c.block != 128 && c.block != 256)) return false;
+    if ((c.kind != 0 && c.kind != 2) || (c.block != 128 && c.block != 256)) return false;
     return vec_supported(precision, c.vec);
 }
 
@@ -291,6 +304,12 @@ cudaError_t launch_levels(mclbm_ctx* const* lv, int nlev, const LaunchConfig& cf
 }
 
 cudaError_t launch_step(mclbm_ctx* c) { return launch_step_with(c, c->launch); }
+
+cudaError_t launch_wait_selftest(mclbm_ctx* c)
+{
+    k_wait_selftest<<<1, 32, 0, c->stream>>>((int*)(c->work + c->wl.flag) + 1, 1L << 12);
+    return cudaGetLastError();
+}
 
 // One pull step from an explicit source lattice to an explicit destination lattice (both
 // pull layout, same shape as the context's); the context's own state is not touched.

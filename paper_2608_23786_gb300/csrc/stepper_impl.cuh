@@ -313,3 +313,153 @@ __global__ void __launch_bounds__(BLOCK) k_step_batch(const BatchArgs<E> args)
 }
 
 }  // namespace mclbm
+
+namespace mclbm {
+
+// ---------------------------------------------------------------------------------
+// Prefetching variant of the direct kernel.  Each thread issues the loads of its next
+// run (one persistent-grid stride ahead) before it collides and stores the current
+// run, so a warp keeps its next 19 loads in flight during its arithmetic.  The raw
+// vector and the one boundary element of every population are kept as loaded; the
+// warp shuffles that apply the x-shift happen only when the run is consumed (a shuffle
+// of an outstanding load would wait for it).
+
+template <class E, int VEC>
+struct RawRun {
+    E w[VEC];
+    E edge;  // the element before (c_x = +1) or after (c_x = -1) the run, where no lane has it
+};
+
+// mode: 0 pull (slot i, rows shifted by -c_i), 1 AA even (slot i, own rows), 2 AA odd
+// (slot opp(i), rows shifted by -c_i)
+struct RunLoc {
+    int l, m, x0, y, z, mode;
+    int64_t node;
+};
+
+template <class E, int VEC, int CXI>
+__device__ __forceinline__ void issue_row(const E* row, int x0, int N, int lane, RawRun<E, VEC>& r)
+{
+    vload<E, VEC>(row + x0, r.w);
+    if constexpr (CXI > 0) {
+        if (lane == 0 || x0 == 0) r.edge = sload<E>(row + ((x0 - 1) & (N - 1)));
+    } else if constexpr (CXI < 0) {
+        if (lane == 31 || x0 + VEC == N) r.edge = sload<E>(row + ((x0 + VEC) & (N - 1)));
+    }
+}
+
+template <class E, int VEC, int CXI>
+__device__ __forceinline__ void finish_row(const RawRun<E, VEC>& r, int x0, int N, int lane,
+                                           typename Storage<E>::compute (&v)[VEC])
+{
+    if constexpr (CXI == 0) {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) v[k] = to_c<E>(r.w[k]);
+    } else if constexpr (CXI > 0) {
+        E prev = __shfl_up_sync(0xffffffffu, r.w[VEC - 1], 1);
+        if (lane == 0 || x0 == 0) prev = r.edge;
+        v[0] = to_c<E>(prev);
+#pragma unroll
+        for (int k = 1; k < VEC; ++k) v[k] = to_c<E>(r.w[k - 1]);
+    } else {
+        E next = __shfl_down_sync(0xffffffffu, r.w[0], 1);
+        if (lane == 31 || x0 + VEC == N) next = r.edge;
+#pragma unroll
+        for (int k = 0; k < VEC - 1; ++k) v[k] = to_c<E>(r.w[k + 1]);
+        v[VEC - 1] = to_c<E>(next);
+    }
+}
+
+template <class E, int VEC, int I = 0>
+__device__ __forceinline__ void issue_all(const E* base, const Geom& g, const RunLoc& p, int lane,
+                                          RawRun<E, VEC> (&raw)[Q])
+{
+    if constexpr (I < Q) {
+        const bool shift = p.mode != 1;
+        const int slot = p.mode == 2 ? Dir<I>::o : I;
+        const int ry = shift ? g.wrap(p.y - Dir<I>::y) : p.y;
+        const int rz = shift ? g.wrap(p.z - Dir<I>::z) : p.z;
+        const E* row = base + (int64_t)slot * g.n + g.node(0, ry, rz);
+        if (shift)
+            issue_row<E, VEC, Dir<I>::x>(row, p.x0, g.N, lane, raw[I]);
+        else
+            issue_row<E, VEC, 0>(row, p.x0, g.N, lane, raw[I]);
+        issue_all<E, VEC, I + 1>(base, g, p, lane, raw);
+    }
+}
+
+template <class E, int VEC, int I = 0>
+__device__ __forceinline__ void finish_all(const Geom& g, const RunLoc& p, int lane, const RawRun<E, VEC> (&raw)[Q],
+                                           typename Storage<E>::compute (&v)[Q][VEC])
+{
+    if constexpr (I < Q) {
+        if (p.mode != 1)
+            finish_row<E, VEC, Dir<I>::x>(raw[I], p.x0, g.N, lane, v[I]);
+        else
+            finish_row<E, VEC, 0>(raw[I], p.x0, g.N, lane, v[I]);
+        finish_all<E, VEC, I + 1>(g, p, lane, raw, v);
+    }
+}
+
+template <class E, int VEC>
+__device__ __forceinline__ RunLoc locate(const BatchArgs<E>& args, int64_t t, int pattern)
+{
+    RunLoc p;
+    int l = 0;
+#pragma unroll 1
+    while (l + 1 < args.nlev && t >= args.prefix[l + 1]) ++l;
+    const Geom& g = args.lev[l].g;
+    const int64_t first = (t - args.prefix[l]) * VEC;
+    p.l = l;
+    p.m = (int)(first >> (3 * g.logN));
+    p.node = first & (g.n - 1);
+    p.x0 = (int)(p.node & (g.N - 1));
+    p.y = (int)((p.node >> g.logN) & (g.N - 1));
+    p.z = (int)(p.node >> (2 * g.logN));
+    p.mode = pattern == 0 ? 0 : (args.lev[l].parity == 0 ? 1 : 2);
+    return p;
+}
+
+template <class E, int VEC, int PATTERN, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_step_prefetch(const BatchArgs<E> args)
+{
+    using C = typename Storage<E>::compute;
+    const int lane = threadIdx.x & 31;
+    const int64_t total = args.prefix[args.nlev];
+    const int64_t stride = (int64_t)gridDim.x * BLOCK;
+    int64_t t = blockIdx.x * (int64_t)BLOCK + threadIdx.x;
+    if (t >= total) return;  // whole warps: totals and strides are multiples of 32
+    RunLoc cur = locate<E, VEC>(args, t, PATTERN);
+    RawRun<E, VEC> raw[Q];
+    {
+        const LevelArgs<E>& L = args.lev[cur.l];
+        issue_all<E, VEC>(L.src + (int64_t)cur.m * Q * L.g.n, L.g, cur, lane, raw);
+    }
+    while (true) {
+        const LevelArgs<E>& L = args.lev[cur.l];
+        const Geom g = L.g;
+        C v[Q][VEC];
+        finish_all<E, VEC>(g, cur, lane, raw, v);
+        const int64_t tn = t + stride;
+        const bool more = tn < total;
+        RunLoc nxt = cur;
+        if (more) {
+            nxt = locate<E, VEC>(args, tn, PATTERN);
+            const LevelArgs<E>& Ln = args.lev[nxt.l];
+            issue_all<E, VEC>(Ln.src + (int64_t)nxt.m * Q * Ln.g.n, Ln.g, nxt, lane, raw);
+        }
+        collide_run<E, VEC>(v, L);
+        E* base = L.dst + (int64_t)cur.m * Q * g.n;
+        if (cur.mode == 0)
+            scatter_all<E, VEC, 0>(base, g, cur.x0, cur.y, cur.z, lane, v);
+        else if (cur.mode == 1)
+            store_own_opp<E, VEC>(base, g, cur.node, v);
+        else
+            scatter_all<E, VEC, 1>(base, g, cur.x0, cur.y, cur.z, lane, v);
+        if (!more) break;
+        t = tn;
+        cur = nxt;
+    }
+}
+
+}  // namespace mclbm

@@ -29,6 +29,27 @@ cudaError_t launch_variant(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, 
     return cudaGetLastError();
 }
 
+template <class E, int VEC, int PATTERN, int BLOCK>
+cudaError_t launch_prefetch_variant(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, int* occupancy_out)
+{
+    auto kern = k_step_prefetch<E, VEC, PATTERN, BLOCK>;
+    static int occ = -1;
+    if (occ < 0) {
+        int o = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, BLOCK, 0);
+        if (e != cudaSuccess) return e;
+        occ = o > 0 ? o : 1;
+    }
+    if (occupancy_out) *occupancy_out = occ;
+    const int64_t total = a.prefix[a.nlev];
+    int64_t blocks = (total + BLOCK - 1) / BLOCK;
+    const int64_t cap = (int64_t)grid_cap * occ;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, BLOCK, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <class E, int PATTERN, int... VECS>
 cudaError_t launch_vec_block(const BatchArgs<E>& a, const LaunchConfig& cfg, int grid_cap, cudaStream_t s, int* occ)
 {
@@ -38,7 +59,14 @@ cudaError_t launch_vec_block(const BatchArgs<E>& a, const LaunchConfig& cfg, int
         constexpr int V = decltype(vec_tag)::value;
         if (found || cfg.vec != V) return;
         found = true;
-        if (cfg.block == 128)
+        if (cfg.kind == 2) {
+            if (cfg.block == 128)
+                e = launch_prefetch_variant<E, V, PATTERN, 128>(a, grid_cap, s, occ);
+            else if (cfg.block == 256)
+                e = launch_prefetch_variant<E, V, PATTERN, 256>(a, grid_cap, s, occ);
+            else
+                e = cudaErrorInvalidConfiguration;
+        } else if (cfg.block == 128)
             e = launch_variant<E, V, PATTERN, 128>(a, grid_cap, s, occ);
         else if (cfg.block == 256)
             e = launch_variant<E, V, PATTERN, 256>(a, grid_cap, s, occ);

@@ -86,6 +86,10 @@ _SIGNATURES = {
     "mclbm_grad_required_bytes": (_c.c_int, [_ctx_p, _c.c_int64, _c.c_int32, _size_p]),
     "mclbm_grad": (_c.c_int, [_ctx_p, _c.c_int32, _c.c_int64, _c.c_int32, _vp, _c.c_size_t, _dp, _dp]),
     "mclbm_adjoint_step": (_c.c_int, [_ctx_p, _vp, _vp, _vp]),
+    "mclbm_grad_timing": (_c.c_int, [_ctx_p, _dp]),
+    "mclbm_selftest_timeout": (_c.c_int, [_ctx_p]),
+    "mclbm_save": (_c.c_int, [_ctx_p, _c.c_char_p]),
+    "mclbm_load": (_c.c_int, [_ctx_p, _c.c_char_p]),
     "mclbm_batch_create": (_c.c_int, [_c.POINTER(_ctx_p), _c.c_int32, _i32p, _c.POINTER(_vp)]),
     "mclbm_batch_destroy": (None, [_vp]),
     "mclbm_batch_set_graph": (_c.c_int, [_vp, _c.c_int32]),
@@ -363,3 +367,23 @@ def mclbm_grad(ctx, objective, nsteps, ckpt_every, d_buf, buf_bytes, M):
 
 def mclbm_adjoint_step(ctx, d_f, d_lambda_next, d_lambda):
     _check(load().mclbm_adjoint_step(ctx, d_f, d_lambda_next, d_lambda))
+
+
+def mclbm_grad_timing(ctx):
+    """ms of the phases of the last mclbm_grad: forward, recompute, reverse, parameter reduction."""
+    import numpy as np
+    out = np.zeros(4)
+    _check(load().mclbm_grad_timing(ctx, _darr(out)))
+    return out
+
+
+def mclbm_selftest_timeout(ctx):
+    _check(load().mclbm_selftest_timeout(ctx))
+
+
+def mclbm_save(ctx, path):
+    _check(load().mclbm_save(ctx, os.fsencode(path)))
+
+
+def mclbm_load(ctx, path):
+    _check(load().mclbm_load(ctx, os.fsencode(path)))

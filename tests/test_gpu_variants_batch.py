@@ -16,7 +16,7 @@ STAGED = [1, 2]
 
 def _shapes(precision, N):
     """(kind, vec, block) of every launch shape that applies to a lattice of side N."""
-    out = [(0, v, b) for v in VARIANTS[precision] if N % v == 0 for b in (128, 256)]
+    out = [(k, v, b) for k in (0, 2) for v in VARIANTS[precision] if N % v == 0 for b in (128, 256)]
     out += [(1, v, 0) for v in STAGED if N % v == 0]
     return out
 
@@ -83,7 +83,7 @@ def _levels(precision, pattern, stream, sizes=((16, 3), (32, 2), (64, 1)), seeds
 @pytest.mark.parametrize("precision,pattern", [("fp32", "pull"), ("fp32", "aa"), ("fp16", "aa"), ("fp64", "pull")])
 @pytest.mark.parametrize("substeps,graph,macro", [((1, 4, 16), True, 3), ((1, 4, 16), False, 2), ((2, 4, 8), True, 4),
                                                    ((1, 2, 4), True, 5)])
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 2])
 def test_batch_equals_separate_levels(precision, pattern, substeps, graph, macro, kind):
     """One persistent launch per sub-step over all levels (and its graph replay) equals
     stepping each level on its own by macro * substeps[l] steps, bit for bit; includes odd
@@ -97,6 +97,8 @@ def test_batch_equals_separate_levels(precision, pattern, substeps, graph, macro
         mclbm.mclbm_batch_set_graph(b, graph)
         if kind == 1:
             mclbm.mclbm_batch_set_launch(b, 1, 0, kind=1)
+        elif kind == 2:
+            mclbm.mclbm_batch_set_launch(b, 2, 128, kind=2)
         mclbm.mclbm_batch_step(b, macro)
         assert mclbm.mclbm_batch_macro_steps(b) == macro
         stream.synchronize()
