@@ -28,18 +28,19 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(name="rtgv_64cube_x64_fp32_pull", N=64, M=64, Re=800.0, Ma=0.025, precision="fp32",
                 pattern="pull", updates_per_step=50, seed=1)
-KINDS = ["direct", "staged", "prefetch"]
-KERNEL_NAMES = ["k_step_batch", "k_step_staged", "k_step_prefetch"]
+KINDS = ["direct", "staged", "prefetch", "prefetch_packed", "async_ring2", "async_ring3"]
+KERNEL_NAMES = ["k_step_batch", "k_step_staged", "k_step_prefetch", "k_step_prefetch", "k_step_async", "k_step_async"]
 BYTES_PER_LU = {"fp64": 2 * 19 * 8, "fp32": 2 * 19 * 4, "fp16": 2 * 19 * 2}
 STEPPER_SOURCES = ["paper_2608_23786_gb300/csrc/stepper.cu", "paper_2608_23786_gb300/csrc/collide.cuh",
                    "paper_2608_23786_gb300/csrc/storage.cuh", "paper_2608_23786_gb300/csrc/lattice.cuh",
                    "paper_2608_23786_gb300/csrc/stepper_impl.cuh", "paper_2608_23786_gb300/csrc/stepper_launch.cuh",
-                   "paper_2608_23786_gb300/csrc/stepper_staged.cuh", "paper_2608_23786_gb300/csrc/stepper_f32_pull.cu"]
+                   "paper_2608_23786_gb300/csrc/stepper_staged.cuh", "paper_2608_23786_gb300/csrc/stepper_async.cuh",
+                   "paper_2608_23786_gb300/csrc/stepper_f32_pull.cu"]
 # DRAM bytes (read + write) per launch of the stepper on this workload, from one ncu capture of the
 # kernel built from sources with this digest and launched with this shape (kind, vec, block); the
-# capture ran 16 of the 64 samples (318.8 MB read + 264.9 MB written) and is scaled by 64/16.
-# Reported as null when the sources or the tuned shape differ.
-NCU_TRAFFIC = {"sha256": "ce7bcd9f5fff619b", "launch": (2, 4, 128), "bytes_per_launch": 4 * (318.829568e6 + 264.895488e6)}
+# capture ran 16 of the 64 samples (318.8 MB read + 267.8 MB written) and is scaled by 64/16.
+# Reported as null when the sources or the launch shape differ.
+NCU_TRAFFIC = {"sha256": "40ff16d37c8f7eb7", "launch": (3, 2, 128), "bytes_per_launch": 4 * (318.807552e6 + 267.839488e6)}
 
 
 def stepper_digest():
@@ -294,7 +295,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end and plain-FP64 legs (profiling)")
     ap.add_argument("--N", type=int, default=None, help="override the lattice size (profiling of small cases)")
     ap.add_argument("--M", type=int, default=None, help="override the number of samples (profiling of small cases)")
-    ap.add_argument("--launch", default=None, help="kind,vec,block instead of the autotuner (e.g. 0,2,128)")
+    ap.add_argument("--launch", default=None, help="kind,vec,block instead of the library default (e.g. 0,2,128)")
+    ap.add_argument("--autotune", action="store_true", help="let the library's autotuner pick the launch shape")
     ap.add_argument("--workload", default="ensemble64", choices=["ensemble64", "levels_fp32", "levels_fp16", "large"],
                     help="ensemble64 (default): 64^3 x 64 FP32; levels_*: 3-level batch; large: 512^3 x 4 FP16 AA")
     args = ap.parse_args()
@@ -336,13 +338,16 @@ def main():
     X = gen.draw_params(wl["seed"], wl["M"], first_sample=rank * wl["M"])
     ens = Ensemble(wl["N"], wl["M"], Re=wl["Re"], Ma=wl["Ma"], precision=wl["precision"], pattern=wl["pattern"],
                    seed=wl["seed"], device=dev, stream=stream).init(X)
-    # launch shape picked by the library's autotuner on this ensemble (restores the initial state)
+    # launch shape: the library default, an explicit one, or the autotuner's pick on this ensemble
+    # (the autotuner restores the initial state)
     if args.launch:
         kind, vec, block = (int(v) for v in args.launch.split(","))
         mclbm.mclbm_set_launch(ens.ctx, vec, block, kind)
         tuned = (kind, vec, block, None)
-    else:
+    elif args.autotune:
         tuned = mclbm.mclbm_autotune(ens.ctx, 3)
+    else:
+        tuned = tuple(mclbm.mclbm_get_launch(ens.ctx)) + (None,)
     mean = torch.empty((3,) + (wl["N"],) * 3, dtype=torch.float64, device=dev)
     var = torch.empty_like(mean)
     E = np.zeros(wl["M"])
@@ -488,9 +493,10 @@ def main():
                    "storage": wl["precision"], "streaming": wl["pattern"], "updates_per_step": S,
                    "reductions_per_step": ["E_m(t)", "mean/var fields"], "l2": f"inputs ({BYTES_PER_LU[wl['precision']] * wl['M'] * wl['N'] ** 3 / 1e9:.2f} GB moved per update) "
                          "larger than the 129 MB L2: no flush",
-                   "launch": {"kind": KINDS[tuned[0]], "vec": tuned[1], "block": tuned[2]}},
+                   "launch": {"kind": KINDS[tuned[0]], "vec": tuned[1], "block": tuned[2],
+                              "chosen_by": "explicit" if args.launch else ("autotuner" if args.autotune else "default")}},
         "roofline": {"kernel": KERNEL_NAMES[tuned[0]] +
-                     f"<{wl['precision']},{wl['pattern']},vec={tuned[1]}" + (f",block={tuned[2]}>" if tuned[0] == 0 else ">"),
+                     f"<{wl['precision']},{wl['pattern']},vec={tuned[1]},block={tuned[2]}>",
                      "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "peak_kind": peak_kind,
                      "traffic": traffic, "algorithmic_bytes_per_launch": bpl,

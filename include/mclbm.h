@@ -225,7 +225,10 @@ MCLBM_API int mclbm_w1_restricted(const double* d_a, int32_t MA, const double* d
  * in {1, 2} nodes per thread); `block` is ignored.
  * kind 2: the direct kernel with the next run's loads issued before the current
  * run's arithmetic (same vec and block values as kind 0).
- * Results do not depend on the shape (same arithmetic per node). */
+ * kind 3: kind 2 with the FP32 collision of two nodes at a time in the packed FP32
+ * instructions of sm_100 and later (FP32 and FP16 storage, even vec).
+ * Results do not depend on the shape (same arithmetic per node, every operation
+ * rounded once in the same order). */
 MCLBM_API int mclbm_set_launch(mclbm_ctx* ctx, int32_t kind, int32_t vec, int32_t block);
 MCLBM_API int mclbm_get_launch(const mclbm_ctx* ctx, int32_t* kind, int32_t* vec, int32_t* block);
 

@@ -31,9 +31,10 @@
 
 namespace mclbm {
 
-// 1/x: IEEE in FP64, the fast approximate division in FP32 (a few ulp)
+// 1/x: IEEE in FP64, the hardware reciprocal approximation in FP32 (one ulp; the arguments are
+// 1 + O(Ma) densities and equilibria, and <Dh|Dh> above its guard)
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
-__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float recip(float x) { return lanes::rcp_approx(x); }
 
 template <class T>
 __device__ __forceinline__ void kbc_vjp(const T (&h)[Q], const T (&mu)[Q], T omega, T hh_guard, T (&lam)[Q])

@@ -107,11 +107,15 @@ int validate(const mclbm_config* cfg, mclbm_units* u)
 
 }  // namespace
 
-LaunchConfig default_launch(int precision)
+// Default launch shape: the fastest measured on a GB300 for the 64^3 x 64 and 128^3 x 32
+// ensembles (the autotuner may pick another).  FP32: packed collision, 2 nodes per thread;
+// FP16 pull: shared-memory prefetch ring, 8 nodes per thread; FP16 AA: packed collision,
+// 4 nodes per thread; FP64 (bound by the FP64 units): the direct kernel.
+LaunchConfig default_launch(int precision, int pattern)
 {
-    if (precision == MCLBM_FP64) return LaunchConfig{1, 256};
-    if (precision == MCLBM_FP32) return LaunchConfig{2, 256};
-    return LaunchConfig{4, 256};
+    if (precision == MCLBM_FP64) return LaunchConfig{2, 128, 0};
+    if (precision == MCLBM_FP32) return LaunchConfig{2, 128, 3};
+    return pattern == MCLBM_PULL ? LaunchConfig{8, 128, 4} : LaunchConfig{4, 128, 3};
 }
 
 int set_error(int code, const std::string& msg)
@@ -248,7 +252,7 @@ int mclbm_create(const mclbm_config* cfg, void* d_pop, size_t pop_bytes, void* d
     c->params.assign((size_t)cfg->M * 24, 0.0);
     c->elem_bytes = elem_bytes_of(cfg->precision);
     c->twiddles_ready = false;
-    c->launch = default_launch(cfg->precision);
+    c->launch = default_launch(cfg->precision, cfg->pattern);
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
     c->num_sms = sms;

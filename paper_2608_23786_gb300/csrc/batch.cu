@@ -147,10 +147,11 @@ std::vector<LaunchConfig> candidates(int precision, int N)
         vecs = kVecF16;
         nv = sizeof(kVecF16) / sizeof(int);
     }
-    for (int kind : {0, 2})
+    for (int kind : {0, 2, 3, 4, 5})
         for (int i = 0; i < nv; ++i)
             for (int blk : kBlocks)
-                if (N % vecs[i] == 0) v.push_back(LaunchConfig{vecs[i], blk, kind});
+                if (N % vecs[i] == 0 && launch_supported(precision, LaunchConfig{vecs[i], blk, kind}))
+                    v.push_back(LaunchConfig{vecs[i], blk, kind});
     for (int vs : kVecStaged)
         if (N % vs == 0) v.push_back(LaunchConfig{vs, 0, 1});
     return v;

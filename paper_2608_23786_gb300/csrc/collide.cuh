@@ -95,91 +95,220 @@ __host__ __device__ __forceinline__ T kbc_raw(T (&f)[Q], T omega)
 // this the higher-order non-equilibrium is at rounding level).
 constexpr float kHHGuard = 1e-30f;
 
-// KBC on normalised deviations h_i = f_i / w_i - 1 (in place), FP32.  a = 2/omega and
-// b = 2 - 2/omega are passed in (computed once on the host); the reciprocals 1/rho and
-// w_i / (1 + heq_i) and the quotient sh/hh use the fast approximate division (a few ulp,
-// below the FP32 rounding already present in the sums).
-__device__ __forceinline__ float kbc_shifted(float (&h)[Q], float omega, float a, float b)
+// Lane arithmetic of the FP32 shifted collision.  A lane type V is float (one node) or
+// float2 (two nodes in the packed FP32 pipe of sm_100+: one add, multiply or fma
+// instruction serves both).  Every operation rounds once to nearest, with no contraction
+// left to the compiler, so a node gets bit-identical results in either lane type.
+namespace lanes {
+template <class V>
+__device__ __forceinline__ V bc(float s);
+template <>
+__device__ __forceinline__ float bc<float>(float s) { return s; }
+template <>
+__device__ __forceinline__ float2 bc<float2>(float s) { return make_float2(s, s); }
+// Both lane types are written in PTX with the rounding mode spelled out: an add or multiply
+// with an explicit rounding modifier is never fused with a neighbour into an fma, and no
+// compiler pass above the assembler rewrites them, which keeps the two lane types
+// bit-identical.
+__device__ __forceinline__ float add(float a, float b)
 {
-    constexpr float w0 = 1.0f / 3.0f, w1 = 1.0f / 18.0f, w2 = 1.0f / 36.0f;
-    // density deviation and momentum: sum w h, sum w c h
-    float s0 = h[0], s1 = 0.f, s2 = 0.f;
+    float d;
+    asm("add.rn.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+__device__ __forceinline__ float mul(float a, float b)
+{
+    float d;
+    asm("mul.rn.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+__device__ __forceinline__ float fma(float a, float b, float c)
+{
+    float d;
+    asm("fma.rn.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+// a - b = a + (-1) b, rounded once (the same form as the packed subtraction)
+__device__ __forceinline__ float sub(float a, float b) { return fma(b, -1.f, a); }
+__device__ __forceinline__ float2 add(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 pa, pb, pd;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "add.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 mul(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 pa, pb, pd;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "mul.rn.f32x2 pd, pa, pb;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 pa, pb, pc, pd;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "mov.b64 pc, {%6, %7};\n\tfma.rn.f32x2 pd, pa, pb, pc;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+// a - b = a + (-1) b, rounded once: the same value as the scalar subtraction
+__device__ __forceinline__ float2 sub(float2 a, float2 b) { return fma(b, make_float2(-1.f, -1.f), a); }
+// Hardware reciprocal approximation (rcp.approx, within one ulp; subnormals flushed).  The
+// arguments here are 1 + O(Ma) densities and equilibria, and <Dh|Dh> above its guard.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+// lane-wise scalar function
+template <class F>
+__device__ __forceinline__ float map(float a, F f) { return f(a); }
+template <class F>
+__device__ __forceinline__ float2 map(float2 a, F f) { return make_float2(f(a.x), f(a.y)); }
+template <class F>
+__device__ __forceinline__ float map(float a, float b, F f) { return f(a, b); }
+template <class F>
+__device__ __forceinline__ float2 map(float2 a, float2 b, F f) { return make_float2(f(a.x, b.x), f(a.y, b.y)); }
+}  // namespace lanes
+
+// The shifted collision hard-codes the library velocity order: odd i and i + 1 are
+// opposite, the first non-zero component of an odd velocity is +1, and the pairs run
+// +-x, +-y, +-z, xy(++), xy(+-), xz(++), xz(+-), yz(++), yz(+-).
+constexpr bool shifted_order_holds()
+{
+    for (int i = 1; i < Q; i += 2) {
+        if (opp(i) != i + 1) return false;
+        const int first = cx(i) != 0 ? cx(i) : (cy(i) != 0 ? cy(i) : cz(i));
+        if (first != 1) return false;
+    }
+    return cx(1) == 1 && cy(3) == 1 && cz(5) == 1 && cx(7) == 1 && cy(7) == 1 && cx(9) == 1 && cy(9) == -1 &&
+           cx(11) == 1 && cz(11) == 1 && cx(13) == 1 && cz(13) == -1 && cy(15) == 1 && cz(15) == 1 &&
+           cy(17) == 1 && cz(17) == -1;
+}
+static_assert(shifted_order_holds(), "kbc_shifted assumes the library velocity order");
+
+// c_i . j for odd i (compile-time constant after unrolling)
+template <class V>
+__device__ __forceinline__ V c_dot(int i, V jx, V jy, V jz)
+{
+    using namespace lanes;
+    if (cx(i) == 0 && cy(i) == 0) return jz;
+    if (cx(i) == 0) return cz(i) == 0 ? jy : (cz(i) > 0 ? add(jy, jz) : sub(jy, jz));
+    if (cy(i) != 0) return cy(i) > 0 ? add(jx, jy) : sub(jx, jy);
+    if (cz(i) != 0) return cz(i) > 0 ? add(jx, jz) : sub(jx, jz);
+    return jx;
+}
+
+// KBC on normalised deviations h_i = f_i / w_i - 1 (in place), FP32, one node (V = float)
+// or two (V = float2).  a = 2/omega and b = 2 - 2/omega are passed in (computed once on the
+// host); the reciprocals 1/rho, 1/(1 + heq_i) and 1/hh are the hardware approximation (one
+// ulp, below the FP32 rounding already present in the sums).
+template <class V>
+__device__ __forceinline__ V kbc_shifted(V (&h)[Q], float omega, float a, float b)
+{
+    using namespace lanes;
+    const V one = bc<V>(1.f), W0 = bc<V>(1.0f / 3.0f), W1 = bc<V>(1.0f / 18.0f), W2 = bc<V>(1.0f / 36.0f);
+    const auto frcp = [](float x) { return rcp_approx(x); };
+    // density deviation and momentum: sum w h, sum w c h (d_p: difference of pair p)
+    const V s1 = add(add(add(h[1], h[2]), add(h[3], h[4])), add(h[5], h[6]));
+    const V s2 = add(add(add(add(h[7], h[8]), add(h[9], h[10])), add(add(h[11], h[12]), add(h[13], h[14]))),
+                     add(add(h[15], h[16]), add(h[17], h[18])));
+    const V drho = fma(W0, h[0], fma(W1, s1, mul(W2, s2)));
+    const V rho = add(one, drho);
+    V d[9];
 #pragma unroll
-    for (int i = 1; i < 7; ++i) s1 += h[i];
-#pragma unroll
-    for (int i = 7; i < Q; ++i) s2 += h[i];
-    const float drho = w0 * s0 + w1 * s1 + w2 * s2;
-    const float rho = 1.0f + drho;
-    const float jx = w1 * (h[1] - h[2]) + w2 * ((h[7] - h[8]) + (h[9] - h[10]) + (h[11] - h[12]) + (h[13] - h[14]));
-    const float jy = w1 * (h[3] - h[4]) + w2 * ((h[7] - h[8]) - (h[9] - h[10]) + (h[15] - h[16]) + (h[17] - h[18]));
-    const float jz = w1 * (h[5] - h[6]) + w2 * ((h[11] - h[12]) - (h[13] - h[14]) + (h[15] - h[16]) - (h[17] - h[18]));
-    const float rinv = __fdividef(1.0f, rho);
-    const float jj = jx * jx + jy * jy + jz * jz;
+    for (int p = 0; p < 9; ++p) d[p] = sub(h[2 * p + 1], h[2 * p + 2]);
+    const V jx = fma(W1, d[0], mul(W2, add(add(d[3], d[4]), add(d[5], d[6]))));
+    const V jy = fma(W1, d[1], mul(W2, add(sub(d[3], d[4]), add(d[7], d[8]))));
+    const V jz = fma(W1, d[2], mul(W2, add(sub(d[5], d[6]), sub(d[7], d[8]))));
+    const V rinv = map(rho, frcp);
+    const V jj15 = mul(bc<V>(-1.5f), fma(jx, jx, fma(jy, jy, mul(jz, jz))));
     // f^eq / w - 1 = (rho - 1) + 3 c.j + (4.5 (c.j)^2 - 1.5 |j|^2) / rho: the linear term in c.j
     // carries exactly the node's momentum whatever the rounding of 1/rho.  Opposite velocities
     // share the even part q and differ in the sign of 3 c.j.
-    float heq[Q], n[Q];
-    heq[0] = drho - 1.5f * jj * rinv;
-    n[0] = h[0] - heq[0];
+    V heq[Q], n[Q];
+    heq[0] = fma(jj15, rinv, drho);
+    n[0] = sub(h[0], heq[0]);
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
         const int i = 2 * p + 1;
-        float cj = 0.f;
-        MCLBM_SIGNED_ADD(cj, cx(i), jx);
-        MCLBM_SIGNED_ADD(cj, cy(i), jy);
-        MCLBM_SIGNED_ADD(cj, cz(i), jz);
-        const float q = drho + rinv * (4.5f * cj * cj - 1.5f * jj);
-        heq[i] = q + 3.0f * cj;
-        heq[i + 1] = q - 3.0f * cj;
-        n[i] = h[i] - heq[i];
-        n[i + 1] = h[i + 1] - heq[i + 1];
+        const V cj = c_dot(i, jx, jy, jz);
+        const V q = fma(rinv, fma(bc<V>(4.5f), mul(cj, cj), jj15), drho);
+        heq[i] = fma(bc<V>(3.f), cj, q);
+        heq[i + 1] = fma(bc<V>(-3.f), cj, q);
+        n[i] = sub(h[i], heq[i]);
+        n[i + 1] = sub(h[i + 1], heq[i + 1]);
     }
     // second moments of f^neq (normalised): P_ab = sum w c_a c_b n
-    const float ex = n[7] + n[8] + n[9] + n[10];      // xy edges
-    const float exz = n[11] + n[12] + n[13] + n[14];  // xz edges
-    const float eyz = n[15] + n[16] + n[17] + n[18];  // yz edges
-    const float pxx = w1 * (n[1] + n[2]) + w2 * (ex + exz);
-    const float pyy = w1 * (n[3] + n[4]) + w2 * (ex + eyz);
-    const float pzz = w1 * (n[5] + n[6]) + w2 * (exz + eyz);
-    const float pxy = w2 * ((n[7] + n[8]) - (n[9] + n[10]));
-    const float pxz = w2 * ((n[11] + n[12]) - (n[13] + n[14]));
-    const float pyz = w2 * ((n[15] + n[16]) - (n[17] + n[18]));
-    const float tr3 = (pxx + pyy + pzz) * (1.0f / 3.0f);
-    // shear part normalised by w (equal on opposite velocities): faces 9 D_aa, edges 9 s l P_ab
-    float sp[9];
-    sp[0] = 9.0f * (pxx - tr3);
-    sp[1] = 9.0f * (pyy - tr3);
-    sp[2] = 9.0f * (pzz - tr3);
-    sp[3] = 9.0f * pxy;
-    sp[4] = -9.0f * pxy;
-    sp[5] = 9.0f * pxz;
-    sp[6] = -9.0f * pxz;
-    sp[7] = 9.0f * pyz;
-    sp[8] = -9.0f * pyz;
-    // <Ds|Dh> and <Dh|Dh> with 1/f^eq = 1/(w (1 + heq)): sum w s k / (1 + heq)
-    float k[Q];
+    const V a78 = add(n[7], n[8]), a910 = add(n[9], n[10]), a1112 = add(n[11], n[12]);
+    const V a1314 = add(n[13], n[14]), a1516 = add(n[15], n[16]), a1718 = add(n[17], n[18]);
+    const V exy = add(a78, a910), exz = add(a1112, a1314), eyz = add(a1516, a1718);
+    const V pxx = fma(W1, add(n[1], n[2]), mul(W2, add(exy, exz)));
+    const V pyy = fma(W1, add(n[3], n[4]), mul(W2, add(exy, eyz)));
+    const V pzz = fma(W1, add(n[5], n[6]), mul(W2, add(exz, eyz)));
+    const V tr3 = mul(add(add(pxx, pyy), pzz), bc<V>(1.0f / 3.0f));
+    // Shear part normalised by w (equal on opposite velocities): s = 9 D_c on the faces (D_c =
+    // P_cc - tr/3) and s l P_ab / (4 w2) = +-D_c / 4 on the edges (D_c = the edge-sum difference,
+    // sign + for pairs p = 3, 5, 7 and - for p = 4, 6, 8).  The factors enter only as constants
+    // of single fma or multiply operations, never as a separately rounded product.
+    V D[6];
+    D[0] = sub(pxx, tr3);
+    D[1] = sub(pyy, tr3);
+    D[2] = sub(pzz, tr3);
+    D[3] = sub(a78, a910);
+    D[4] = sub(a1112, a1314);
+    D[5] = sub(a1516, a1718);
+    // k = Dh / w = n - s;  <Ds|Dh> = sum w s k / (1 + heq),  <Dh|Dh> = sum w k^2 / (1 + heq)
+    V k[Q], A[9];
     k[0] = n[0];
-    float hh = __fdividef(w0, 1.0f + heq[0]) * k[0] * k[0];
-    float sh = 0.f;
+    const V kr0 = mul(k[0], map(add(one, heq[0]), frcp));
+    V hf = bc<V>(0.f), he = bc<V>(0.f);
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
         const int i = 2 * p + 1;
-        k[i] = n[i] - sp[p];
-        k[i + 1] = n[i + 1] - sp[p];
-        const float wa = __fdividef(weight<float>(i), 1.0f + heq[i]);
-        const float wb = __fdividef(weight<float>(i), 1.0f + heq[i + 1]);
-        const float ka = wa * k[i], kb = wb * k[i + 1];
-        sh += sp[p] * (ka + kb);
-        hh += ka * k[i] + kb * k[i + 1];
+        const V Dp = D[p < 3 ? p : 3 + (p - 3) / 2];
+        const float ms = p < 3 ? -9.f : ((p - 3) % 2 == 1 ? 0.25f : -0.25f);  // -s / D
+        k[i] = fma(Dp, bc<V>(ms), n[i]);
+        k[i + 1] = fma(Dp, bc<V>(ms), n[i + 1]);
+        const V ka = mul(k[i], map(add(one, heq[i]), frcp));
+        const V kb = mul(k[i + 1], map(add(one, heq[i + 1]), frcp));
+        A[p] = add(ka, kb);
+        if (p == 0)
+            hf = fma(kb, k[i + 1], mul(ka, k[i]));
+        else if (p < 3)
+            hf = fma(kb, k[i + 1], fma(ka, k[i], hf));
+        else if (p == 3)
+            he = fma(kb, k[i + 1], mul(ka, k[i]));
+        else
+            he = fma(kb, k[i + 1], fma(ka, k[i], he));
     }
-    const float gamma = (hh <= kHHGuard) ? 2.0f : a - b * __fdividef(sh, hh);
-    const float bo = 0.5f * omega * gamma;
-    h[0] = h[0] - bo * k[0];
+    // sh = w1 sum_faces 9 D (ka + kb) + w2 sum_edges (+-D / 4)(ka + kb), w1 9 = 1/2, w2 / 4 = 1/144
+    const V sf = fma(D[0], A[0], fma(D[1], A[1], mul(D[2], A[2])));
+    const V se = fma(D[3], sub(A[3], A[4]), fma(D[4], sub(A[5], A[6]), mul(D[5], sub(A[7], A[8]))));
+    const V sh = fma(bc<V>(0.5f), sf, mul(bc<V>(1.0f / 144.0f), se));
+    const V hh = fma(W0, mul(kr0, k[0]), fma(W1, hf, mul(W2, he)));
+    const V gamma = map(hh, sh, [a, b](float hs, float ss) {
+        return hs <= kHHGuard ? 2.0f : fma(-b, mul(ss, rcp_approx(hs)), a);
+    });
+    // f* = f - omega Ds - (omega gamma / 2) Dh, written as f^eq + (1 - omega) Ds + (1 - beta) Dh so
+    // that h is not needed past n (fewer live registers)
+    const V omb = fma(bc<V>(-0.5f * omega), gamma, one);  // 1 - beta
+    h[0] = fma(omb, k[0], heq[0]);
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
         const int i = 2 * p + 1;
-        h[i] = h[i] - omega * sp[p] - bo * k[i];
-        h[i + 1] = h[i + 1] - omega * sp[p] - bo * k[i + 1];
+        const float sd = p < 3 ? 9.f : ((p - 3) % 2 == 1 ? -0.25f : 0.25f);  // s / D
+        const V cs = bc<V>(sd * (1.0f - omega));
+        const V Dp = D[p < 3 ? p : 3 + (p - 3) / 2];
+        h[i] = fma(omb, k[i], fma(Dp, cs, heq[i]));
+        h[i + 1] = fma(omb, k[i + 1], fma(Dp, cs, heq[i + 1]));
     }
     return gamma;
 }

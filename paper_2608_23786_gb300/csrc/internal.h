@@ -78,7 +78,7 @@ cudaError_t launch_wait_selftest(mclbm_ctx* c);
 cudaError_t launch_levels(mclbm_ctx* const* levels, int nlev, const LaunchConfig& cfg, cudaStream_t s, int* occ);
 bool vec_supported(int precision, int vec);
 bool launch_supported(int precision, const LaunchConfig& c);
-LaunchConfig default_launch(int precision);
+LaunchConfig default_launch(int precision, int pattern);
 cudaError_t launch_get_populations(const mclbm_ctx* c, int sample, double* d_out);
 cudaError_t launch_set_populations(mclbm_ctx* c, int sample, const double* d_in);
 cudaError_t launch_moments(const mclbm_ctx* c, int sample, double* d_rho, double* d_u);

@@ -13,7 +13,11 @@ constexpr int kMaxLevels = 8;  // levels of one batched launch
 struct LaunchConfig {
     int vec;       // nodes per thread along x
     int block;     // threads per block (128 or 256); the staged kernel always uses 288
-    int kind = 0;  // 0: direct loads (stepper_impl.cuh), 1: shared-memory staging (stepper_staged.cuh)
+    int kind = 0;  // 0: direct loads (stepper_impl.cuh), 1: shared-memory staging (stepper_staged.cuh),
+                   // 2: direct loads with the next run prefetched, 3: as 2 with the packed FP32
+                   // collision of node pairs (shifted storage, even vec), 4 / 5: runs ahead
+                   // prefetched by cp.async into shared memory, 1 / 2 runs deep (shifted
+                   // storage, block 128; packed collision for even vec)
 };
 
 // Variants compiled per element type (nodes per thread; VEC * sizeof(E) <= 16 bytes).

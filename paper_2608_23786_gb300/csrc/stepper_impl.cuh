@@ -199,22 +199,41 @@ __device__ __forceinline__ void scatter_row(E* row, int x0, int N, int lane, con
     }
 }
 
-template <class E, int VEC>
+// Collide the VEC nodes of a run.  PACK (shifted storage, VEC even) runs the FP32
+// collision on node pairs in the packed FP32 pipe; the results are bit-identical to the
+// one-node form.
+template <class E, int VEC, bool PACK = false>
 __device__ __forceinline__ void collide_run(typename Storage<E>::compute (&v)[Q][VEC], const LevelArgs<E>& L)
 {
     const typename Storage<E>::compute omega = omega_of<E>(L);
     using C = typename Storage<E>::compute;
+    if constexpr (PACK) {
+        static_assert(Storage<E>::shifted && VEC % 2 == 0, "packed collision needs FP32 lanes in pairs");
 #pragma unroll
-    for (int k = 0; k < VEC; ++k) {
-        C t[Q];
+        for (int k = 0; k < VEC; k += 2) {
+            float2 t[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) t[i] = v[i][k];
-        if constexpr (Storage<E>::shifted)
-            kbc_shifted(t, omega, L.a32, L.b32);
-        else
-            kbc_raw(t, omega);
+            for (int i = 0; i < Q; ++i) t[i] = make_float2(v[i][k], v[i][k + 1]);
+            kbc_shifted<float2>(t, omega, L.a32, L.b32);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) v[i][k] = t[i];
+            for (int i = 0; i < Q; ++i) {
+                v[i][k] = t[i].x;
+                v[i][k + 1] = t[i].y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            C t[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) t[i] = v[i][k];
+            if constexpr (Storage<E>::shifted)
+                kbc_shifted<float>(t, omega, L.a32, L.b32);
+            else
+                kbc_raw(t, omega);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) v[i][k] = t[i];
+        }
     }
 }
 
@@ -370,13 +389,14 @@ __device__ __forceinline__ void finish_row(const RawRun<E, VEC>& r, int x0, int 
     }
 }
 
-template <class E, int VEC, int I = 0>
+template <class E, int VEC, int FIX, int I = 0>
 __device__ __forceinline__ void issue_all(const E* base, const Geom& g, const RunLoc& p, int lane,
                                           RawRun<E, VEC> (&raw)[Q])
 {
     if constexpr (I < Q) {
-        const bool shift = p.mode != 1;
-        const int slot = p.mode == 2 ? Dir<I>::o : I;
+        const int mode = FIX >= 0 ? FIX : p.mode;
+        const bool shift = mode != 1;
+        const int slot = mode == 2 ? Dir<I>::o : I;
         const int ry = shift ? g.wrap(p.y - Dir<I>::y) : p.y;
         const int rz = shift ? g.wrap(p.z - Dir<I>::z) : p.z;
         const E* row = base + (int64_t)slot * g.n + g.node(0, ry, rz);
@@ -384,20 +404,21 @@ __device__ __forceinline__ void issue_all(const E* base, const Geom& g, const Ru
             issue_row<E, VEC, Dir<I>::x>(row, p.x0, g.N, lane, raw[I]);
         else
             issue_row<E, VEC, 0>(row, p.x0, g.N, lane, raw[I]);
-        issue_all<E, VEC, I + 1>(base, g, p, lane, raw);
+        issue_all<E, VEC, FIX, I + 1>(base, g, p, lane, raw);
     }
 }
 
-template <class E, int VEC, int I = 0>
+template <class E, int VEC, int FIX, int I = 0>
 __device__ __forceinline__ void finish_all(const Geom& g, const RunLoc& p, int lane, const RawRun<E, VEC> (&raw)[Q],
                                            typename Storage<E>::compute (&v)[Q][VEC])
 {
     if constexpr (I < Q) {
-        if (p.mode != 1)
+        const int mode = FIX >= 0 ? FIX : p.mode;
+        if (mode != 1)
             finish_row<E, VEC, Dir<I>::x>(raw[I], p.x0, g.N, lane, v[I]);
         else
             finish_row<E, VEC, 0>(raw[I], p.x0, g.N, lane, v[I]);
-        finish_all<E, VEC, I + 1>(g, p, lane, raw, v);
+        finish_all<E, VEC, FIX, I + 1>(g, p, lane, raw, v);
     }
 }
 
@@ -420,7 +441,10 @@ __device__ __forceinline__ RunLoc locate(const BatchArgs<E>& args, int64_t t, in
     return p;
 }
 
-template <class E, int VEC, int PATTERN, int BLOCK>
+// FIX: -1 takes each level's mode at run time; 0 (pull), 1 (AA even) or 2 (AA odd) when every
+// level of the launch has that mode, which drops the other branches.  PACK: packed FP32
+// collision of node pairs.
+template <class E, int VEC, int PATTERN, int BLOCK, int FIX, bool PACK>
 __global__ void __launch_bounds__(BLOCK) k_step_prefetch(const BatchArgs<E> args)
 {
     using C = typename Storage<E>::compute;
@@ -433,26 +457,27 @@ __global__ void __launch_bounds__(BLOCK) k_step_prefetch(const BatchArgs<E> args
     RawRun<E, VEC> raw[Q];
     {
         const LevelArgs<E>& L = args.lev[cur.l];
-        issue_all<E, VEC>(L.src + (int64_t)cur.m * Q * L.g.n, L.g, cur, lane, raw);
+        issue_all<E, VEC, FIX>(L.src + (int64_t)cur.m * Q * L.g.n, L.g, cur, lane, raw);
     }
     while (true) {
         const LevelArgs<E>& L = args.lev[cur.l];
         const Geom g = L.g;
         C v[Q][VEC];
-        finish_all<E, VEC>(g, cur, lane, raw, v);
+        finish_all<E, VEC, FIX>(g, cur, lane, raw, v);
         const int64_t tn = t + stride;
         const bool more = tn < total;
         RunLoc nxt = cur;
         if (more) {
             nxt = locate<E, VEC>(args, tn, PATTERN);
             const LevelArgs<E>& Ln = args.lev[nxt.l];
-            issue_all<E, VEC>(Ln.src + (int64_t)nxt.m * Q * Ln.g.n, Ln.g, nxt, lane, raw);
+            issue_all<E, VEC, FIX>(Ln.src + (int64_t)nxt.m * Q * Ln.g.n, Ln.g, nxt, lane, raw);
         }
-        collide_run<E, VEC>(v, L);
+        collide_run<E, VEC, PACK>(v, L);
         E* base = L.dst + (int64_t)cur.m * Q * g.n;
-        if (cur.mode == 0)
+        const int mode = FIX >= 0 ? FIX : cur.mode;
+        if (mode == 0)
             scatter_all<E, VEC, 0>(base, g, cur.x0, cur.y, cur.z, lane, v);
-        else if (cur.mode == 1)
+        else if (mode == 1)
             store_own_opp<E, VEC>(base, g, cur.node, v);
         else
             scatter_all<E, VEC, 1>(base, g, cur.x0, cur.y, cur.z, lane, v);

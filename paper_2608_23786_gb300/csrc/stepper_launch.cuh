@@ -3,6 +3,7 @@
 // once, so the variants compile in parallel.
 #pragma once
 #include "launch.h"
+#include "stepper_async.cuh"
 #include "stepper_impl.cuh"
 #include "stepper_staged.cuh"
 
@@ -29,10 +30,10 @@ cudaError_t launch_variant(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, 
     return cudaGetLastError();
 }
 
-template <class E, int VEC, int PATTERN, int BLOCK>
-cudaError_t launch_prefetch_variant(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, int* occupancy_out)
+template <class E, int VEC, int PATTERN, int BLOCK, int FIX, bool PACK>
+cudaError_t launch_prefetch_fixed(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, int* occupancy_out)
 {
-    auto kern = k_step_prefetch<E, VEC, PATTERN, BLOCK>;
+    auto kern = k_step_prefetch<E, VEC, PATTERN, BLOCK, FIX, PACK>;
     static int occ = -1;
     if (occ < 0) {
         int o = 0;
@@ -50,6 +51,67 @@ cudaError_t launch_prefetch_variant(const BatchArgs<E>& a, int grid_cap, cudaStr
     return cudaGetLastError();
 }
 
+// Pull launches take the pull-only kernel; AA launches whose levels all share a parity take the
+// even- or odd-only kernel, mixed parities the general one.
+template <class E, int VEC, int PATTERN, int BLOCK, bool PACK>
+cudaError_t launch_prefetch_variant(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, int* occ)
+{
+    if constexpr (PATTERN == 0) {
+        return launch_prefetch_fixed<E, VEC, 0, BLOCK, 0, PACK>(a, grid_cap, s, occ);
+    } else {
+        bool all_even = true, all_odd = true;
+        for (int l = 0; l < a.nlev; ++l) {
+            all_even = all_even && a.lev[l].parity == 0;
+            all_odd = all_odd && a.lev[l].parity == 1;
+        }
+        if (all_even) return launch_prefetch_fixed<E, VEC, 1, BLOCK, 1, PACK>(a, grid_cap, s, occ);
+        if (all_odd) return launch_prefetch_fixed<E, VEC, 1, BLOCK, 2, PACK>(a, grid_cap, s, occ);
+        return launch_prefetch_fixed<E, VEC, 1, BLOCK, -1, PACK>(a, grid_cap, s, occ);
+    }
+}
+
+template <class E, int VEC, int PATTERN, int BLOCK, int FIX, int STAGES>
+cudaError_t launch_async_fixed(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, int* occupancy_out)
+{
+    auto kern = k_step_async<E, VEC, PATTERN, BLOCK, FIX, STAGES>;
+    constexpr int smem = AsyncRing<E, VEC, BLOCK, STAGES>::kBytes;
+    static int occ = -1;
+    if (occ < 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        int o = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, BLOCK, smem);
+        if (e != cudaSuccess) return e;
+        if (o < 1) return cudaErrorInvalidConfiguration;
+        occ = o;
+    }
+    if (occupancy_out) *occupancy_out = occ;
+    const int64_t total = a.prefix[a.nlev];
+    int64_t blocks = (total + BLOCK - 1) / BLOCK;
+    const int64_t cap = (int64_t)grid_cap * occ;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, BLOCK, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <class E, int VEC, int PATTERN, int BLOCK, int STAGES>
+cudaError_t launch_async_variant(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, int* occ)
+{
+    if constexpr (PATTERN == 0) {
+        return launch_async_fixed<E, VEC, 0, BLOCK, 0, STAGES>(a, grid_cap, s, occ);
+    } else {
+        bool all_even = true, all_odd = true;
+        for (int l = 0; l < a.nlev; ++l) {
+            all_even = all_even && a.lev[l].parity == 0;
+            all_odd = all_odd && a.lev[l].parity == 1;
+        }
+        if (all_even) return launch_async_fixed<E, VEC, 1, BLOCK, 1, STAGES>(a, grid_cap, s, occ);
+        if (all_odd) return launch_async_fixed<E, VEC, 1, BLOCK, 2, STAGES>(a, grid_cap, s, occ);
+        return launch_async_fixed<E, VEC, 1, BLOCK, -1, STAGES>(a, grid_cap, s, occ);
+    }
+}
+
 template <class E, int PATTERN, int... VECS>
 cudaError_t launch_vec_block(const BatchArgs<E>& a, const LaunchConfig& cfg, int grid_cap, cudaStream_t s, int* occ)
 {
@@ -61,11 +123,33 @@ cudaError_t launch_vec_block(const BatchArgs<E>& a, const LaunchConfig& cfg, int
         found = true;
         if (cfg.kind == 2) {
             if (cfg.block == 128)
-                e = launch_prefetch_variant<E, V, PATTERN, 128>(a, grid_cap, s, occ);
+                e = launch_prefetch_variant<E, V, PATTERN, 128, false>(a, grid_cap, s, occ);
             else if (cfg.block == 256)
-                e = launch_prefetch_variant<E, V, PATTERN, 256>(a, grid_cap, s, occ);
+                e = launch_prefetch_variant<E, V, PATTERN, 256, false>(a, grid_cap, s, occ);
             else
                 e = cudaErrorInvalidConfiguration;
+        } else if (cfg.kind == 3) {
+            if constexpr (Storage<E>::shifted && V % 2 == 0) {
+                if (cfg.block == 128)
+                    e = launch_prefetch_variant<E, V, PATTERN, 128, true>(a, grid_cap, s, occ);
+                else if (cfg.block == 256)
+                    e = launch_prefetch_variant<E, V, PATTERN, 256, true>(a, grid_cap, s, occ);
+                else
+                    e = cudaErrorInvalidConfiguration;
+            } else {
+                e = cudaErrorInvalidConfiguration;
+            }
+        } else if (cfg.kind == 4 || cfg.kind == 5) {
+            if constexpr (Storage<E>::shifted) {
+                if (cfg.block != 128)
+                    e = cudaErrorInvalidConfiguration;
+                else if (cfg.kind == 4)
+                    e = launch_async_variant<E, V, PATTERN, 128, 2>(a, grid_cap, s, occ);
+                else
+                    e = launch_async_variant<E, V, PATTERN, 128, 3>(a, grid_cap, s, occ);
+            } else {
+                e = cudaErrorInvalidConfiguration;
+            }
         } else if (cfg.block == 128)
             e = launch_variant<E, V, PATTERN, 128>(a, grid_cap, s, occ);
         else if (cfg.block == 256)

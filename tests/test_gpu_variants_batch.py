@@ -17,6 +17,9 @@ STAGED = [1, 2]
 def _shapes(precision, N):
     """(kind, vec, block) of every launch shape that applies to a lattice of side N."""
     out = [(k, v, b) for k in (0, 2) for v in VARIANTS[precision] if N % v == 0 for b in (128, 256)]
+    if precision != "fp64":  # packed FP32 collision of node pairs; shared-memory prefetch rings
+        out += [(3, v, b) for v in VARIANTS[precision] if v % 2 == 0 and N % v == 0 for b in (128, 256)]
+        out += [(k, v, 128) for k in (4, 5) for v in VARIANTS[precision] if N % v == 0]
     out += [(1, v, 0) for v in STAGED if N % v == 0]
     return out
 
