@@ -283,6 +283,55 @@ def run_large(args):
     print(json.dumps(out))
 
 
+def run_adjoint(args):
+    """Adjoint workload alone: dE(T)/dX of 64^3 x M randomized-TGV samples (M = 16 unless --M), T = 500
+    FP32 steps (--T), checkpoint every 50; one bench step = one whole gradient (forward with
+    checkpoints, segment recomputation, reverse sweep, parameter reduction)."""
+    import torch
+    from paper_2608_23786_gb300 import Ensemble, mclbm
+    import ensemble_inputs as gen
+    mclbm.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    M, T, K = args.M or 16, args.T, 50
+    X = gen.draw_params(1, M)
+    ens = Ensemble(64, M, Re=800.0, Ma=0.025, precision="fp32", pattern="pull", device=dev, stream=stream).init(X)
+    need = mclbm.mclbm_grad_required_bytes(ens.ctx, T, K)
+    gbuf = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+    gptr = (gbuf.data_ptr() + 255) // 256 * 256
+    for _ in range(max(3, args.warmup)):
+        ens.init(X)
+        mclbm.mclbm_grad(ens.ctx, 0, T, K, gptr, need, M)
+    torch.cuda.synchronize()
+    ph = np.zeros(4)
+    with ClockSampler(0) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ens.init(X)
+            J, G = mclbm.mclbm_grad(ens.ctx, 0, T, K, gptr, need, M)  # synchronises (host results)
+            ph += np.array(mclbm.mclbm_grad_timing(ens.ctx))
+        sec = time.perf_counter() - t0
+    ph /= args.steps
+    lu = M * 64**3 * T
+    peaks, peak_kind = measured_peaks()
+    rev_bytes = 3 * 19 * 4 * lu
+    achieved = rev_bytes / (ph[2] / 1e3) / 1e9
+    out = {
+        "metric": "adjoint_glups", "value": lu * args.steps / sec / 1e9, "unit": "GLUPS (whole gradient)",
+        "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": sec / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"rtgv_64cube_x{M}_fp32_{T}steps_ckpt{K}_dE", "l2": "inputs larger than L2"},
+        "phases_ms": {"forward": ph[0], "recompute": ph[1], "reverse": ph[2], "reduction": ph[3]},
+        "roofline": {"kernel": "k_adjoint_async<float,2,2>", "bound": "hbm", "achieved": achieved,
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                     "peak_kind": peak_kind, "traffic": None, "algorithmic_bytes_per_lu": 3 * 19 * 4,
+                     "reverse_glups": lu / (ph[2] / 1e3) / 1e9},
+        "grad_finite": bool(np.all(np.isfinite(G))), "clocks": clk.summary(),
+    }
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -297,13 +346,18 @@ def main():
     ap.add_argument("--M", type=int, default=None, help="override the number of samples (profiling of small cases)")
     ap.add_argument("--launch", default=None, help="kind,vec,block instead of the library default (e.g. 0,2,128)")
     ap.add_argument("--autotune", action="store_true", help="let the library's autotuner pick the launch shape")
-    ap.add_argument("--workload", default="ensemble64", choices=["ensemble64", "levels_fp32", "levels_fp16", "large"],
-                    help="ensemble64 (default): 64^3 x 64 FP32; levels_*: 3-level batch; large: 512^3 x 4 FP16 AA")
+    ap.add_argument("--workload", default="ensemble64",
+                    choices=["ensemble64", "levels_fp32", "levels_fp16", "large", "adjoint"],
+                    help="ensemble64 (default): 64^3 x 64 FP32; levels_*: 3-level batch; large: 512^3 x 4 FP16 AA; "
+                         "adjoint: gradient of E(T), 64^3 x 16, 500 steps")
+    ap.add_argument("--T", type=int, default=500, help="adjoint horizon (steps) of --workload adjoint")
     args = ap.parse_args()
     if args.workload.startswith("levels"):
         return run_levels(args, args.workload.split("_")[1])
     if args.workload == "large":
         return run_large(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     wl = dict(WORKLOAD)
     if args.N or args.M:
         wl["N"] = args.N or wl["N"]

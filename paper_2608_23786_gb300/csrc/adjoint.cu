@@ -19,6 +19,7 @@
 
 #include "adjoint.cuh"
 #include "internal.h"
+#include "stepper_async.cuh"
 #include "stepper_impl.cuh"
 
 namespace mclbm {
@@ -71,6 +72,172 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_step(const E* __restrict__ s
 #pragma unroll
         for (int i = 0; i < Q; ++i) lo[(int64_t)i * g.n + node] = lam[i];
     }
+}
+
+// Threads per block of the FP32 adjoint kernel.  It works on runs of VEC consecutive x-nodes
+// with the thread mapping and x-shift shuffles of the forward stepper; runs = M N^3 / VEC is a
+// multiple of 32, so warps stay whole.
+constexpr int kRunBlock = 128;
+
+// Shared-memory ring of the adjoint run kernel: per stage, the Q state vectors, the Q lambda^{t+1}
+// vectors and the edge words (state and lambda, x-moving populations only) of every thread.
+template <class E, int VEC, int STAGES>
+struct AdjRing {
+    static constexpr int kVS = VEC * (int)sizeof(E), kVL = VEC * 4;
+    static constexpr int kStateBytes = STAGES * Q * kRunBlock * kVS;
+    static constexpr int kLamBytes = STAGES * Q * kRunBlock * kVL;
+    static constexpr int kBytes = kStateBytes + kLamBytes + STAGES * 2 * kEdges * kRunBlock * 4;
+    __device__ __forceinline__ static int state_off(int stage, int i, int tid) { return ((stage * Q + i) * kRunBlock + tid) * kVS; }
+    __device__ __forceinline__ static int lam_off(int stage, int i, int tid)
+    {
+        return kStateBytes + ((stage * Q + i) * kRunBlock + tid) * kVL;
+    }
+    __device__ __forceinline__ static int edge_off(int stage, int which, int i, int tid)
+    {
+        return kStateBytes + kLamBytes + (((stage * 2 + which) * kEdges + edge_index(i)) * kRunBlock + tid) * 4;
+    }
+};
+
+struct RunPos {
+    int m, x0, y, z;
+    int64_t node;
+};
+
+__device__ __forceinline__ RunPos run_pos(const Geom& g, int64_t t, int vec)
+{
+    RunPos r;
+    const int64_t first = t * vec;
+    r.m = (int)(first >> (3 * g.logN));
+    r.node = first & (g.n - 1);
+    r.x0 = (int)(r.node & (g.N - 1));
+    r.y = (int)((r.node >> g.logN) & (g.N - 1));
+    r.z = (int)(r.node >> (2 * g.logN));
+    return r;
+}
+
+// Issue the copies of one run: state f_i(x) from slot i of x - c_i, lambda^{t+1} from slot i of x + c_i.
+template <class E, int VEC, int STAGES, int I = 0>
+__device__ __forceinline__ void adj_issue(const E* sbase, const float* lbase, const Geom& g, const RunPos& p, int lane,
+                                          uint32_t smem, int stage)
+{
+    if constexpr (I < Q) {
+        using Ring = AdjRing<E, VEC, STAGES>;
+        const int tid = threadIdx.x;
+        const E* srow = sbase + (int64_t)I * g.n + g.node(0, g.wrap(p.y - Dir<I>::y), g.wrap(p.z - Dir<I>::z));
+        const float* lrow = lbase + (int64_t)I * g.n + g.node(0, g.wrap(p.y + Dir<I>::y), g.wrap(p.z + Dir<I>::z));
+        cp_async<Ring::kVS>(smem + Ring::state_off(stage, I, tid), srow + p.x0);
+        cp_async<Ring::kVL>(smem + Ring::lam_off(stage, I, tid), lrow + p.x0);
+        const bool first = lane == 0 || p.x0 == 0, last = lane == 31 || p.x0 + VEC == g.N;
+        const int before = (p.x0 - 1) & (g.N - 1), after = (p.x0 + VEC) & (g.N - 1);
+        if constexpr (Dir<I>::x > 0) {  // state from x - 1, lambda from x + 1
+            if (first) cp_async<4>(smem + Ring::edge_off(stage, 0, I, tid), edge_word(srow, before));
+            if (last) cp_async<4>(smem + Ring::edge_off(stage, 1, I, tid), lrow + after);
+        } else if constexpr (Dir<I>::x < 0) {  // state from x + 1, lambda from x - 1
+            if (last) cp_async<4>(smem + Ring::edge_off(stage, 0, I, tid), edge_word(srow, after));
+            if (first) cp_async<4>(smem + Ring::edge_off(stage, 1, I, tid), lrow + before);
+        }
+        adj_issue<E, VEC, STAGES, I + 1>(sbase, lbase, g, p, lane, smem, stage);
+    }
+}
+
+template <class T, int VEC, int CXI>
+__device__ __forceinline__ RawRun<T, VEC> adj_raw(const unsigned char* smem, int vec_off, int edge_off)
+{
+    using R = typename RawOf<VEC * sizeof(T)>::type;
+    RawRun<T, VEC> r;
+    const R w = *reinterpret_cast<const R*>(smem + vec_off);
+    memcpy(r.w, &w, sizeof(R));
+    if constexpr (CXI != 0) {
+        const unsigned int e = *reinterpret_cast<const unsigned int*>(smem + edge_off);
+        if constexpr (sizeof(T) == 2) {  // source x - 1 is odd (high half), x + VEC even (low half)
+            const unsigned short hv = CXI > 0 ? (unsigned short)(e >> 16) : (unsigned short)(e & 0xffffu);
+            memcpy(&r.edge, &hv, 2);
+        } else {
+            memcpy(&r.edge, &e, 4);
+        }
+    }
+    return r;
+}
+
+template <class E, int VEC, int STAGES, int I = 0>
+__device__ __forceinline__ void adj_finish(const unsigned char* smem, int stage, const Geom& g, const RunPos& p,
+                                           int lane, float (&hv)[Q][VEC], float (&mv)[Q][VEC])
+{
+    if constexpr (I < Q) {
+        using Ring = AdjRing<E, VEC, STAGES>;
+        const int tid = threadIdx.x;
+        const RawRun<E, VEC> rs = adj_raw<E, VEC, Dir<I>::x>(smem, Ring::state_off(stage, I, tid),
+                                                             Ring::edge_off(stage, 0, I, tid));
+        finish_row<E, VEC, Dir<I>::x>(rs, p.x0, g.N, lane, hv[I]);
+        const RawRun<float, VEC> rl = adj_raw<float, VEC, -Dir<I>::x>(smem, Ring::lam_off(stage, I, tid),
+                                                                      Ring::edge_off(stage, 1, I, tid));
+        finish_row<float, VEC, -Dir<I>::x>(rl, p.x0, g.N, lane, mv[I]);
+        adj_finish<E, VEC, STAGES, I + 1>(smem, stage, g, p, lane, hv, mv);
+    }
+}
+
+// FP32 adjoint step: gather the pre-collision state (pull layout, shifted storage; f_i(x) from
+// slot i of x - c_i) and lambda^{t+1}(x + c_i) (the transpose of pull streaming), apply the paired
+// lane-form product to node pairs in packed FP32x2, store lambda^t aligned.  The next run's state
+// and lambda^{t+1} are copied into shared memory (cp.async, STAGES - 1 runs ahead) during the
+// current run's product; each thread reads back only its own slots after its own wait_group (no
+// block barrier, no spin).
+template <class E, int VEC, int STAGES>
+__global__ void __launch_bounds__(kRunBlock) k_adjoint_async(const E* __restrict__ state,
+                                                             const float* __restrict__ lam_next,
+                                                             float* __restrict__ lam_out, Geom g, int64_t runs,
+                                                             float omega, float a, float b)
+{
+    static_assert(VEC == 2, "node pairs");
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * kRunBlock;
+    int64_t t = blockIdx.x * (int64_t)kRunBlock + threadIdx.x;
+    if (t >= runs) return;  // whole warps: runs and strides are multiples of 32
+#pragma unroll
+    for (int s = 0; s < STAGES - 1; ++s) {
+        const int64_t ts = t + s * stride;
+        if (ts < runs) {
+            const RunPos p = run_pos(g, ts, VEC);
+            adj_issue<E, VEC, STAGES>(state + (int64_t)p.m * Q * g.n, lam_next + (int64_t)p.m * Q * g.n, g, p, lane,
+                                      sbase, s);
+        }
+        cp_async_commit();
+    }
+    int stage = 0;
+    for (;;) {
+        const int64_t ta = t + (int64_t)(STAGES - 1) * stride;
+        if (ta < runs) {
+            const RunPos p = run_pos(g, ta, VEC);
+            int sa = stage + STAGES - 1;
+            if (sa >= STAGES) sa -= STAGES;
+            adj_issue<E, VEC, STAGES>(state + (int64_t)p.m * Q * g.n, lam_next + (int64_t)p.m * Q * g.n, g, p, lane,
+                                      sbase, sa);
+        }
+        cp_async_commit();
+        cp_async_wait<STAGES - 1>();
+        const RunPos p = run_pos(g, t, VEC);
+        float hv[Q][VEC], mv[Q][VEC];
+        adj_finish<E, VEC, STAGES>(smem, stage, g, p, lane, hv, mv);
+        float2 h2[Q], m2[Q], l2[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            h2[i] = make_float2(hv[i][0], hv[i][1]);
+            m2[i] = make_float2(mv[i][0], mv[i][1]);
+        }
+        kbc_vjp_shifted<float2>(h2, m2, omega, a, b, l2);
+        float* lo = lam_out + (int64_t)p.m * Q * g.n + p.node;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const float o[2] = {l2[i].x, l2[i].y};
+            vstore<float, 2>(lo + (int64_t)i * g.n, o);
+        }
+        t += stride;
+        if (t >= runs) break;
+        stage = stage + 1 == STAGES ? 0 : stage + 1;
+    }
+    cp_async_wait<0>();
 }
 
 // rho and u (lattice units) of f(x) in FP64
@@ -248,8 +415,27 @@ cudaError_t adjoint_step_t(mclbm_ctx* c, const void* state, const void* lin, voi
         k_adjoint_step<double, double><<<grid_for((int64_t)c->M * c->n), kBlock, 0, c->stream>>>(
             (const double*)state, (const double*)lin, (double*)lout, g, c->M, c->units.omega, 0.0);
     } else {
-        k_adjoint_step<E, float><<<grid_for((int64_t)c->M * c->n), kBlock, 0, c->stream>>>(
-            (const E*)state, (const float*)lin, (float*)lout, g, c->M, (float)c->units.omega, kHHGuard);
+        constexpr int kVec = 2;
+        const int64_t runs = (int64_t)c->M * c->n / kVec;
+        int64_t blocks = (runs + kRunBlock - 1) / kRunBlock;
+        if (blocks > (int64_t)c->num_sms * 16) blocks = (int64_t)c->num_sms * 16;
+        const float om = (float)c->units.omega;
+        const float a = (float)(2.0 / c->units.omega), b = (float)(2.0 - 2.0 / c->units.omega);
+        constexpr int kStages = 2;
+        auto kern = k_adjoint_async<E, kVec, kStages>;
+        constexpr int smem = AdjRing<E, kVec, kStages>::kBytes;
+        static int occ = -1;  // resident blocks per SM (per element type)
+        if (occ < 0) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            int o = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kRunBlock, smem);
+            if (e != cudaSuccess) return e;
+            occ = o > 0 ? o : 1;
+        }
+        if (blocks > (int64_t)c->num_sms * occ) blocks = (int64_t)c->num_sms * occ;
+        kern<<<(unsigned)blocks, kRunBlock, smem, c->stream>>>((const E*)state, (const float*)lin, (float*)lout, g,
+                                                               runs, om, a, b);
     }
     return cudaGetLastError();
 }
@@ -428,7 +614,10 @@ __global__ void k_adjoint_step_natural(const double* __restrict__ f, const doubl
             h[i] = (T)(fm[(int64_t)i * g.n + node] / weight<double>(i) - 1.0);
             mu[i] = (T)ln[(int64_t)i * g.n + g.node(g.wrap(x + cx(i)), g.wrap(y + cy(i)), g.wrap(z + cz(i)))];
         }
-        kbc_vjp<T>(h, mu, omega, guard, lam);
+        if constexpr (std::is_same<T, float>::value)  // the FP32 path's product (as in k_adjoint_run)
+            kbc_vjp_shifted<float>(h, mu, omega, 2.0f / omega, 2.0f - 2.0f / omega, lam);
+        else
+            kbc_vjp<T>(h, mu, omega, guard, lam);
         for (int i = 0; i < Q; ++i) lam_out[(int64_t)m * Q * g.n + (int64_t)i * g.n + node] = (double)lam[i];
     }
 }

@@ -175,4 +175,193 @@ __device__ __forceinline__ void kbc_vjp(const T (&h)[Q], const T (&mu)[Q], T ome
     }
 }
 
+// The same product for the FP32 path in the lane form of collide.cuh (V = float for one node,
+// float2 for two nodes in the packed FP32x2 instructions), with opposite velocities paired:
+// the pair shares s, c_i c_i^T and the even part of the equilibrium, so A^T v, the
+// equilibrium chain and the c_j . Q_u term are formed once per pair.  With nq = -q and
+// NV = sum_i nq_i w_i (3 c_i + 9 (c_i . u) c_i - 3 u) (so Q_u / rho = -NV) and
+// NQr = sum_i nq_i w_i e_i (so Q_rho = -NQr / rho):
+//   lambda_j = mu_j + r_j + (NV . u - NQr / rho) - c_j . NV,
+// and a pair (c, -c) contributes 3 w [(nq_+ - nq_-) + 3 (c . u)(nq_+ + nq_-)] c - 3 w u (nq_+ + nq_-)
+// to NV.  Forward quantities are those of kbc_shifted (same operations up to k); gamma = 2 and
+// no dgamma where <Dh|Dh> is at or below kHHGuard.
+template <class V>
+__device__ __forceinline__ void kbc_vjp_shifted(const V (&h)[Q], const V (&mu)[Q], float omega, float a, float b,
+                                                V (&lam)[Q])
+{
+    using namespace lanes;
+    const V one = bc<V>(1.f), W0 = bc<V>(1.0f / 3.0f), W1 = bc<V>(1.0f / 18.0f), W2 = bc<V>(1.0f / 36.0f);
+    const auto frcp = [](float x) { return rcp_approx(x); };
+    // ---- forward, as kbc_shifted
+    const V s1 = add(add(add(h[1], h[2]), add(h[3], h[4])), add(h[5], h[6]));
+    const V s2 = add(add(add(add(h[7], h[8]), add(h[9], h[10])), add(add(h[11], h[12]), add(h[13], h[14]))),
+                     add(add(h[15], h[16]), add(h[17], h[18])));
+    const V drho = fma(W0, h[0], fma(W1, s1, mul(W2, s2)));
+    const V rho = add(one, drho);
+    V d[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) d[p] = sub(h[2 * p + 1], h[2 * p + 2]);
+    const V jx = fma(W1, d[0], mul(W2, add(add(d[3], d[4]), add(d[5], d[6]))));
+    const V jy = fma(W1, d[1], mul(W2, add(sub(d[3], d[4]), add(d[7], d[8]))));
+    const V jz = fma(W1, d[2], mul(W2, add(sub(d[5], d[6]), sub(d[7], d[8]))));
+    const V rinv = map(rho, frcp);
+    const V jj15 = mul(bc<V>(-1.5f), fma(jx, jx, fma(jy, jy, mul(jz, jz))));
+    V heq[Q], n[Q];
+    heq[0] = fma(jj15, rinv, drho);
+    n[0] = sub(h[0], heq[0]);
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const int i = 2 * p + 1;
+        const V cj = c_dot(i, jx, jy, jz);
+        const V q = fma(rinv, fma(bc<V>(4.5f), mul(cj, cj), jj15), drho);
+        heq[i] = fma(bc<V>(3.f), cj, q);
+        heq[i + 1] = fma(bc<V>(-3.f), cj, q);
+        n[i] = sub(h[i], heq[i]);
+        n[i + 1] = sub(h[i + 1], heq[i + 1]);
+    }
+    const V a78 = add(n[7], n[8]), a910 = add(n[9], n[10]), a1112 = add(n[11], n[12]);
+    const V a1314 = add(n[13], n[14]), a1516 = add(n[15], n[16]), a1718 = add(n[17], n[18]);
+    const V exy = add(a78, a910), exz = add(a1112, a1314), eyz = add(a1516, a1718);
+    const V pxx = fma(W1, add(n[1], n[2]), mul(W2, add(exy, exz)));
+    const V pyy = fma(W1, add(n[3], n[4]), mul(W2, add(exy, eyz)));
+    const V pzz = fma(W1, add(n[5], n[6]), mul(W2, add(exz, eyz)));
+    const V tr3 = mul(add(add(pxx, pyy), pzz), bc<V>(1.0f / 3.0f));
+    V D[6];
+    D[0] = sub(pxx, tr3);
+    D[1] = sub(pyy, tr3);
+    D[2] = sub(pzz, tr3);
+    D[3] = sub(a78, a910);
+    D[4] = sub(a1112, a1314);
+    D[5] = sub(a1516, a1718);
+    // k = Dh / w, ie = w / f^eq = 1 / (1 + heq), kr = k ie
+    V k[Q], ie[Q], kr[Q];
+    k[0] = n[0];
+    ie[0] = map(add(one, heq[0]), frcp);
+    kr[0] = mul(k[0], ie[0]);
+    V A[9];
+    V hf = bc<V>(0.f), he = bc<V>(0.f), mf = bc<V>(0.f), me = bc<V>(0.f);
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const int i = 2 * p + 1;
+        const V Dp = D[p < 3 ? p : 3 + (p - 3) / 2];
+        const float ms = p < 3 ? -9.f : ((p - 3) % 2 == 1 ? 0.25f : -0.25f);  // -s / D
+        k[i] = fma(Dp, bc<V>(ms), n[i]);
+        k[i + 1] = fma(Dp, bc<V>(ms), n[i + 1]);
+        ie[i] = map(add(one, heq[i]), frcp);
+        ie[i + 1] = map(add(one, heq[i + 1]), frcp);
+        kr[i] = mul(k[i], ie[i]);
+        kr[i + 1] = mul(k[i + 1], ie[i + 1]);
+        A[p] = add(kr[i], kr[i + 1]);
+        const V hp = fma(kr[i + 1], k[i + 1], mul(kr[i], k[i]));
+        const V mp = fma(mu[i + 1], k[i + 1], mul(mu[i], k[i]));
+        if (p < 3) {
+            hf = p == 0 ? hp : add(hf, hp);
+            mf = p == 0 ? mp : add(mf, mp);
+        } else {
+            he = p == 3 ? hp : add(he, hp);
+            me = p == 3 ? mp : add(me, mp);
+        }
+    }
+    const V sf = fma(D[0], A[0], fma(D[1], A[1], mul(D[2], A[2])));
+    const V se = fma(D[3], sub(A[3], A[4]), fma(D[4], sub(A[5], A[6]), mul(D[5], sub(A[7], A[8]))));
+    const V sh = fma(bc<V>(0.5f), sf, mul(bc<V>(1.0f / 144.0f), se));
+    const V hh = fma(W0, mul(kr[0], k[0]), fma(W1, hf, mul(W2, he)));
+    const V mk = fma(W0, mul(mu[0], k[0]), fma(W1, mf, mul(W2, me)));  // mu . Dh
+    // ---- gamma and the coefficients of dgamma (R1 = mu.Dh / hh, R2 = sh / hh; zero where inactive)
+    const V ihh = map(hh, [](float x) { return x > kHHGuard ? rcp_approx(x) : 0.f; });
+    const V R2 = mul(sh, ihh);
+    const V R1 = mul(mk, ihh);
+    const V gamma = map(hh, R2, [a, b](float x, float r2) { return x > kHHGuard ? fma(-b, r2, a) : 2.0f; });
+    const V nbeta = mul(bc<V>(-0.5f * omega), gamma);
+    const V c1 = mul(bc<V>(0.5f * omega * b), R1);
+    const V c2 = mul(c1, mul(bc<V>(-1.f), R2));
+    const V tc2 = mul(bc<V>(2.f), c2);
+    const V nom = bc<V>(-omega);
+    // ---- coefficient vectors: gh, nq = -(geq) + r, dd = gs - gh (s_i = sd D_c per pair)
+    V gh[Q], ng[Q], dd[Q];
+    gh[0] = fma(nbeta, mu[0], mul(mul(tc2, k[0]), ie[0]));
+    ng[0] = mul(mul(kr[0], ie[0]), mul(c2, k[0]));
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const int i = 2 * p + 1;
+        const float sd = p < 3 ? 9.f : ((p - 3) % 2 == 1 ? -0.25f : 0.25f);  // s / D
+        const V c1s = mul(c1, mul(bc<V>(sd), D[p < 3 ? p : 3 + (p - 3) / 2]));
+#pragma unroll
+        for (int o = 0; o < 2; ++o) {
+            const int j = i + o;
+            const V gs = fma(c1, kr[j], mul(nom, mu[j]));
+            gh[j] = fma(nbeta, mu[j], mul(fma(tc2, k[j], c1s), ie[j]));
+            ng[j] = mul(mul(kr[j], ie[j]), fma(c2, k[j], c1s));
+            dd[j] = sub(gs, gh[j]);
+        }
+    }
+    // ---- r = A^T dd + gh through the adjoint second moments
+    const V F = add(add(add(dd[1], dd[2]), add(dd[3], dd[4])), add(dd[5], dd[6]));
+    const V nf6 = mul(bc<V>(-1.0f / 6.0f), F);
+    const V Pxx = fma(bc<V>(0.5f), add(dd[1], dd[2]), nf6);
+    const V Pyy = fma(bc<V>(0.5f), add(dd[3], dd[4]), nf6);
+    const V Pzz = fma(bc<V>(0.5f), add(dd[5], dd[6]), nf6);
+    const V Pxy = mul(bc<V>(0.25f), sub(add(dd[7], dd[8]), add(dd[9], dd[10])));
+    const V Pxz = mul(bc<V>(0.25f), sub(add(dd[11], dd[12]), add(dd[13], dd[14])));
+    const V Pyz = mul(bc<V>(0.25f), sub(add(dd[15], dd[16]), add(dd[17], dd[18])));
+    V r[Q];
+    r[0] = gh[0];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const int i = 2 * p + 1;
+        V at;
+        if (p == 0) at = Pxx;
+        else if (p == 1) at = Pyy;
+        else if (p == 2) at = Pzz;
+        else if (p < 5) at = p == 3 ? add(add(Pxx, Pyy), Pxy) : sub(add(Pxx, Pyy), Pxy);
+        else if (p < 7) at = p == 5 ? add(add(Pxx, Pzz), Pxz) : sub(add(Pxx, Pzz), Pxz);
+        else at = p == 7 ? add(add(Pyy, Pzz), Pyz) : sub(add(Pyy, Pzz), Pyz);
+        r[i] = add(at, gh[i]);
+        r[i + 1] = add(at, gh[i + 1]);
+    }
+    // ---- equilibrium chain: NQr = sum w nq e, NV = sum w nq (3c + 9 (c.u) c - 3u)
+    const V nq0 = add(ng[0], r[0]);
+    const V rinv3 = mul(bc<V>(3.f), rinv);
+    V qf = mul(nq0, add(one, heq[0]));  // rest term of NQr (weight applied below)
+    V ef = bc<V>(0.f), ee = bc<V>(0.f), sgf = bc<V>(0.f), sge = bc<V>(0.f);
+    V vf[3], vx = bc<V>(0.f), vy = bc<V>(0.f), vz = bc<V>(0.f);
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const int i = 2 * p + 1;
+        const V nqa = add(ng[i], r[i]), nqb = add(ng[i + 1], r[i + 1]);
+        const V ep = fma(nqb, add(one, heq[i + 1]), mul(nqa, add(one, heq[i])));
+        const V sg = add(nqa, nqb);
+        const V v = fma(sg, mul(c_dot(i, jx, jy, jz), rinv3), sub(nqa, nqb));
+        if (p < 3) {
+            ef = p == 0 ? ep : add(ef, ep);
+            sgf = p == 0 ? sg : add(sgf, sg);
+            vf[p] = v;
+        } else {
+            ee = p == 3 ? ep : add(ee, ep);
+            sge = p == 3 ? sg : add(sge, sg);
+            if (cx(i) > 0) vx = add(vx, v);
+            if (cy(i) > 0) vy = add(vy, v);
+            else if (cy(i) < 0) vy = sub(vy, v);
+            if (cz(i) > 0) vz = add(vz, v);
+            else if (cz(i) < 0) vz = sub(vz, v);
+        }
+    }
+    const V NQr = fma(W0, qf, fma(W1, ef, mul(W2, ee)));
+    const V Swnq = fma(W0, nq0, fma(W1, sgf, mul(W2, sge)));
+    const V nrinv = mul(bc<V>(-1.f), rinv);
+    const V NVx = mul(bc<V>(3.f), fma(mul(jx, nrinv), Swnq, fma(W1, vf[0], mul(W2, vx))));
+    const V NVy = mul(bc<V>(3.f), fma(mul(jy, nrinv), Swnq, fma(W1, vf[1], mul(W2, vy))));
+    const V NVz = mul(bc<V>(3.f), fma(mul(jz, nrinv), Swnq, fma(W1, vf[2], mul(W2, vz))));
+    // base = NV . u - NQr / rho,  u = j / rho
+    const V base = fma(rinv, fma(NVx, jx, fma(NVy, jy, mul(NVz, jz))), mul(NQr, nrinv));
+    lam[0] = add(add(mu[0], r[0]), base);
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const int i = 2 * p + 1;
+        const V cN = c_dot(i, NVx, NVy, NVz);
+        lam[i] = add(add(mu[i], r[i]), sub(base, cN));
+        lam[i + 1] = add(add(mu[i + 1], r[i + 1]), add(base, cN));
+    }
+}
+
 }  // namespace mclbm
