@@ -186,9 +186,15 @@ def ot_w1_lp(X, Y):
     for j in range(MB):
         A_eq[MA + j, j::MB] = 1.0
     b_eq = np.concatenate([np.full(MA, 1.0 / MA), np.full(MB, 1.0 / MB)])
-    res = linprog(C.ravel(), A_eq=A_eq, b_eq=b_eq, bounds=(0, None), method="highs")
+    # the solver's tolerances are absolute: solve with costs scaled to a unit maximum and
+    # tightened tolerances, then scale the optimum back
+    cmax = C.max()
+    if cmax == 0.0:
+        return 0.0
+    res = linprog(C.ravel() / cmax, A_eq=A_eq, b_eq=b_eq, bounds=(0, None), method="highs",
+                  options={"primal_feasibility_tolerance": 1e-10, "dual_feasibility_tolerance": 1e-10})
     assert res.status == 0
-    return float(res.fun)
+    return float(res.fun) * cmax
 
 
 def ot_w1_assignment(X, Y):
