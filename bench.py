@@ -211,6 +211,13 @@ def run_levels(args, precision):
     sfa = [e.sf_axes(3) for e in levels]
     w1 = [levels[k].w1(levels[k + 1]) for k in range(2)]
     stats_s = time.perf_counter() - t0
+    # two-point W1 between consecutive levels on the 8^3 grid (131328 point pairs; L = 64 and 32)
+    w12 = {}
+    for vector, key in ((True, "vector"), (False, "componentwise")):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        vals = [levels[k].w1_2pt(levels[k + 1], Q=8, vector=vector) for k in range(2)]
+        w12[key] = {"values": vals, "s": time.perf_counter() - t1}
     out = {
         "metric": "ensemble_glups", "value": lu / sec / 1e9, "unit": "GLUPS", "n_gpus": 1, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": sec / args.steps * 1e3, "higher_is_better": True,
@@ -221,7 +228,7 @@ def run_levels(args, precision):
                    "l2": "inputs larger than L2"},
         "roofline": {"kernel": KERNEL_NAMES[tuned[0]], "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "peak_kind": peak_kind, "traffic": None},
-        "stats_once_s": stats_s, "w1_consecutive_levels": w1,
+        "stats_once_s": stats_s, "w1_consecutive_levels": w1, "w1_2pt_consecutive_levels": w12,
         "spectrum_finite": bool(all(np.all(np.isfinite(x)) for x in spectra + sfa)),
         "clocks": clk.summary(),
     }

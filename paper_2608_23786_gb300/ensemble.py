@@ -162,5 +162,18 @@ class Ensemble:
         W = _m.mclbm_w1_1pt(self.ctx, other.ctx, Q, pp)
         return (W, pp) if per_point else W
 
+    def w1_2pt(self, other, Q=8, vector=True):
+        """Two-point W1 (W_{1,2}^v if vector, else the component-wise W_{1,2}) between the laws of
+        this ensemble and `other` on the common Q^3 restriction grid (mclbm_w1_2pt)."""
+        ua, ub = self.restrict(Q), other.restrict(Q)
+        G = Q**3
+        nb = _m.mclbm_w1_2pt_work_bytes(G, int(vector))
+        work = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        self._enter(work, ua, ub)
+        W = _m.mclbm_w1_2pt(ua.data_ptr(), self.M, ub.data_ptr(), other.M, G, int(vector), work.data_ptr(), nb,
+                            self.stream.cuda_stream)
+        self._exit()
+        return W
+
     def check_finite(self):
         _m.mclbm_check_finite(self.ctx)

@@ -77,6 +77,9 @@ _SIGNATURES = {
     "mclbm_w1_1pt": (_c.c_int, [_ctx_p, _ctx_p, _c.c_int32, _dp, _dp]),
     "mclbm_w1_work_bytes": (_c.c_size_t, [_c.c_int32, _c.c_int32, _c.c_int32]),
     "mclbm_w1_restricted": (_c.c_int, [_vp, _c.c_int32, _vp, _c.c_int32, _c.c_int32, _vp, _c.c_size_t, _vp, _dp, _dp]),
+    "mclbm_w1_2pt_work_bytes": (_c.c_size_t, [_c.c_int32, _c.c_int32]),
+    "mclbm_w1_2pt": (_c.c_int, [_vp, _c.c_int32, _vp, _c.c_int32, _c.c_int32, _c.c_int32, _vp, _c.c_size_t, _vp, _dp,
+                                _vp]),
     "mclbm_check_finite": (_c.c_int, [_ctx_p]),
     "mclbm_w1_restricted_noalloc": (_c.c_int, [_vp, _c.c_int32, _vp, _c.c_int32, _c.c_int32, _vp, _dp, _dp]),
     "mclbm_set_launch": (_c.c_int, [_ctx_p, _c.c_int32, _c.c_int32, _c.c_int32]),
@@ -274,6 +277,18 @@ def mclbm_w1_restricted(d_a, MA, d_b, MB, G, d_work, work_bytes, stream=0, per_p
     W = ctypes.c_double()
     _check(load().mclbm_w1_restricted(d_a, int(MA), d_b, int(MB), int(G), d_work, work_bytes, stream or None,
                                       ctypes.byref(W), _darr(per_point)))
+    return W.value
+
+
+def mclbm_w1_2pt_work_bytes(G, vector):
+    return load().mclbm_w1_2pt_work_bytes(int(G), int(vector))
+
+
+def mclbm_w1_2pt(d_a, MA, d_b, MB, G, vector, d_work, work_bytes, stream=0, d_per_pair=None):
+    """Two-point W1 (vector or component-wise) on restricted device fields; returns W."""
+    W = ctypes.c_double()
+    _check(load().mclbm_w1_2pt(d_a, int(MA), d_b, int(MB), int(G), int(vector), d_work, work_bytes, stream or None,
+                               ctypes.byref(W), d_per_pair or None))
     return W.value
 
 
