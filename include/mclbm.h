@@ -234,6 +234,17 @@ MCLBM_API size_t mclbm_w1_2pt_work_bytes(int32_t G, int32_t vector);
 MCLBM_API int mclbm_w1_2pt(const double* d_a, int32_t MA, const double* d_b, int32_t MB, int32_t G, int32_t vector,
                            void* d_work, size_t work_bytes, void* cuda_stream, double* W, double* d_per_pair);
 
+/* Sample convergence check, Eq. (sample_error): the ensemble-averaged relative L1 error
+ * (1/M) sum_m sum_k |u_m(x_k) - ref_m(x_k)| / sum_k |ref_m(x_k)| between paired samples (the
+ * same parameters at two resolutions) on the G restriction points.  d_u, d_ref: device FP64
+ * [M][G][3] (e.g. from mclbm_restrict).  out: host [4], the x, y, z components (absolute
+ * value) and the velocity vector (Euclidean norm).  d_work: >= mclbm_sample_error_work_bytes(M)
+ * bytes.  Runs on cuda_stream and synchronises it.  FP64, fixed reduction order.  Errors:
+ * INVALID_ARG, OOM (work buffer too small). */
+MCLBM_API size_t mclbm_sample_error_work_bytes(int32_t M);
+MCLBM_API int mclbm_sample_error(const double* d_u, const double* d_ref, int32_t M, int32_t G, void* d_work,
+                                 size_t work_bytes, void* cuda_stream, double* out);
+
 /* ---- launch shape and autotuning ------------------------------------------
  * kind 0: the direct stepper kernel updates `vec` consecutive nodes along x per
  * thread (vec-wide loads and stores, warp shuffles for the x-shifts) in blocks of

@@ -250,3 +250,18 @@ def w1_two_point(ua, ub, vector=True, per_pair=False):
                     total += w * D[k, c]
     total /= G * G
     return (total, D) if per_pair else total
+
+
+def sample_error(u, uref):
+    """Ensemble-averaged relative L1 error between paired samples on the restriction grid,
+    Eq. (sample_error): (1/M) sum_m sum_k |u_m(x_k) - uref_m(x_k)| / sum_k |uref_m(x_k)|, for
+    each velocity component (|.| the absolute value) and for the velocity vector (|.| the
+    Euclidean norm).  u, uref [M][G][3] (the same samples m at two resolutions).  Returns
+    [4]: x, y, z, vector."""
+    u = np.asarray(u, dtype=np.float64)
+    uref = np.asarray(uref, dtype=np.float64)
+    out = np.zeros(4)
+    for c in range(3):
+        out[c] = np.mean(np.abs(u[:, :, c] - uref[:, :, c]).sum(axis=1) / np.abs(uref[:, :, c]).sum(axis=1))
+    out[3] = np.mean(np.linalg.norm(u - uref, axis=2).sum(axis=1) / np.linalg.norm(uref, axis=2).sum(axis=1))
+    return out

@@ -175,5 +175,17 @@ class Ensemble:
         self._exit()
         return W
 
+    def sample_error(self, ref, Q=8):
+        """Eq. (sample_error) between this ensemble and `ref` (the same samples at another
+        resolution) on the common Q^3 grid: [4] for x, y, z and the vector (mclbm_sample_error)."""
+        u, ur = self.restrict(Q), ref.restrict(Q)
+        nb = _m.mclbm_sample_error_work_bytes(self.M)
+        work = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        self._enter(work, u, ur)
+        out = _m.mclbm_sample_error(u.data_ptr(), ur.data_ptr(), self.M, Q**3, work.data_ptr(), nb,
+                                    self.stream.cuda_stream)
+        self._exit()
+        return out
+
     def check_finite(self):
         _m.mclbm_check_finite(self.ctx)

@@ -78,6 +78,8 @@ _SIGNATURES = {
     "mclbm_w1_work_bytes": (_c.c_size_t, [_c.c_int32, _c.c_int32, _c.c_int32]),
     "mclbm_w1_restricted": (_c.c_int, [_vp, _c.c_int32, _vp, _c.c_int32, _c.c_int32, _vp, _c.c_size_t, _vp, _dp, _dp]),
     "mclbm_w1_2pt_work_bytes": (_c.c_size_t, [_c.c_int32, _c.c_int32]),
+    "mclbm_sample_error_work_bytes": (_c.c_size_t, [_c.c_int32]),
+    "mclbm_sample_error": (_c.c_int, [_vp, _vp, _c.c_int32, _c.c_int32, _vp, _c.c_size_t, _vp, _dp]),
     "mclbm_w1_2pt": (_c.c_int, [_vp, _c.c_int32, _vp, _c.c_int32, _c.c_int32, _c.c_int32, _vp, _c.c_size_t, _vp, _dp,
                                 _vp]),
     "mclbm_check_finite": (_c.c_int, [_ctx_p]),
@@ -290,6 +292,18 @@ def mclbm_w1_2pt(d_a, MA, d_b, MB, G, vector, d_work, work_bytes, stream=0, d_pe
     _check(load().mclbm_w1_2pt(d_a, int(MA), d_b, int(MB), int(G), int(vector), d_work, work_bytes, stream or None,
                                ctypes.byref(W), d_per_pair or None))
     return W.value
+
+
+def mclbm_sample_error_work_bytes(M):
+    return load().mclbm_sample_error_work_bytes(int(M))
+
+
+def mclbm_sample_error(d_u, d_ref, M, G, d_work, work_bytes, stream=0):
+    """Eq. (sample_error) on restricted device fields; returns [4] (x, y, z, vector)."""
+    import numpy as np
+    out = np.zeros(4)
+    _check(load().mclbm_sample_error(d_u, d_ref, int(M), int(G), d_work, work_bytes, stream or None, _darr(out)))
+    return out
 
 
 def mclbm_w1_restricted_noalloc(d_a, MA, d_b, MB, G, stream=0, per_point=None):

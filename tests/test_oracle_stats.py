@@ -204,3 +204,20 @@ def test_mean_var_two_samples_closed_form():
     mean, var = stats.mean_var(np.concatenate([a, b]))
     np.testing.assert_allclose(mean, 0.5 * (a[0] + b[0]), rtol=1e-15)
     np.testing.assert_allclose(var, 0.5 * (a[0] - b[0]) ** 2, rtol=1e-13)
+
+
+def test_sample_error_closed_forms():
+    """Eq. (sample_error): a field scaled by (1 + s) has relative L1 error |s| in every component
+    and in the vector norm; identical fields have error 0; the error is the mean of the
+    per-sample ratios."""
+    from oracle import stats as st
+    uref = gen.uniform(61, (5, 64, 3)) + 0.2
+    s = np.array([0.1, -0.3, 0.02, 0.5, -0.05])[:, None, None]
+    e = st.sample_error(uref * (1 + s), uref)
+    assert np.allclose(e, np.mean(np.abs(s)), rtol=1e-14)
+    assert np.all(st.sample_error(uref, uref) == 0.0)
+    u = uref.copy()
+    u[0, 3, 1] += 0.25  # one node of one sample in the y component
+    e = st.sample_error(u, uref)
+    assert abs(e[1] - 0.25 / np.abs(uref[0, :, 1]).sum() / 5) <= 1e-15
+    assert e[0] == 0.0 and e[2] == 0.0
