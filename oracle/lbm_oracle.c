@@ -7,19 +7,20 @@
  * the CUDA library: the velocity set is enumerated here from its definition
  * and every formula is written out in the paper's notation.
  *
- * The file is compiled twice: once with real_t = double (symbols orc_*) and
- * once with real_t = double complex (symbols orcz_*, -DORC_COMPLEX) so that
- * the complex-step derivative of any scalar of the whole simulation with
- * respect to the 24 uncertainty parameters can be taken through exactly the
- * same code.  Only +, -, *, / act on real_t values, so the complex build is
- * the analytic continuation of the real one.
+ * The file is compiled for two velocity sets (-DORC_Q=19: D3Q19, the paper's;
+ * -DORC_Q=27: D3Q27) and twice for each: once with real_t = double (symbols
+ * orc_* / orc27_*) and once with real_t = double complex (symbols orcz_* /
+ * orcz27_*, -DORC_COMPLEX) so that the complex-step derivative of any scalar
+ * of the whole simulation with respect to the 24 uncertainty parameters can be
+ * taken through exactly the same code.  Only +, -, *, / act on real_t values,
+ * so the complex build is the analytic continuation of the real one.
  *
  * Parity status: every function below is pinned by a CPU test (lattice
  * moments, equilibrium moments, shear part vs. the moment-space definition,
  * fixed points, conservation, closed-form gamma vs. a bisection root,
  * units vs. Table "params2", initial energy closed form, shear-wave decay).
  *
- * Layout of a population field: f[m][i][z][y][x], m < M samples, i < 19
+ * Layout of a population field: f[m][i][z][y][x], m < M samples, i < Q
  * velocities in this file's own enumeration order, n = N*N*N nodes with x
  * fastest.  The stored state at integer time t is the pre-collision one.
  */
@@ -27,40 +28,69 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifndef ORC_Q
+#define ORC_Q 19
+#endif
+#if ORC_Q == 19
+#define PFX_R orc_
+#define PFX_C orcz_
+#elif ORC_Q == 27
+#define PFX_R orc27_
+#define PFX_C orcz27_
+#else
+#error "ORC_Q must be 19 or 27"
+#endif
+#define CAT2(a, b) a##b
+#define CAT(a, b) CAT2(a, b)
+/* RSYM: real-only entry points; SYM: entry points of both arithmetic twins */
+#define RSYM(name) CAT(PFX_R, name)
 #ifdef ORC_COMPLEX
 #include <complex.h>
 typedef double complex real_t;
-#define SYM(name) orcz_##name
+#define SYM(name) CAT(PFX_C, name)
 #define RE(v) creal(v)
 #else
 typedef double real_t;
-#define SYM(name) orc_##name
+#define SYM(name) CAT(PFX_R, name)
 #define RE(v) (v)
 #endif
 
-#define Q 19
+#define Q ORC_Q
 
-/* ---- D3Q19 velocity set (Sec. "Entropic multi-relaxation lattice Boltzmann
- * scheme"): the 19 vectors of {-1,0,1}^3 with |c|^2 <= 2.  Weights are the
- * usual ones, w = 1/3, 1/18, 1/36 for |c|^2 = 0, 1, 2; c_s^2 = 1/3. ---- */
+/* ---- Velocity set.  D3Q19 (Sec. "Entropic multi-relaxation lattice Boltzmann
+ * scheme"): the 19 vectors of {-1,0,1}^3 with |c|^2 <= 2, weights 1/3, 1/18, 1/36
+ * for |c|^2 = 0, 1, 2.  D3Q27: all 27 vectors of {-1,0,1}^3, weights 8/27, 2/27,
+ * 1/54, 1/216 for |c|^2 = 0, 1, 2, 3 (the tensor product of the D1Q3 weights
+ * 2/3, 1/6).  c_s^2 = 1/3 for both. ---- */
 static int C[Q][3];
 static double W[Q];
 static int OPP[Q];
 static int lattice_ready = 0;
 
+static double shell_weight(int shell)
+{
+#if ORC_Q == 19
+    static const double w[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
+#else
+    static const double w[4] = {8.0 / 27.0, 2.0 / 27.0, 1.0 / 54.0, 1.0 / 216.0};
+#endif
+    return w[shell];
+}
+
 static void build_lattice(void)
 {
     if (lattice_ready) return;
     int q = 0;
-    /* rest, then faces, then edges; within each shell a fixed scan order */
-    for (int shell = 0; shell <= 2; ++shell)
+    const int max_shell = Q == 19 ? 2 : 3;
+    /* rest, then faces, edges (and corners); within each shell a fixed scan order */
+    for (int shell = 0; shell <= max_shell; ++shell)
         for (int cz = -1; cz <= 1; ++cz)
             for (int cy = -1; cy <= 1; ++cy)
                 for (int cx = -1; cx <= 1; ++cx) {
                     int n2 = cx * cx + cy * cy + cz * cz;
                     if (n2 != shell) continue;
                     C[q][0] = cx; C[q][1] = cy; C[q][2] = cz;
-                    W[q] = shell == 0 ? 1.0 / 3.0 : (shell == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+                    W[q] = shell_weight(shell);
                     ++q;
                 }
     for (int i = 0; i < Q; ++i)
@@ -72,7 +102,7 @@ static void build_lattice(void)
 static const double CS2 = 1.0 / 3.0;
 
 #ifndef ORC_COMPLEX
-void orc_lattice(int *c, double *w, int *opp)
+void RSYM(lattice)(int *c, double *w, int *opp)
 {
     build_lattice();
     for (int i = 0; i < Q; ++i) {
@@ -88,7 +118,7 @@ void orc_lattice(int *c, double *w, int *opp)
  *   nu_phys = U_c l_c / Re (l_c = 1),  nu_lat = nu_phys dt / dx^2,
  *   omega_nu = 2 c_s^2 / (2 nu_lat + c_s^2),  tau = 1 / omega_nu.
  * out = {dx, U_lat, dt, nu_lat, tau, omega_nu}. */
-void orc_units(int N, double Re, double Ma, double Uc, double *out)
+void RSYM(units)(int N, double Re, double Ma, double Uc, double *out)
 {
     const double pi = 3.14159265358979323846;
     double dx = 2.0 * pi / N;
@@ -129,11 +159,13 @@ void SYM(node_moments)(const real_t *f, real_t *rho, real_t *u)
 /* Shear part of the non-equilibrium populations (Sec. "Entropic
  * multi-relaxation", Table "frequencySummary"): the populations that carry
  * exactly the deviatoric raw second moments D_ab = P_ab - delta_ab tr(P)/3 of
- * f^neq (the shear tensors N and Pi) and nothing else of the D3Q19 moment
- * basis.  Written out per velocity class:
+ * f^neq (the shear tensors N and Pi) and nothing else of the lattice's raw
+ * moment basis (for D3Q27 the 27 products c_x^a c_y^b c_z^c, a, b, c <= 2).
+ * Written out per velocity class:
  *   rest:                      0
  *   face  +-e_a:               D_aa / 2
- *   edge  s e_a + l e_b:       s l P_ab / 4.                                */
+ *   edge  s e_a + l e_b:       s l P_ab / 4
+ *   corner (D3Q27):            0.                                            */
 void SYM(shear_part)(const real_t *fneq, real_t *ds)
 {
     build_lattice();
@@ -151,11 +183,13 @@ void SYM(shear_part)(const real_t *fneq, real_t *ds)
         } else if (n2 == 1) {
             int a = C[i][0] ? 0 : (C[i][1] ? 1 : 2);
             ds[i] = 0.5 * (P[a][a] - tr / 3.0);
-        } else {
+        } else if (n2 == 2) {
             int a = -1, b = -1;
             for (int k = 0; k < 3; ++k)
                 if (C[i][k]) { if (a < 0) a = k; else b = k; }
             ds[i] = 0.25 * C[i][a] * C[i][b] * P[a][b];
+        } else {
+            ds[i] = 0;
         }
     }
 }
@@ -342,7 +376,7 @@ void SYM(energy)(int N, int M, const real_t *u, double ulat, double uc, real_t *
 #ifndef ORC_COMPLEX
 /* Global relative entropy, Eqs. (relEntropy1), (relEntropy2):
  * H_rel = eps^3 sum_x sum_i [f_i ln(f_i/w_i) - f_i + w_i], eps = 2 pi / N. */
-double orc_hrel(int N, int M, const double *f)
+double RSYM(hrel)(int N, int M, const double *f)
 {
     build_lattice();
     const double pi = 3.14159265358979323846;

@@ -1,8 +1,10 @@
 """NumPy front end of the C oracle stepper (test infrastructure only).
 
 Arrays are C-contiguous float64 (or complex128 for the complex-step twin).
-Population fields are [M][19][N][N][N] (x fastest) in the oracle's own
-velocity order, which ``lattice()`` reports.
+Population fields are [M][Q][N][N][N] (x fastest, Q = 19 for D3Q19, the paper's
+velocity set, or 27 for D3Q27) in the oracle's own velocity order, which
+``lattice(Q)`` reports.  Functions taking a population field infer Q from it;
+the others take ``lattice=19`` or ``27``.
 """
 import ctypes
 
@@ -24,17 +26,18 @@ def _arr(a, cplx=False):
     return np.ascontiguousarray(a, dtype=dt)
 
 
-def _fn(name, cplx=False):
+def _fn(name, cplx=False, lattice=19):
+    assert lattice in (19, 27)
     lib = load_oracle()
-    return getattr(lib, ("orcz_" if cplx else "orc_") + name)
+    return getattr(lib, ("orcz" if cplx else "orc") + ("27_" if lattice == 27 else "_") + name)
 
 
-def lattice():
-    """(c [19,3] int, w [19] float64, opp [19] int) of the oracle's D3Q19 set."""
-    c = np.zeros((19, 3), dtype=np.int32)
-    w = np.zeros(19)
-    opp = np.zeros(19, dtype=np.int32)
-    load_oracle().orc_lattice(c.ctypes.data_as(_ip), _ptr(w, np.float64), opp.ctypes.data_as(_ip))
+def lattice(lattice=19):
+    """(c [Q,3] int, w [Q] float64, opp [Q] int) of the oracle's D3Q19 or D3Q27 set."""
+    c = np.zeros((lattice, 3), dtype=np.int32)
+    w = np.zeros(lattice)
+    opp = np.zeros(lattice, dtype=np.int32)
+    _fn("lattice", lattice=lattice)(c.ctypes.data_as(_ip), _ptr(w, np.float64), opp.ctypes.data_as(_ip))
     return c.astype(np.int64), w, opp.astype(np.int64)
 
 
@@ -47,11 +50,11 @@ def units(N, Re, Ma, Uc=1.0):
     return dict(zip(("dx", "ulat", "dt", "nu_lat", "tau", "omega"), out.tolist()))
 
 
-def equilibrium(rho, u):
+def equilibrium(rho, u, lattice=19):
     """f^eq(rho, u) of Eq. (equilibrium), real arguments."""
     u = _arr(u)
-    feq = np.zeros(19)
-    fn = _fn("equilibrium")
+    feq = np.zeros(lattice)
+    fn = _fn("equilibrium", lattice=lattice)
     fn.argtypes = [ctypes.c_double, _dp, _dp]
     fn(float(rho), _ptr(u, np.float64), _ptr(feq, np.float64))
     return feq
@@ -59,8 +62,8 @@ def equilibrium(rho, u):
 
 def shear_part(fneq):
     fneq = _arr(fneq)
-    ds = np.zeros(19)
-    _fn("shear_part")(_ptr(fneq, np.float64), _ptr(ds, np.float64))
+    ds = np.zeros(len(fneq))
+    _fn("shear_part", lattice=len(fneq))(_ptr(fneq, np.float64), _ptr(ds, np.float64))
     return ds
 
 
@@ -68,25 +71,26 @@ def collide(f, omega, cplx=False):
     """One-node KBC collision: returns (f*, gamma, Ds, Dh)."""
     f = _arr(f, cplx)
     dt = f.dtype
-    fs = np.zeros(19, dtype=dt)
-    ds = np.zeros(19, dtype=dt)
-    dh = np.zeros(19, dtype=dt)
+    q = len(f)
+    fs = np.zeros(q, dtype=dt)
+    ds = np.zeros(q, dtype=dt)
+    dh = np.zeros(q, dtype=dt)
     g = np.zeros(1, dtype=dt)
-    fn = _fn("collide", cplx)
+    fn = _fn("collide", cplx, q)
     fn.argtypes = [_dp, ctypes.c_double, _dp, _dp, _dp, _dp]
     fn(_ptr(f, dt), float(omega), _ptr(fs, dt), _ptr(g, dt), _ptr(ds, dt), _ptr(dh, dt))
     return fs, g[0], ds, dh
 
 
-def init_ensemble(N, params, ulat, uc=1.0, density_mode=0, M=None, cplx=False):
-    """Equilibrium-initialised RTGV ensemble [M][19][N][N][N]; params [M][24] or None."""
+def init_ensemble(N, params, ulat, uc=1.0, density_mode=0, M=None, cplx=False, lattice=19):
+    """Equilibrium-initialised RTGV ensemble [M][Q][N][N][N]; params [M][24] or None."""
     dt = np.complex128 if cplx else np.float64
     if params is not None:
         params = _arr(params, cplx).reshape(-1, 24)
         M = params.shape[0]
     assert M is not None
-    f = np.zeros((M, 19, N, N, N), dtype=dt)
-    fn = _fn("init", cplx)
+    f = np.zeros((M, lattice, N, N, N), dtype=dt)
+    fn = _fn("init", cplx, lattice)
     fn.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp]
     fn(int(N), int(M), None if params is None else _ptr(params, dt), float(ulat), float(uc), int(density_mode),
        _ptr(f, dt))
@@ -97,10 +101,10 @@ def step(f, omega, with_gamma=False):
     """Advance f (modified in place) by one stream+collide step; optionally return gamma [M][N^3]."""
     cplx = f.dtype == np.complex128
     M, q, N = f.shape[0], f.shape[1], f.shape[2]
-    assert q == 19 and f.flags["C_CONTIGUOUS"]
+    assert q in (19, 27) and f.flags["C_CONTIGUOUS"]
     scratch = np.empty_like(f)
     g = np.zeros((M, N * N * N), dtype=f.dtype) if with_gamma else None
-    fn = _fn("step", cplx)
+    fn = _fn("step", cplx, q)
     fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp]
     fn(int(N), int(M), float(omega), _ptr(f, f.dtype), _ptr(scratch, f.dtype),
        None if g is None else _ptr(g, f.dtype))
@@ -112,7 +116,7 @@ def run(f, omega, nsteps):
     cplx = f.dtype == np.complex128
     M, N = f.shape[0], f.shape[2]
     scratch = np.empty_like(f)
-    fn = _fn("run", cplx)
+    fn = _fn("run", cplx, f.shape[1])
     fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, _dp]
     fn(int(N), int(M), float(omega), int(nsteps), _ptr(f, f.dtype), _ptr(scratch, f.dtype))
     return f
@@ -124,7 +128,7 @@ def moments(f):
     M, N = f.shape[0], f.shape[2]
     rho = np.zeros((M, N, N, N), dtype=f.dtype)
     u = np.zeros((M, 3, N, N, N), dtype=f.dtype)
-    fn = _fn("moments", cplx)
+    fn = _fn("moments", cplx, f.shape[1])
     fn.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
     fn(int(N), int(M), _ptr(f, f.dtype), _ptr(rho, f.dtype), _ptr(u, f.dtype))
     return rho, u
@@ -147,13 +151,13 @@ def hrel(f):
     """Global relative entropy H_rel, Eq. (relEntropy2)."""
     f = _arr(f)
     M, N = f.shape[0], f.shape[2]
-    fn = load_oracle().orc_hrel
+    fn = _fn("hrel", lattice=f.shape[1])
     fn.argtypes = [ctypes.c_int, ctypes.c_int, _dp]
     fn.restype = ctypes.c_double
     return fn(int(N), int(M), _ptr(f, np.float64))
 
 
-def complex_step_grad(N, params, ulat, omega, nsteps, objective="energy", h=1e-30, uc=1.0):
+def complex_step_grad(N, params, ulat, omega, nsteps, objective="energy", h=1e-30, uc=1.0, lattice=19):
     """d J / d X (J = mean kinetic energy or enstrophy of each sample at step nsteps)
     by complex-step differentiation of the whole oracle: J(X + i h e_k) has imaginary
     part h dJ/dX_k to machine precision.  Returns [M][24]."""
@@ -163,7 +167,7 @@ def complex_step_grad(N, params, ulat, omega, nsteps, objective="energy", h=1e-3
     for k in range(24):
         p = params.astype(np.complex128)
         p[:, k] += 1j * h
-        f = init_ensemble(N, p, ulat, uc, cplx=True)
+        f = init_ensemble(N, p, ulat, uc, cplx=True, lattice=lattice)
         run(f, omega, nsteps)
         _, u = moments(f)
         E, Z = energy(u, ulat, uc)
