@@ -27,6 +27,8 @@
 //   Pi_dd = (v_{+d} + v_{-d})/2 - (sum over faces v)/6,  Pi_ab = (sum over ab edges s l v)/4,
 //   (A^T v)_j = sum_d Pi_dd c_jd^2 + sum_{a<b} Pi_ab c_ja c_jb.
 #pragma once
+#include <type_traits>
+
 #include "collide.cuh"
 
 namespace mclbm {
@@ -81,12 +83,14 @@ __device__ __forceinline__ void kbc_vjp(const T (&h)[Q], const T (&mu)[Q], T ome
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int n2 = norm2(i);
-        if (n2 == 0) s[i] = 0;
-        else if (n2 == 1) s[i] = T(9) * ((cx(i) ? pxx : (cy(i) ? pyy : pzz)) - tr3);
+        // normalised shear part s = Ds / w: D_aa / (2 w) on faces, s l P_ab / (4 w) on edges,
+        // 0 at rest and on (D3Q27) corners
+        if (n2 == 0 || n2 == 3) s[i] = 0;
+        else if (n2 == 1) s[i] = T(0.5) * inv_weight<T>(i) * ((cx(i) ? pxx : (cy(i) ? pyy : pzz)) - tr3);
         else {
             const T p = (cz(i) == 0) ? pxy : ((cy(i) == 0) ? pxz : pyz);
             const int sg = (cz(i) == 0) ? cx(i) * cy(i) : ((cy(i) == 0) ? cx(i) * cz(i) : cy(i) * cz(i));
-            s[i] = sg > 0 ? T(9) * p : -T(9) * p;
+            s[i] = (sg > 0 ? T(0.25) : -T(0.25)) * inv_weight<T>(i) * p;
         }
     }
     T sh = 0, hh = 0, mk = 0;
@@ -175,6 +179,7 @@ __device__ __forceinline__ void kbc_vjp(const T (&h)[Q], const T (&mu)[Q], T ome
     }
 }
 
+#ifndef MCLBM_D3Q27
 // The same product for the FP32 path in the lane form of collide.cuh (V = float for one node,
 // float2 for two nodes in the packed FP32x2 instructions), with opposite velocities paired:
 // the pair shares s, c_i c_i^T and the even part of the equilibrium, so A^T v, the
@@ -363,5 +368,39 @@ __device__ __forceinline__ void kbc_vjp_shifted(const V (&h)[Q], const V (&mu)[Q
         lam[i + 1] = add(add(mu[i + 1], r[i + 1]), add(base, cN));
     }
 }
+
+#else  // MCLBM_D3Q27
+
+// D3Q27: the FP32 path applies the generic product node by node (the paired form above is
+// written for the D3Q19 pair structure).
+template <class V>
+__device__ __forceinline__ void kbc_vjp_shifted(const V (&h)[Q], const V (&mu)[Q], float omega, float a, float b,
+                                                V (&lam)[Q])
+{
+    (void)a;
+    (void)b;
+    if constexpr (std::is_same<V, float>::value) {
+        kbc_vjp<float>(h, mu, omega, kHHGuard, lam);
+    } else {
+        float h1[Q], m1[Q], l1[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            h1[i] = h[i].x;
+            m1[i] = mu[i].x;
+        }
+        kbc_vjp<float>(h1, m1, omega, kHHGuard, l1);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            lam[i].x = l1[i];
+            h1[i] = h[i].y;
+            m1[i] = mu[i].y;
+        }
+        kbc_vjp<float>(h1, m1, omega, kHHGuard, l1);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) lam[i].y = l1[i];
+    }
+}
+
+#endif  // MCLBM_D3Q27
 
 }  // namespace mclbm

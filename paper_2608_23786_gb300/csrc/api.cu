@@ -113,9 +113,9 @@ int validate(const mclbm_config* cfg, mclbm_units* u)
 // 4 nodes per thread; FP64 (bound by the FP64 units): the direct kernel.
 LaunchConfig default_launch(int precision, int pattern)
 {
-    if (precision == MCLBM_FP64) return LaunchConfig{2, 128, 0};
+    if (precision == MCLBM_FP64) return LaunchConfig{kVecF64[sizeof(kVecF64) / sizeof(int) - 1], 128, 0};
     if (precision == MCLBM_FP32) return LaunchConfig{2, 128, 3};
-    return pattern == MCLBM_PULL ? LaunchConfig{8, 128, 4} : LaunchConfig{4, 128, 3};
+    return pattern == MCLBM_PULL && kAsyncKinds ? LaunchConfig{8, 128, 4} : LaunchConfig{4, 128, 3};
 }
 
 int set_error(int code, const std::string& msg)
@@ -177,7 +177,7 @@ static size_t w1_region_bytes(int M)
 
 extern "C" {
 
-const char* mclbm_version(void) { return "mclbm 0.1.0 (D3Q19 KBC, sm_103a)"; }
+const char* mclbm_version(void) { return "mclbm 0.1.0 (" MCLBM_LATTICE_NAME " KBC, sm_103a)"; }
 
 const char* mclbm_last_error(void) { return g_last_error.c_str(); }
 

@@ -66,7 +66,7 @@ __host__ __device__ __forceinline__ T kbc_raw(T (&f)[Q], T omega)
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int n2 = norm2(i);
-        if (n2 == 0) ds[i] = 0;
+        if (n2 == 0 || n2 == 3) ds[i] = 0;  // rest and (D3Q27) corners carry no shear
         else if (n2 == 1) ds[i] = T(0.5) * ((cx(i) ? pxx : (cy(i) ? pyy : pzz)) - tr3);
         else {
             const T p = (cz(i) == 0) ? pxy : ((cy(i) == 0) ? pxz : pyz);
@@ -199,6 +199,10 @@ template <class V>
 __device__ __forceinline__ V c_dot(int i, V jx, V jy, V jz)
 {
     using namespace lanes;
+    if (cx(i) != 0 && cy(i) != 0 && cz(i) != 0) {  // corner (D3Q27)
+        const V t = cy(i) > 0 ? add(jx, jy) : sub(jx, jy);
+        return cz(i) > 0 ? add(t, jz) : sub(t, jz);
+    }
     if (cx(i) == 0 && cy(i) == 0) return jz;
     if (cx(i) == 0) return cz(i) == 0 ? jy : (cz(i) > 0 ? add(jy, jz) : sub(jy, jz));
     if (cy(i) != 0) return cy(i) > 0 ? add(jx, jy) : sub(jx, jy);
@@ -206,6 +210,7 @@ __device__ __forceinline__ V c_dot(int i, V jx, V jy, V jz)
     return jx;
 }
 
+#ifndef MCLBM_D3Q27
 // KBC on normalised deviations h_i = f_i / w_i - 1 (in place), FP32, one node (V = float)
 // or two (V = float2).  a = 2/omega and b = 2 - 2/omega are passed in (computed once on the
 // host); the reciprocals 1/rho, 1/(1 + heq_i) and 1/hh are the hardware approximation (one
@@ -312,5 +317,137 @@ __device__ __forceinline__ V kbc_shifted(V (&h)[Q], float omega, float a, float 
     }
     return gamma;
 }
+
+#else  // MCLBM_D3Q27
+
+// D3Q27 form of kbc_shifted: the same operations written over the 13 opposite pairs by
+// velocity class (faces, edges, corners).  The shear part is D_aa / 2 on faces, s l P_ab / 4
+// on edges and 0 on corners; normalised by the weights, s = D_aa / (2 w1) and
+// s l P_ab / (4 w2).  P_ab includes the corners.
+template <class V>
+__device__ __forceinline__ V kbc_shifted(V (&h)[Q], float omega, float a, float b)
+{
+    using namespace lanes;
+    constexpr int NP = (Q - 1) / 2;
+    const V one = bc<V>(1.f), zero = bc<V>(0.f);
+    const auto frcp = [](float x) { return rcp_approx(x); };
+    V S[4] = {zero, zero, zero, zero};   // sum of h per class (1 faces, 2 edges, 3 corners)
+    V J[4][3];                           // sum of c h per class and axis
+#pragma unroll
+    for (int k = 0; k < 4; ++k) J[k][0] = J[k][1] = J[k][2] = zero;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const int i = 2 * p + 1, k = norm2(i);
+        S[k] = add(S[k], add(h[i], h[i + 1]));
+        const V d = sub(h[i], h[i + 1]);
+        if (cx(i) > 0) J[k][0] = add(J[k][0], d);
+        if (cy(i) > 0) J[k][1] = add(J[k][1], d);
+        else if (cy(i) < 0) J[k][1] = sub(J[k][1], d);
+        if (cz(i) > 0) J[k][2] = add(J[k][2], d);
+        else if (cz(i) < 0) J[k][2] = sub(J[k][2], d);
+    }
+    const V W0 = bc<V>(weight<float>(0)), W1 = bc<V>(weight<float>(1)), W2 = bc<V>(weight<float>(7)),
+            W3 = bc<V>(weight<float>(19));
+    const V drho = fma(W0, h[0], fma(W1, S[1], fma(W2, S[2], mul(W3, S[3]))));
+    const V rho = add(one, drho);
+    V j3[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) j3[c] = fma(W1, J[1][c], fma(W2, J[2][c], mul(W3, J[3][c])));
+    const V jx = j3[0], jy = j3[1], jz = j3[2];
+    const V rinv = map(rho, frcp);
+    const V jj15 = mul(bc<V>(-1.5f), fma(jx, jx, fma(jy, jy, mul(jz, jz))));
+    V heq[Q], n[Q];
+    heq[0] = fma(jj15, rinv, drho);
+    n[0] = sub(h[0], heq[0]);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const int i = 2 * p + 1;
+        const V cj = c_dot(i, jx, jy, jz);
+        const V q = fma(rinv, fma(bc<V>(4.5f), mul(cj, cj), jj15), drho);
+        heq[i] = fma(bc<V>(3.f), cj, q);
+        heq[i + 1] = fma(bc<V>(-3.f), cj, q);
+        n[i] = sub(h[i], heq[i]);
+        n[i + 1] = sub(h[i + 1], heq[i + 1]);
+    }
+    // second moments of f^neq (normalised): P_ab = sum w c_a c_b n, by class
+    V Pd[4][3], Po[4][3];  // diagonal (aa) and off-diagonal (xy, xz, yz) partial sums
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Pd[k][c] = Po[k][c] = zero;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const int i = 2 * p + 1, k = norm2(i);
+        const V s2 = add(n[i], n[i + 1]);
+        if (cx(i) != 0) Pd[k][0] = add(Pd[k][0], s2);
+        if (cy(i) != 0) Pd[k][1] = add(Pd[k][1], s2);
+        if (cz(i) != 0) Pd[k][2] = add(Pd[k][2], s2);
+        const int sxy = cx(i) * cy(i), sxz = cx(i) * cz(i), syz = cy(i) * cz(i);
+        if (sxy > 0) Po[k][0] = add(Po[k][0], s2);
+        else if (sxy < 0) Po[k][0] = sub(Po[k][0], s2);
+        if (sxz > 0) Po[k][1] = add(Po[k][1], s2);
+        else if (sxz < 0) Po[k][1] = sub(Po[k][1], s2);
+        if (syz > 0) Po[k][2] = add(Po[k][2], s2);
+        else if (syz < 0) Po[k][2] = sub(Po[k][2], s2);
+    }
+    V Pdd[3], Pod[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        Pdd[c] = fma(W1, Pd[1][c], fma(W2, Pd[2][c], mul(W3, Pd[3][c])));
+        Pod[c] = fma(W2, Po[2][c], mul(W3, Po[3][c]));
+    }
+    const V tr3 = mul(add(add(Pdd[0], Pdd[1]), Pdd[2]), bc<V>(1.0f / 3.0f));
+    // shear part normalised by w, per pair: faces D_aa / (2 w1), edges s l P_ab / (4 w2)
+    const float cf = 0.5f * inv_weight<float>(1), ce = 0.25f * inv_weight<float>(7);
+    V sp[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const int i = 2 * p + 1, k = norm2(i);
+        if (k == 1) {
+            const int c = cx(i) ? 0 : (cy(i) ? 1 : 2);
+            sp[p] = mul(bc<V>(cf), sub(Pdd[c], tr3));
+        } else if (k == 2) {
+            const int c = cz(i) == 0 ? 0 : (cy(i) == 0 ? 1 : 2);
+            const int sg = c == 0 ? cx(i) * cy(i) : (c == 1 ? cx(i) * cz(i) : cy(i) * cz(i));
+            sp[p] = mul(bc<V>(sg > 0 ? ce : -ce), Pod[c]);
+        } else {
+            sp[p] = zero;
+        }
+    }
+    // k = n - s;  <Ds|Dh> = sum w s k / (1 + heq),  <Dh|Dh> = sum w k^2 / (1 + heq)
+    V k[Q];
+    k[0] = n[0];
+    const V kr0 = mul(k[0], map(add(one, heq[0]), frcp));
+    V HH[4] = {zero, zero, zero, zero}, SH[4] = {zero, zero, zero, zero};
+    HH[0] = mul(kr0, k[0]);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const int i = 2 * p + 1, cl = norm2(i);
+        k[i] = sub(n[i], sp[p]);
+        k[i + 1] = sub(n[i + 1], sp[p]);
+        const V ka = mul(k[i], map(add(one, heq[i]), frcp));
+        const V kb = mul(k[i + 1], map(add(one, heq[i + 1]), frcp));
+        HH[cl] = fma(kb, k[i + 1], fma(ka, k[i], HH[cl]));
+        if (cl < 3) SH[cl] = fma(sp[p], add(ka, kb), SH[cl]);
+    }
+    const V hh = fma(W0, HH[0], fma(W1, HH[1], fma(W2, HH[2], mul(W3, HH[3]))));
+    const V sh = fma(W1, SH[1], mul(W2, SH[2]));
+    const V gamma = map(hh, sh, [a, b](float hs, float ss) {
+        return hs <= kHHGuard ? 2.0f : fma(-b, mul(ss, rcp_approx(hs)), a);
+    });
+    // f* = f^eq + (1 - omega) Ds + (1 - beta) Dh
+    const V omb = fma(bc<V>(-0.5f * omega), gamma, one);
+    const V om1 = bc<V>(1.0f - omega);
+    h[0] = fma(omb, k[0], heq[0]);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const int i = 2 * p + 1;
+        h[i] = fma(omb, k[i], fma(om1, sp[p], heq[i]));
+        h[i + 1] = fma(omb, k[i + 1], fma(om1, sp[p], heq[i + 1]));
+    }
+    return gamma;
+}
+
+#endif  // MCLBM_D3Q27
 
 }  // namespace mclbm

@@ -20,10 +20,29 @@ struct LaunchConfig {
                    // storage, block 128; packed collision for even vec)
 };
 
-// Variants compiled per element type (nodes per thread; VEC * sizeof(E) <= 16 bytes).
+// Variants compiled per element type (nodes per thread; VEC * sizeof(E) <= 16 bytes).  The
+// D3Q27 build compiles a reduced set (its collision is heavier to compile and the shapes
+// measured fastest for D3Q19 carry over): no shared-memory ring kinds and one AA kernel for
+// both parities.
+#ifdef MCLBM_D3Q27
+#define MCLBM_VECS_F64 1
+#define MCLBM_VECS_F32 2
+#define MCLBM_VECS_F16 4
+constexpr int kVecF64[] = {1};
+constexpr int kVecF32[] = {2};
+constexpr int kVecF16[] = {4};
+constexpr bool kAsyncKinds = false;        // kinds 4 and 5
+constexpr bool kParitySpecialised = false;  // AA kernels per parity
+#else
+#define MCLBM_VECS_F64 1, 2
+#define MCLBM_VECS_F32 1, 2, 4
+#define MCLBM_VECS_F16 2, 4, 8
 constexpr int kVecF64[] = {1, 2};
 constexpr int kVecF32[] = {1, 2, 4};
 constexpr int kVecF16[] = {2, 4, 8};
+constexpr bool kAsyncKinds = true;
+constexpr bool kParitySpecialised = true;
+#endif
 constexpr int kBlocks[] = {128, 256};
 
 template <class E>

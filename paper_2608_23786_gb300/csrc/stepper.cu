@@ -271,7 +271,7 @@ bool launch_supported(int precision, const LaunchConfig& c)
     if (c.kind == 1) return c.vec == 1 || c.vec == 2;
     if (c.kind < 0 || c.kind > 5 || c.kind == 1 || (c.block != 128 && c.block != 256)) return false;
     if (c.kind == 3 && (precision == MCLBM_FP64 || c.vec % 2 != 0)) return false;
-    if (c.kind >= 4 && (precision == MCLBM_FP64 || c.block != 128)) return false;
+    if (c.kind >= 4 && (!kAsyncKinds || precision == MCLBM_FP64 || c.block != 128)) return false;
     return vec_supported(precision, c.vec);
 }
 

@@ -5,7 +5,7 @@ namespace mclbm {
 
 cudaError_t launch_batch_f16_aa(const BatchArgs<__half>& a, const LaunchConfig& c, int grid_cap, cudaStream_t s, int* occ)
 {
-    return launch_vec_block<__half, 1, 2, 4, 8>(a, c, grid_cap, s, occ);
+    return launch_vec_block<__half, 1, MCLBM_VECS_F16>(a, c, grid_cap, s, occ);
 }
 
 cudaError_t launch_staged_f16_aa(StagedArgs<__half>& a, const LaunchConfig& c, int grid_cap, cudaStream_t s)

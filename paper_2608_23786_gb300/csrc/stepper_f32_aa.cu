@@ -5,7 +5,7 @@ namespace mclbm {
 
 cudaError_t launch_batch_f32_aa(const BatchArgs<float>& a, const LaunchConfig& c, int grid_cap, cudaStream_t s, int* occ)
 {
-    return launch_vec_block<float, 1, 1, 2, 4>(a, c, grid_cap, s, occ);
+    return launch_vec_block<float, 1, MCLBM_VECS_F32>(a, c, grid_cap, s, occ);
 }
 
 cudaError_t launch_staged_f32_aa(StagedArgs<float>& a, const LaunchConfig& c, int grid_cap, cudaStream_t s)

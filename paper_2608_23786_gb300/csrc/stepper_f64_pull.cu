@@ -5,7 +5,7 @@ namespace mclbm {
 
 cudaError_t launch_batch_f64_pull(const BatchArgs<double>& a, const LaunchConfig& c, int grid_cap, cudaStream_t s, int* occ)
 {
-    return launch_vec_block<double, 0, 1, 2>(a, c, grid_cap, s, occ);
+    return launch_vec_block<double, 0, MCLBM_VECS_F64>(a, c, grid_cap, s, occ);
 }
 
 cudaError_t launch_staged_f64_pull(StagedArgs<double>& a, const LaunchConfig& c, int grid_cap, cudaStream_t s)

@@ -58,6 +58,8 @@ cudaError_t launch_prefetch_variant(const BatchArgs<E>& a, int grid_cap, cudaStr
 {
     if constexpr (PATTERN == 0) {
         return launch_prefetch_fixed<E, VEC, 0, BLOCK, 0, PACK>(a, grid_cap, s, occ);
+    } else if constexpr (!kParitySpecialised) {
+        return launch_prefetch_fixed<E, VEC, 1, BLOCK, -1, PACK>(a, grid_cap, s, occ);
     } else {
         bool all_even = true, all_odd = true;
         for (int l = 0; l < a.nlev; ++l) {
@@ -95,21 +97,14 @@ cudaError_t launch_async_fixed(const BatchArgs<E>& a, int grid_cap, cudaStream_t
     return cudaGetLastError();
 }
 
+// The ring kernels take the parity at run time for AA (one kernel for both parities).
 template <class E, int VEC, int PATTERN, int BLOCK, int STAGES>
 cudaError_t launch_async_variant(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, int* occ)
 {
-    if constexpr (PATTERN == 0) {
+    if constexpr (PATTERN == 0)
         return launch_async_fixed<E, VEC, 0, BLOCK, 0, STAGES>(a, grid_cap, s, occ);
-    } else {
-        bool all_even = true, all_odd = true;
-        for (int l = 0; l < a.nlev; ++l) {
-            all_even = all_even && a.lev[l].parity == 0;
-            all_odd = all_odd && a.lev[l].parity == 1;
-        }
-        if (all_even) return launch_async_fixed<E, VEC, 1, BLOCK, 1, STAGES>(a, grid_cap, s, occ);
-        if (all_odd) return launch_async_fixed<E, VEC, 1, BLOCK, 2, STAGES>(a, grid_cap, s, occ);
+    else
         return launch_async_fixed<E, VEC, 1, BLOCK, -1, STAGES>(a, grid_cap, s, occ);
-    }
 }
 
 template <class E, int PATTERN, int... VECS>
@@ -140,7 +135,7 @@ cudaError_t launch_vec_block(const BatchArgs<E>& a, const LaunchConfig& cfg, int
                 e = cudaErrorInvalidConfiguration;
             }
         } else if (cfg.kind == 4 || cfg.kind == 5) {
-            if constexpr (Storage<E>::shifted) {
+            if constexpr (Storage<E>::shifted && kAsyncKinds) {
                 if (cfg.block != 128)
                     e = cudaErrorInvalidConfiguration;
                 else if (cfg.kind == 4)

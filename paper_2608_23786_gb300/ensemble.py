@@ -10,16 +10,17 @@ from . import mclbm as _m
 
 
 class Ensemble:
-    """M RTGV samples on an N^3 periodic D3Q19 lattice at viscosity nu = 1/Re.
+    """M RTGV samples on an N^3 periodic lattice at viscosity nu = 1/Re.
 
-    precision: "fp64" | "fp32" | "fp16"; pattern: "pull" | "aa".
+    precision: "fp64" | "fp32" | "fp16"; pattern: "pull" | "aa"; lattice: 19 (D3Q19, the
+    paper's velocity set, libmclbm.so) or 27 (D3Q27, libmclbm_d3q27.so).
     """
 
     PREC = {"fp64": _m.FP64, "fp32": _m.FP32, "fp16": _m.FP16}
     PAT = {"pull": _m.PULL, "aa": _m.AA}
 
     def __init__(self, N, M, Re=None, nu=None, Ma=None, dt=0.0, precision="fp32", pattern="pull", seed=1,
-                 width=0.025, U_c=1.0, init_density=0, device=None, stream=None):
+                 width=0.025, U_c=1.0, init_density=0, device=None, stream=None, lattice=19):
         if not torch.cuda.is_available():
             raise RuntimeError("Ensemble needs a CUDA device (there is no CPU path)")
         if nu is None:
@@ -30,7 +31,8 @@ class Ensemble:
                              init_density=init_density, reserved=0)
         self.N, self.M = N, M
         self.precision, self.pattern = precision, pattern
-        pop_bytes, work_bytes = _m.mclbm_required_bytes(self.cfg)
+        self.Q = self.lattice = lattice
+        pop_bytes, work_bytes = _m.mclbm_required_bytes(self.cfg, lattice=lattice)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         with torch.cuda.device(self.device):
             self.pop = torch.empty(pop_bytes + 256, dtype=torch.uint8, device=self.device)
@@ -44,7 +46,7 @@ class Ensemble:
         self._work_ptr = (self.work.data_ptr() + 255) // 256 * 256
         with torch.cuda.device(self.device):
             self.ctx = _m.mclbm_create(self.cfg, self._pop_ptr, pop_bytes, self._work_ptr, work_bytes,
-                                       self.stream.cuda_stream)
+                                       self.stream.cuda_stream, lattice=lattice)
         self.units = _m.mclbm_get_units(self.ctx).as_dict()
 
     def __del__(self):
@@ -98,8 +100,8 @@ class Ensemble:
 
     # ---- fields ----------------------------------------------------------------
     def populations(self, sample=0):
-        """Pre-collision f [19][N][N][N] (FP64, library velocity order) as a CUDA tensor."""
-        out = torch.empty((19, self.N, self.N, self.N), dtype=torch.float64, device=self.device)
+        """Pre-collision f [Q][N][N][N] (FP64, library velocity order) as a CUDA tensor."""
+        out = torch.empty((self.Q, self.N, self.N, self.N), dtype=torch.float64, device=self.device)
         self._enter(out)
         _m.mclbm_get_populations(self.ctx, sample, out.data_ptr())
         self._exit()

@@ -8,6 +8,7 @@ library is missing this module raises on first use.
 """
 import ctypes
 import os
+import threading
 
 from . import build as _build
 
@@ -104,33 +105,52 @@ _SIGNATURES = {
     "mclbm_batch_autotune": (_c.c_int, [_vp, _c.c_int32, _i32p, _i32p, _i32p, _dp]),
 }
 
-_lib = None
+_libs = {}  # lattice (19 or 27) -> loaded library
+_owner = {}  # context / batch handle value -> lattice of the library that created it
+_tls = threading.local()  # library of the calling thread's last call (for mclbm_last_error)
 
 
-def library_path():
-    return _build.LIB
+def library_path(lattice=19):
+    return _build.LATTICE_LIBS[lattice]
 
 
-def load(build_if_missing=False):
-    """Load libmclbm.so from the package's _build directory (raises if it is missing)."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    path = library_path()
-    if not os.path.exists(path):
-        if build_if_missing:
-            _build.build()
-        else:
-            raise RuntimeError(
-                f"libmclbm.so not found at {path}; build it with paper_2608_23786_gb300.build.build() "
-                "(the CUDA library is required: there is no CPU fallback)")
-    lib = ctypes.CDLL(path)
-    for name, (res, args) in _SIGNATURES.items():
-        fn = getattr(lib, name)
-        fn.restype = res
-        fn.argtypes = args
-    _lib = lib
+def load(build_if_missing=False, lattice=19):
+    """Load the in-tree library for the velocity set: libmclbm.so (D3Q19, default) or
+    libmclbm_d3q27.so (D3Q27).  Raises if it is missing (there is no CPU fallback)."""
+    if lattice not in _build.LATTICE_LIBS:
+        raise ValueError("lattice must be 19 or 27")
+    lib = _libs.get(lattice)
+    if lib is None:
+        path = library_path(lattice)
+        if not os.path.exists(path):
+            if build_if_missing:
+                _build.build()
+            else:
+                raise RuntimeError(
+                    f"{os.path.basename(path)} not found at {path}; build it with "
+                    "paper_2608_23786_gb300.build.build() (the CUDA library is required: there is no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _libs[lattice] = lib
+    _tls.lib = lib
     return lib
+
+
+def _value(h):
+    return h.value if isinstance(h, _c.c_void_p) else h
+
+
+def lattice_of(h):
+    """Velocity set (19 or 27) of the library that created a context or batch handle."""
+    return _owner.get(_value(h), 19)
+
+
+def _L(h):
+    """Library that owns handle h (a context or a batch)."""
+    return load(lattice=lattice_of(h))
 
 
 def declared_symbols():
@@ -140,7 +160,8 @@ def declared_symbols():
 
 def _check(code):
     if code != MCLBM_OK:
-        raise MclbmError(code, load().mclbm_last_error().decode())
+        lib = getattr(_tls, "lib", None) or load()
+        raise MclbmError(code, lib.mclbm_last_error().decode())
     return code
 
 
@@ -155,19 +176,21 @@ def _darr(a):
 
 # ---- same-named wrappers ------------------------------------------------------
 
-def mclbm_version():
-    return load().mclbm_version().decode()
+def mclbm_version(lattice=19):
+    return load(lattice=lattice).mclbm_version().decode()
 
 
 def mclbm_last_error():
-    return load().mclbm_last_error().decode()
+    lib = getattr(_tls, "lib", None) or load()
+    return lib.mclbm_last_error().decode()
 
 
-def mclbm_lattice():
+def mclbm_lattice(lattice=19):
+    """(c [Q][3], w [Q]) of the library for the velocity set (Q = lattice)."""
     import numpy as np
-    c = np.zeros((Q, 3), dtype=np.int32)
-    w = np.zeros(Q)
-    _check(load().mclbm_lattice(c.ctypes.data_as(_i32p), _darr(w)))
+    c = np.zeros((lattice, 3), dtype=np.int32)
+    w = np.zeros(lattice)
+    _check(load(lattice=lattice).mclbm_lattice(c.ctypes.data_as(_i32p), _darr(w)))
     return c, w
 
 
@@ -177,32 +200,34 @@ def mclbm_compute_units(cfg):
     return u
 
 
-def mclbm_required_bytes(cfg):
+def mclbm_required_bytes(cfg, lattice=19):
     pop = ctypes.c_size_t()
     work = ctypes.c_size_t()
-    _check(load().mclbm_required_bytes(ctypes.byref(cfg), ctypes.byref(pop), ctypes.byref(work)))
+    _check(load(lattice=lattice).mclbm_required_bytes(ctypes.byref(cfg), ctypes.byref(pop), ctypes.byref(work)))
     return pop.value, work.value
 
 
-def mclbm_create(cfg, d_pop, pop_bytes, d_work, work_bytes, stream=0):
+def mclbm_create(cfg, d_pop, pop_bytes, d_work, work_bytes, stream=0, lattice=19):
     ctx = _ctx_p()
-    _check(load().mclbm_create(ctypes.byref(cfg), d_pop, pop_bytes, d_work, work_bytes, stream or None,
-                               ctypes.byref(ctx)))
+    _check(load(lattice=lattice).mclbm_create(ctypes.byref(cfg), d_pop, pop_bytes, d_work, work_bytes,
+                                              stream or None, ctypes.byref(ctx)))
+    _owner[ctx.value] = lattice
     return ctx
 
 
 def mclbm_destroy(ctx):
-    load().mclbm_destroy(ctx)
+    _L(ctx).mclbm_destroy(ctx)
+    _owner.pop(_value(ctx), None)
 
 
 def mclbm_get_units(ctx):
     u = Units()
-    _check(load().mclbm_get_units(ctx, ctypes.byref(u)))
+    _check(_L(ctx).mclbm_get_units(ctx, ctypes.byref(u)))
     return u
 
 
 def mclbm_init_ensemble(ctx, params=None):
-    _check(load().mclbm_init_ensemble(ctx, _darr(params)))
+    _check(_L(ctx).mclbm_init_ensemble(ctx, _darr(params)))
 
 
 def mclbm_draw_params(seed, first_sample, M, width=0.025):
@@ -213,61 +238,61 @@ def mclbm_draw_params(seed, first_sample, M, width=0.025):
 
 
 def mclbm_init_tgv(ctx):
-    _check(load().mclbm_init_tgv(ctx))
+    _check(_L(ctx).mclbm_init_tgv(ctx))
 
 
 def mclbm_get_params(ctx, out):
-    _check(load().mclbm_get_params(ctx, _darr(out)))
+    _check(_L(ctx).mclbm_get_params(ctx, _darr(out)))
     return out
 
 
 def mclbm_step(ctx, nsteps):
-    _check(load().mclbm_step(ctx, int(nsteps)))
+    _check(_L(ctx).mclbm_step(ctx, int(nsteps)))
 
 
 def mclbm_steps_taken(ctx):
-    return load().mclbm_steps_taken(ctx)
+    return _L(ctx).mclbm_steps_taken(ctx)
 
 
 def mclbm_get_populations(ctx, sample, d_out):
-    _check(load().mclbm_get_populations(ctx, int(sample), d_out))
+    _check(_L(ctx).mclbm_get_populations(ctx, int(sample), d_out))
 
 
 def mclbm_set_populations(ctx, sample, d_in):
-    _check(load().mclbm_set_populations(ctx, int(sample), d_in))
+    _check(_L(ctx).mclbm_set_populations(ctx, int(sample), d_in))
 
 
 def mclbm_moments(ctx, sample, d_rho, d_u):
-    _check(load().mclbm_moments(ctx, int(sample), d_rho, d_u))
+    _check(_L(ctx).mclbm_moments(ctx, int(sample), d_rho, d_u))
 
 
 def mclbm_energy(ctx, E, Z=None):
-    _check(load().mclbm_energy(ctx, _darr(E), _darr(Z)))
+    _check(_L(ctx).mclbm_energy(ctx, _darr(E), _darr(Z)))
 
 
 def mclbm_mean_var(ctx, d_mean, d_var):
-    _check(load().mclbm_mean_var(ctx, d_mean, d_var))
+    _check(_L(ctx).mclbm_mean_var(ctx, d_mean, d_var))
 
 
 def mclbm_spectrum(ctx, E):
-    _check(load().mclbm_spectrum(ctx, _darr(E)))
+    _check(_L(ctx).mclbm_spectrum(ctx, _darr(E)))
 
 
 def mclbm_sf_trace(ctx, S2):
-    _check(load().mclbm_sf_trace(ctx, _darr(S2)))
+    _check(_L(ctx).mclbm_sf_trace(ctx, _darr(S2)))
 
 
 def mclbm_sf_axes(ctx, pmax, S):
-    _check(load().mclbm_sf_axes(ctx, int(pmax), _darr(S)))
+    _check(_L(ctx).mclbm_sf_axes(ctx, int(pmax), _darr(S)))
 
 
 def mclbm_restrict(ctx, Qd, d_out):
-    _check(load().mclbm_restrict(ctx, int(Qd), d_out))
+    _check(_L(ctx).mclbm_restrict(ctx, int(Qd), d_out))
 
 
 def mclbm_w1_1pt(ctxA, ctxB, Qd, per_point=None):
     W = ctypes.c_double()
-    _check(load().mclbm_w1_1pt(ctxA, ctxB, int(Qd), ctypes.byref(W), _darr(per_point)))
+    _check(_L(ctxA).mclbm_w1_1pt(ctxA, ctxB, int(Qd), ctypes.byref(W), _darr(per_point)))
     return W.value
 
 
@@ -316,72 +341,78 @@ def mclbm_w1_restricted_noalloc(d_a, MA, d_b, MB, G, stream=0, per_point=None):
 
 
 def mclbm_check_finite(ctx):
-    _check(load().mclbm_check_finite(ctx))
+    _check(_L(ctx).mclbm_check_finite(ctx))
 
 
 def mclbm_set_launch(ctx, vec, block=256, kind=0):
-    _check(load().mclbm_set_launch(ctx, int(kind), int(vec), int(block)))
+    _check(_L(ctx).mclbm_set_launch(ctx, int(kind), int(vec), int(block)))
 
 
 def mclbm_get_launch(ctx):
     """(kind, vec, block) of the context's stepper launch."""
     k, v, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
-    _check(load().mclbm_get_launch(ctx, ctypes.byref(k), ctypes.byref(v), ctypes.byref(b)))
+    _check(_L(ctx).mclbm_get_launch(ctx, ctypes.byref(k), ctypes.byref(v), ctypes.byref(b)))
     return k.value, v.value, b.value
 
 
 def mclbm_autotune(ctx, trial_steps=5):
     """Returns (kind, vec, block, ms per step) of the fastest shape."""
     k, v, b, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
-    _check(load().mclbm_autotune(ctx, int(trial_steps), ctypes.byref(k), ctypes.byref(v), ctypes.byref(b),
+    _check(_L(ctx).mclbm_autotune(ctx, int(trial_steps), ctypes.byref(k), ctypes.byref(v), ctypes.byref(b),
                                  ctypes.byref(ms)))
     return k.value, v.value, b.value, ms.value
 
 
 def mclbm_device_status(ctx):
-    _check(load().mclbm_device_status(ctx))
+    _check(_L(ctx).mclbm_device_status(ctx))
 
 
 def mclbm_batch_create(ctxs, substeps):
     n = len(ctxs)
+    lat = {lattice_of(c) for c in ctxs}
+    if len(lat) != 1:
+        raise ValueError("a batch takes contexts of one velocity set")
     arr = (_ctx_p * n)(*[c.value if isinstance(c, _ctx_p) else c for c in ctxs])
     sub = (ctypes.c_int32 * n)(*[int(s) for s in substeps])
     out = _vp()
-    _check(load().mclbm_batch_create(arr, n, sub, ctypes.byref(out)))
+    lattice = lat.pop()
+    _check(load(lattice=lattice).mclbm_batch_create(arr, n, sub, ctypes.byref(out)))
+    _owner[out.value] = lattice
     return out
 
 
 def mclbm_batch_destroy(b):
-    load().mclbm_batch_destroy(b)
+    _L(b).mclbm_batch_destroy(b)
+    _owner.pop(_value(b), None)
 
 
 def mclbm_batch_set_graph(b, enable):
-    _check(load().mclbm_batch_set_graph(b, int(bool(enable))))
+    _check(_L(b).mclbm_batch_set_graph(b, int(bool(enable))))
 
 
 def mclbm_batch_set_launch(b, vec, block=256, kind=0):
-    _check(load().mclbm_batch_set_launch(b, int(kind), int(vec), int(block)))
+    _check(_L(b).mclbm_batch_set_launch(b, int(kind), int(vec), int(block)))
 
 
 def mclbm_batch_step(b, macro_steps):
-    _check(load().mclbm_batch_step(b, int(macro_steps)))
+    _check(_L(b).mclbm_batch_step(b, int(macro_steps)))
 
 
 def mclbm_batch_macro_steps(b):
-    return load().mclbm_batch_macro_steps(b)
+    return _L(b).mclbm_batch_macro_steps(b)
 
 
 def mclbm_batch_autotune(b, trials=2):
     """Returns (kind, vec, block, ms per macro step) of the fastest shape."""
     k, v, blk, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
-    _check(load().mclbm_batch_autotune(b, int(trials), ctypes.byref(k), ctypes.byref(v), ctypes.byref(blk),
+    _check(_L(b).mclbm_batch_autotune(b, int(trials), ctypes.byref(k), ctypes.byref(v), ctypes.byref(blk),
                                        ctypes.byref(ms)))
     return k.value, v.value, blk.value, ms.value
 
 
 def mclbm_grad_required_bytes(ctx, nsteps, ckpt_every):
     b = ctypes.c_size_t()
-    _check(load().mclbm_grad_required_bytes(ctx, int(nsteps), int(ckpt_every), ctypes.byref(b)))
+    _check(_L(ctx).mclbm_grad_required_bytes(ctx, int(nsteps), int(ckpt_every), ctypes.byref(b)))
     return b.value
 
 
@@ -390,29 +421,29 @@ def mclbm_grad(ctx, objective, nsteps, ckpt_every, d_buf, buf_bytes, M):
     import numpy as np
     J = np.zeros(M)
     G = np.zeros((M, 24))
-    _check(load().mclbm_grad(ctx, int(objective), int(nsteps), int(ckpt_every), d_buf, buf_bytes, _darr(J), _darr(G)))
+    _check(_L(ctx).mclbm_grad(ctx, int(objective), int(nsteps), int(ckpt_every), d_buf, buf_bytes, _darr(J), _darr(G)))
     return J, G
 
 
 def mclbm_adjoint_step(ctx, d_f, d_lambda_next, d_lambda):
-    _check(load().mclbm_adjoint_step(ctx, d_f, d_lambda_next, d_lambda))
+    _check(_L(ctx).mclbm_adjoint_step(ctx, d_f, d_lambda_next, d_lambda))
 
 
 def mclbm_grad_timing(ctx):
     """ms of the phases of the last mclbm_grad: forward, recompute, reverse, parameter reduction."""
     import numpy as np
     out = np.zeros(4)
-    _check(load().mclbm_grad_timing(ctx, _darr(out)))
+    _check(_L(ctx).mclbm_grad_timing(ctx, _darr(out)))
     return out
 
 
 def mclbm_selftest_timeout(ctx):
-    _check(load().mclbm_selftest_timeout(ctx))
+    _check(_L(ctx).mclbm_selftest_timeout(ctx))
 
 
 def mclbm_save(ctx, path):
-    _check(load().mclbm_save(ctx, os.fsencode(path)))
+    _check(_L(ctx).mclbm_save(ctx, os.fsencode(path)))
 
 
 def mclbm_load(ctx, path):
-    _check(load().mclbm_load(ctx, os.fsencode(path)))
+    _check(_L(ctx).mclbm_load(ctx, os.fsencode(path)))

@@ -5,18 +5,19 @@ import oracle
 from paper_2608_23786_gb300 import mclbm
 
 
-def lib_to_oracle_perm():
+def lib_to_oracle_perm(lattice=19):
     """perm[i] = oracle index of the library's velocity i (matched by the velocity vector)."""
-    c_lib, _ = mclbm.mclbm_lattice()
-    c_orc, _, _ = oracle.lattice()
-    return np.array([int(np.where((c_orc == c_lib[i]).all(1))[0][0]) for i in range(19)])
+    c_lib, _ = mclbm.mclbm_lattice(lattice)
+    c_orc, _, _ = oracle.lattice(lattice)
+    return np.array([int(np.where((c_orc == c_lib[i]).all(1))[0][0]) for i in range(lattice)])
 
 
 def lib_populations(ens):
-    """All samples' pre-collision populations in the oracle's velocity order, [M][19][N][N][N]."""
-    perm = lib_to_oracle_perm()
+    """All samples' pre-collision populations in the oracle's velocity order, [M][Q][N][N][N]."""
+    q = getattr(ens, "lattice", 19)
+    perm = lib_to_oracle_perm(q)
     inv = np.argsort(perm)
-    out = np.empty((ens.M, 19, ens.N, ens.N, ens.N))
+    out = np.empty((ens.M, q, ens.N, ens.N, ens.N))
     for m in range(ens.M):
         f = ens.populations(m).cpu().numpy()
         out[m] = f[inv]
@@ -25,7 +26,7 @@ def lib_populations(ens):
 
 def oracle_to_lib(f_orc):
     """One sample's populations from oracle order to library order."""
-    return f_orc[lib_to_oracle_perm()]
+    return f_orc[lib_to_oracle_perm(len(f_orc))]
 
 
 def rel_l2(a, b):

@@ -104,3 +104,19 @@ def test_philox_draw_matches_numpy_philox(lib):
         B = gen.draw_params(seed, 9)
         np.testing.assert_array_equal(A, B)
         np.testing.assert_array_equal(mclbm.mclbm_draw_params(seed, 4, 3), B[4:7])
+
+
+def test_d3q27_library_exports_the_same_abi(lib):
+    """libmclbm_d3q27.so: the same entry points, the D3Q27 set (matching the oracle's), and
+    27 populations per node in the sizes."""
+    lib27 = mclbm.load(lattice=27)
+    for name in _declared():
+        assert hasattr(lib27, name), name
+    c, w = mclbm.mclbm_lattice(27)
+    co, wo, _ = oracle.lattice(27)
+    assert {tuple(v): wi for v, wi in zip(c.tolist(), w)} == {tuple(v): wi for v, wi in zip(co.tolist(), wo)}
+    for i in range(1, 27, 2):
+        assert (c[i] == -c[i + 1]).all()
+    pop, _ = mclbm.mclbm_required_bytes(_cfg(N=64, M=8, precision=mclbm.FP32, pattern=mclbm.PULL), lattice=27)
+    assert pop == 2 * 27 * 4 * 64**3 * 8
+    assert "D3Q27" in mclbm.mclbm_version(27) and "D3Q19" in mclbm.mclbm_version()
