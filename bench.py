@@ -111,7 +111,7 @@ def oracle_sample(wl, budget_s=10.0, max_samples=2):
     import ensemble_inputs as gen
     un = oracle.units(wl["N"], wl["Re"], wl["Ma"])
     X = gen.draw_params(wl["seed"], max_samples)
-    f = oracle.init_ensemble(wl["N"], X, un["ulat"])
+    f = oracle.init_ensemble(wl["N"], X, un["ulat"], lattice=wl.get("lattice", 19))
     lu, steps = 0, 0
     t0 = time.perf_counter()
     while time.perf_counter() - t0 < budget_s:
@@ -358,6 +358,8 @@ def main():
                     help="ensemble64 (default): 64^3 x 64 FP32; levels_*: 3-level batch; large: 512^3 x 4 FP16 AA; "
                          "adjoint: gradient of E(T), 64^3 x 16, 500 steps")
     ap.add_argument("--T", type=int, default=500, help="adjoint horizon (steps) of --workload adjoint")
+    ap.add_argument("--lattice", type=int, default=19, choices=[19, 27],
+                    help="velocity set of the ensemble64 workload: 19 (D3Q19, the paper's) or 27 (D3Q27)")
     args = ap.parse_args()
     if args.workload.startswith("levels"):
         return run_levels(args, args.workload.split("_")[1])
@@ -376,6 +378,9 @@ def main():
         wl["pattern"] = args.pattern
     if args.precision or args.pattern:
         wl["name"] = f"rtgv_64cube_x64_{wl['precision']}_{wl['pattern']}"
+    wl["lattice"] = args.lattice
+    if args.lattice == 27:
+        wl["name"] += "_d3q27"
     if args.impl == "reference":
         return run_reference(args, wl)
 
@@ -398,7 +403,7 @@ def main():
     # each rank owns an independent ensemble: samples rank*M .. rank*M + M - 1 of the Philox stream
     X = gen.draw_params(wl["seed"], wl["M"], first_sample=rank * wl["M"])
     ens = Ensemble(wl["N"], wl["M"], Re=wl["Re"], Ma=wl["Ma"], precision=wl["precision"], pattern=wl["pattern"],
-                   seed=wl["seed"], device=dev, stream=stream).init(X)
+                   seed=wl["seed"], device=dev, stream=stream, lattice=wl["lattice"]).init(X)
     # launch shape: the library default, an explicit one, or the autotuner's pick on this ensemble
     # (the autotuner restores the initial state)
     if args.launch:
@@ -490,7 +495,7 @@ def main():
     plain_glups = None
     if not args.no_e2e:
         plain = Ensemble(wl["N"], 1, Re=wl["Re"], Ma=wl["Ma"], precision="fp64", pattern="pull", device=dev,
-                         stream=stream).init(X[:1])
+                         stream=stream, lattice=wl["lattice"]).init(X[:1])
         plain.step(5)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -507,7 +512,7 @@ def main():
     if not args.no_e2e:
         T4, K4, M4 = 500, 50, 16
         ens4 = Ensemble(64, M4, Re=wl["Re"], Ma=wl["Ma"], precision="fp32", pattern="pull", device=dev,
-                        stream=stream).init(X[:M4])
+                        stream=stream, lattice=wl["lattice"]).init(X[:M4])
         need = mclbm.mclbm_grad_required_bytes(ens4.ctx, T4, K4)
         gbuf = torch.empty(need + 256, dtype=torch.uint8, device=dev)
         gptr = (gbuf.data_ptr() + 255) // 256 * 256
@@ -519,14 +524,14 @@ def main():
         grad_s = time.perf_counter() - t0
         ph = mclbm.mclbm_grad_timing(ens4.ctx)
         lu4 = M4 * 64**3 * T4
-        adj_bytes = 3 * 19 * 4 * lu4  # read state + read lambda + write lambda per update
+        adj_bytes = 3 * wl["lattice"] * 4 * lu4  # read state + read lambda + write lambda per update
         adjoint = {"workload": "rtgv_64cube_x16_fp32_500steps_ckpt50", "objective": "E(T)",
                    "value": lu4 / grad_s / 1e9, "unit": "GLUPS (whole gradient: forward + recompute + reverse)",
                    "phases_ms": {"forward": ph[0], "recompute": ph[1], "reverse": ph[2], "reduction": ph[3]},
                    "reverse_glups": lu4 / (ph[2] / 1e3) / 1e9,
                    "reverse_achieved_gbs": adj_bytes / (ph[2] / 1e3) / 1e9,
                    "reverse_frac_of_hbm": adj_bytes / (ph[2] / 1e3) / 1e9 / measured_peaks()[0]["hbm_gbs"],
-                   "algorithmic_bytes_per_lu_reverse": 3 * 19 * 4,
+                   "algorithmic_bytes_per_lu_reverse": 3 * wl["lattice"] * 4,
                    "grad_finite": bool(np.all(np.isfinite(G4)))}
         del gbuf, ens4
 
@@ -535,11 +540,12 @@ def main():
             dist.destroy_process_group()
         return
     peaks, peak_kind = measured_peaks()
-    bpl = BYTES_PER_LU[wl["precision"]] * wl["M"] * wl["N"] ** 3
+    bpl = BYTES_PER_LU[wl["precision"]] * wl["lattice"] // 19 * wl["M"] * wl["N"] ** 3
     achieved = bpl / stepper_s / 1e9
     digest = stepper_digest()
     traffic = (NCU_TRAFFIC["bytes_per_launch"]
                if NCU_TRAFFIC["sha256"] == digest and tuple(tuned[:3]) == NCU_TRAFFIC["launch"] and wl["M"] == 64
+               and wl["lattice"] == 19
                and wl["N"] == 64 and wl["precision"] == "fp32" and wl["pattern"] == "pull" else None)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -551,8 +557,9 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if wl["precision"] == "fp32" else
         ("f16-storage/f32" if wl["precision"] == "fp16" else "f64"), "data": "synthetic",
         "config": {"workload": wl["name"], "N": wl["N"], "M_per_gpu": wl["M"], "Re": wl["Re"], "Ma": wl["Ma"],
-                   "storage": wl["precision"], "streaming": wl["pattern"], "updates_per_step": S,
-                   "reductions_per_step": ["E_m(t)", "mean/var fields"], "l2": f"inputs ({BYTES_PER_LU[wl['precision']] * wl['M'] * wl['N'] ** 3 / 1e9:.2f} GB moved per update) "
+                   "lattice": f"D3Q{wl['lattice']}", "storage": wl["precision"], "streaming": wl["pattern"],
+                   "updates_per_step": S,
+                   "reductions_per_step": ["E_m(t)", "mean/var fields"], "l2": f"inputs ({bpl / 1e9:.2f} GB moved per update) "
                          "larger than the 129 MB L2: no flush",
                    "launch": {"kind": KINDS[tuned[0]], "vec": tuned[1], "block": tuned[2],
                               "chosen_by": "explicit" if args.launch else ("autotuner" if args.autotune else "default")}},

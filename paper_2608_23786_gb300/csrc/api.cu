@@ -108,14 +108,22 @@ int validate(const mclbm_config* cfg, mclbm_units* u)
 }  // namespace
 
 // Default launch shape: the fastest measured on a GB300 for the 64^3 x 64 and 128^3 x 32
-// ensembles (the autotuner may pick another).  FP32: packed collision, 2 nodes per thread;
-// FP16 pull: shared-memory prefetch ring, 8 nodes per thread; FP16 AA: packed collision,
-// 4 nodes per thread; FP64 (bound by the FP64 units): the direct kernel.
+// ensembles (the autotuner may pick another).  D3Q19: FP32 packed collision, 2 nodes per
+// thread; FP16 pull shared-memory prefetch ring, 8 nodes per thread; FP16 AA packed
+// collision, 4 nodes per thread; FP64 (bound by the FP64 units) the direct kernel.
 LaunchConfig default_launch(int precision, int pattern)
 {
-    if (precision == MCLBM_FP64) return LaunchConfig{kVecF64[sizeof(kVecF64) / sizeof(int) - 1], 128, 0};
+#ifdef MCLBM_D3Q27
+    // D3Q27 (measured): FP32 prefetching kernel (pull: one-node collision, AA: packed); FP16
+    // pull the direct kernel, AA the prefetching one
+    if (precision == MCLBM_FP64) return LaunchConfig{1, 128, 0};
+    if (precision == MCLBM_FP32) return pattern == MCLBM_PULL ? LaunchConfig{2, 128, 2} : LaunchConfig{2, 128, 3};
+    return pattern == MCLBM_PULL ? LaunchConfig{4, 128, 0} : LaunchConfig{4, 128, 2};
+#else
+    if (precision == MCLBM_FP64) return LaunchConfig{2, 128, 0};
     if (precision == MCLBM_FP32) return LaunchConfig{2, 128, 3};
-    return pattern == MCLBM_PULL && kAsyncKinds ? LaunchConfig{8, 128, 4} : LaunchConfig{4, 128, 3};
+    return pattern == MCLBM_PULL ? LaunchConfig{8, 128, 4} : LaunchConfig{4, 128, 3};
+#endif
 }
 
 int set_error(int code, const std::string& msg)

@@ -21,9 +21,8 @@ struct LaunchConfig {
 };
 
 // Variants compiled per element type (nodes per thread; VEC * sizeof(E) <= 16 bytes).  The
-// D3Q27 build compiles a reduced set (its collision is heavier to compile and the shapes
-// measured fastest for D3Q19 carry over): no shared-memory ring kinds and one AA kernel for
-// both parities.
+// D3Q27 build compiles a reduced set (its collision is heavier to compile): one VEC per
+// type and no shared-memory ring kinds.
 #ifdef MCLBM_D3Q27
 #define MCLBM_VECS_F64 1
 #define MCLBM_VECS_F32 2
@@ -31,8 +30,8 @@ struct LaunchConfig {
 constexpr int kVecF64[] = {1};
 constexpr int kVecF32[] = {2};
 constexpr int kVecF16[] = {4};
-constexpr bool kAsyncKinds = false;        // kinds 4 and 5
-constexpr bool kParitySpecialised = false;  // AA kernels per parity
+constexpr bool kAsyncKinds = false;       // kinds 4 and 5
+constexpr bool kParitySpecialised = true;  // AA kernels per parity
 #else
 #define MCLBM_VECS_F64 1, 2
 #define MCLBM_VECS_F32 1, 2, 4
