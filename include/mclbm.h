@@ -79,8 +79,15 @@ typedef struct {
     double width;         /* support w of the uniform parameters (0.025)              */
     uint64_t seed;        /* key of the Philox4x64-10 parameter draw                  */
     int32_t init_density; /* 0: rho_0 = 1 (the paper); 1: TGV pressure density       */
-    int32_t reserved;     /* must be 0                                                */
+    int32_t options;      /* bit flags MCLBM_OPT_*; 0 = the paper's computations      */
 } mclbm_config;
+
+/* Option bits of mclbm_config.options.
+ * MCLBM_OPT_LERAY: initialise with the Leray-projected perturbation, u_0 = u_det + P s
+ * (Sec. "Discretization and well-prepared initial data"; the paper's runs omit P).  The
+ * parameters stay the 24 coefficients X of s; the gradient of mclbm_grad is with respect to
+ * them (the projection's transpose is applied). */
+#define MCLBM_OPT_LERAY 1
 
 /* Derived diffusive-scaling units (Table "frequencySummary", Tables "params1/2"). */
 typedef struct {
@@ -244,6 +251,14 @@ MCLBM_API int mclbm_w1_2pt(const double* d_a, int32_t MA, const double* d_b, int
 MCLBM_API size_t mclbm_sample_error_work_bytes(int32_t M);
 MCLBM_API int mclbm_sample_error(const double* d_u, const double* d_ref, int32_t M, int32_t G, void* d_work,
                                  size_t work_bytes, void* cuda_stream, double* out);
+
+/* Coefficients of the Leray-projected perturbation: P s of Eq. (alpha_perturbation) is again
+ * of that form (every term has wavenumbers (+-2, +-2, +-2), |k|^2 = 12, so
+ * P s = s + grad(div s) / 12), with coefficients Y = L X.  X, Y: host [M][24] (index
+ * 8 alpha + 4 i + 2 j + k as for the parameters).  transpose = 1 applies L^T instead.  Host
+ * only; no device work.  Errors: INVALID_ARG.  The paper has no separate counterpart: this is
+ * the map that MCLBM_OPT_LERAY applies at initialisation. */
+MCLBM_API int mclbm_leray_params(const double* X, int32_t M, int32_t transpose, double* Y);
 
 /* ---- launch shape and autotuning ------------------------------------------
  * kind 0: the direct stepper kernel updates `vec` consecutive nodes along x per

@@ -283,6 +283,25 @@ void SYM(init)(int N, int M, const real_t *params, double ulat, double uc, int d
  * then stream f_i(x + c_i) = f*_i(x) with periodic wrap.  f holds the
  * pre-collision state at t on entry and at t + 1 on exit; scratch has the
  * same size as f.  gamma_out (may be NULL): [M][n] stabiliser values. */
+/* Equilibrium populations f = f^eq(1, u) from a given lattice-unit velocity field
+ * u [M][3][n] (x fastest): Eq. (initialPopulations) for initial velocities built outside
+ * this file (the Leray-projected RTGV of Sec. "Discretization and well-prepared initial
+ * data" is assembled in the NumPy front end). */
+void SYM(init_velocity)(int N, int M, const real_t *u, real_t *f)
+{
+    build_lattice();
+    const size_t n = (size_t)N * N * N;
+    for (int m = 0; m < M; ++m) {
+#pragma omp parallel for schedule(static)
+        for (long long node = 0; node < (long long)n; ++node) {
+            real_t v[3], feq[Q];
+            for (int a = 0; a < 3; ++a) v[a] = u[((size_t)m * 3 + a) * n + node];
+            SYM(equilibrium)(1.0, v, feq);
+            for (int i = 0; i < Q; ++i) f[((size_t)m * Q + i) * n + node] = feq[i];
+        }
+    }
+}
+
 void SYM(step)(int N, int M, double omega, real_t *f, real_t *scratch, real_t *gamma_out)
 {
     build_lattice();

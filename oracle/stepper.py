@@ -97,6 +97,64 @@ def init_ensemble(N, params, ulat, uc=1.0, density_mode=0, M=None, cplx=False, l
     return f
 
 
+def rtgv_fields(N, params, uc=1.0):
+    """(u_det [3][N][N][N], s [M][3][N][N][N]) of Eqs. (tgv_init_velo) and
+    (alpha_perturbation) on the nodes x_n = 2 pi n / N (array axes z, y, x), physical units."""
+    params = np.asarray(params).reshape(-1, 24)
+    x = 2 * np.pi * np.arange(N) / N
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    udet = np.stack([uc * np.sin(X) * np.cos(Y) * np.cos(Z), -uc * np.cos(X) * np.sin(Y) * np.cos(Z),
+                     np.zeros_like(X)])
+    a = [[np.sin(2 * X), np.cos(2 * X)], [np.sin(2 * Y), np.cos(2 * Y)], [np.sin(2 * Z), np.cos(2 * Z)]]
+    s = np.zeros((params.shape[0], 3, N, N, N), dtype=np.result_type(params.dtype, np.float64))
+    for m in range(params.shape[0]):
+        for al in range(3):
+            for i in range(2):
+                for j in range(2):
+                    for k in range(2):
+                        s[m, al] += params[m, 8 * al + 4 * i + 2 * j + k] * a[0][i] * a[1][j] * a[2][k]
+    return udet, s / 8.0
+
+
+def leray_project(v):
+    """Leray projection P v = v - grad Delta^-1 div v of periodic fields v [..][3][N][N][N]
+    (array axes z, y, x; domain [0, 2 pi)^3): per Fourier mode k, (I - k k^T / |k|^2) v_k,
+    the mean (k = 0) kept.  numpy.fft serves as the transform."""
+    v = np.asarray(v)
+    N = v.shape[-1]
+    k1 = np.fft.fftfreq(N, d=1.0 / N)
+    KZ, KY, KX = np.meshgrid(k1, k1, k1, indexing="ij")
+    K = [KX, KY, KZ]
+    K2 = KX**2 + KY**2 + KZ**2
+    K2[0, 0, 0] = 1.0
+    vh = np.fft.fftn(v, axes=(-3, -2, -1))
+    kdotv = sum(K[a] * vh[..., a, :, :, :] for a in range(3))
+    out = np.empty_like(vh)
+    for a in range(3):
+        out[..., a, :, :, :] = vh[..., a, :, :, :] - K[a] * kdotv / K2
+    res = np.fft.ifftn(out, axes=(-3, -2, -1))
+    return res.real if not np.iscomplexobj(v) else res
+
+
+def init_ensemble_leray(N, params, ulat, uc=1.0, cplx=False, lattice=19):
+    """RTGV ensemble initialised with the Leray-projected perturbation, u_0 = (U_lat / U_c)
+    (u_det + P s) (Sec. "Discretization and well-prepared initial data"), f_0 = f^eq(1, u_0)."""
+    dt = np.complex128 if cplx else np.float64
+    params = np.asarray(params, dtype=dt).reshape(-1, 24)
+    M = params.shape[0]
+    udet, s = rtgv_fields(N, params, uc)
+    if cplx:  # the projection of the real and imaginary parts separately (P is a real operator)
+        ps = leray_project(s.real) + 1j * leray_project(s.imag)
+    else:
+        ps = leray_project(s)
+    u = np.ascontiguousarray(((udet[None] + ps) * (ulat / uc)).reshape(M, 3, N * N * N), dtype=dt)
+    f = np.zeros((M, lattice, N, N, N), dtype=dt)
+    fn = _fn("init_velocity", cplx, lattice)
+    fn.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp]
+    fn(int(N), int(M), _ptr(u, dt), _ptr(f, dt))
+    return f
+
+
 def step(f, omega, with_gamma=False):
     """Advance f (modified in place) by one stream+collide step; optionally return gamma [M][N^3]."""
     cplx = f.dtype == np.complex128

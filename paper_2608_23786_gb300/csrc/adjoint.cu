@@ -582,6 +582,9 @@ int run_grad(mclbm_ctx* c, int objective, int64_t nsteps, int K, char* buf, size
     pe.mark(5, c->stream);
     MCLBM_CUDA(cudaMemcpyAsync(h_dJdX, out, sizeof(double) * 24 * c->M, cudaMemcpyDeviceToHost, c->stream));
     MCLBM_CUDA(cudaStreamSynchronize(c->stream));
+    // with the Leray option the kernels differentiate with respect to the evaluated
+    // coefficients Y = L X; dJ/dX = L^T dJ/dY
+    if (c->cfg.options & MCLBM_OPT_LERAY) leray_map(h_dJdX, c->M, true, h_dJdX);
     if (pe.ok) {
         float f = 0, p = 0;
         cudaEventElapsedTime(&f, pe.ev[0], pe.ev[1]);

@@ -83,7 +83,7 @@ int validate(const mclbm_config* cfg, mclbm_units* u)
     if (!(cfg->width >= 0) || !std::isfinite(cfg->width)) return set_error(MCLBM_ERR_INVALID_ARG, "width must be >= 0");
     if (cfg->init_density != 0 && cfg->init_density != 1)
         return set_error(MCLBM_ERR_INVALID_ARG, "init_density must be 0 or 1");
-    if (cfg->reserved != 0) return set_error(MCLBM_ERR_INVALID_ARG, "reserved must be 0");
+    if ((cfg->options & ~MCLBM_OPT_LERAY) != 0) return set_error(MCLBM_ERR_INVALID_ARG, "unknown option bits");
     if (!std::isfinite(cfg->nu)) return set_error(MCLBM_ERR_INVALID_ARG, "nu must be finite");
     const double pi = 3.14159265358979323846;
     mclbm_units r;
@@ -106,6 +106,47 @@ int validate(const mclbm_config* cfg, mclbm_units* u)
 }
 
 }  // namespace
+
+// Leray projection on the 24 coefficients of the perturbation (Sec. "Discretization and
+// well-prepared initial data").  s_a = (1/8) sum_{ijk} X_{a,ijk} B_{ijk} with
+// B_{ijk} = A_i(2x) A_j(2y) A_k(2z), A_0 = sin, A_1 = cos, so the derivative along axis b of
+// B_{ijk} is 2 sg(t) B_{ijk with t flipped}, t the index of axis b, sg(0) = 1, sg(1) = -1.
+// Every term has |k|^2 = 12, hence P s = s + grad(div s) / 12 and, on the coefficients,
+//   Y_{b,lmn} = X_{b,lmn} + (1/3) sum_a sg(I_a(ijk)) sg(I_b(flip_a ijk)) X_{a,ijk},
+//   ijk = flip_a flip_b (lmn).
+void leray_matrix(double L[24][24])
+{
+    for (int r = 0; r < 24; ++r)
+        for (int q = 0; q < 24; ++q) L[r][q] = r == q ? 1.0 : 0.0;
+    for (int b = 0; b < 3; ++b)
+        for (int lmn = 0; lmn < 8; ++lmn)
+            for (int a = 0; a < 3; ++a) {
+                int idx[3] = {(lmn >> 2) & 1, (lmn >> 1) & 1, lmn & 1};
+                idx[b] ^= 1;
+                idx[a] ^= 1;  // ijk = flip_a flip_b (lmn)
+                const int ta = idx[a];
+                int f[3] = {idx[0], idx[1], idx[2]};
+                f[a] ^= 1;  // flip_a (ijk)
+                const int tb = f[b];
+                const double sg = (ta == 0 ? 1.0 : -1.0) * (tb == 0 ? 1.0 : -1.0);
+                L[8 * b + lmn][8 * a + 4 * idx[0] + 2 * idx[1] + idx[2]] += sg / 3.0;
+            }
+}
+
+void leray_map(const double* X, int M, bool transpose, double* Y)
+{
+    double L[24][24];
+    leray_matrix(L);
+    for (int m = 0; m < M; ++m) {
+        double y[24];
+        for (int r = 0; r < 24; ++r) {
+            double acc = 0.0;
+            for (int q = 0; q < 24; ++q) acc += (transpose ? L[q][r] : L[r][q]) * X[24 * m + q];
+            y[r] = acc;
+        }
+        for (int r = 0; r < 24; ++r) Y[24 * m + r] = y[r];
+    }
+}
 
 // Default launch shape: the fastest measured on a GB300 for the 64^3 x 64 and 128^3 x 32
 // ensembles (the autotuner may pick another).  D3Q19: FP32 packed collision, 2 nodes per
@@ -280,7 +321,12 @@ int mclbm_get_units(const mclbm_ctx* ctx, mclbm_units* out)
 static int do_init(mclbm_ctx* c)
 {
     double* d_params = (double*)(c->work + c->wl.params);
-    MCLBM_CUDA(cudaMemcpyAsync(d_params, c->params.data(), sizeof(double) * 24 * c->M, cudaMemcpyHostToDevice, c->stream));
+    // the coefficients of the perturbation the initialisation evaluates: X, or L X with the
+    // Leray projection
+    c->init_coeffs = c->params;
+    if (c->cfg.options & MCLBM_OPT_LERAY) leray_map(c->params.data(), c->M, false, c->init_coeffs.data());
+    MCLBM_CUDA(cudaMemcpyAsync(d_params, c->init_coeffs.data(), sizeof(double) * 24 * c->M, cudaMemcpyHostToDevice,
+                               c->stream));
     c->cur = 0;
     c->steps = 0;
     MCLBM_CUDA(cudaMemsetAsync(c->work + c->wl.flag, 0, 16 * sizeof(int), c->stream));
@@ -315,6 +361,13 @@ int mclbm_init_tgv(mclbm_ctx* ctx)
     if (!ctx) return set_error(MCLBM_ERR_INVALID_ARG, "ctx is NULL");
     std::fill(ctx->params.begin(), ctx->params.end(), 0.0);
     return do_init(ctx);
+}
+
+int mclbm_leray_params(const double* X, int32_t M, int32_t transpose, double* Y)
+{
+    if (!X || !Y || M < 1 || (transpose != 0 && transpose != 1)) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    leray_map(X, M, transpose == 1, Y);
+    return MCLBM_OK;
 }
 
 int mclbm_get_params(const mclbm_ctx* ctx, double* params)

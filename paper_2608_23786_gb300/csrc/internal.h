@@ -45,7 +45,8 @@ struct mclbm_ctx {
     int device;
     int cur;         // pull: lattice (0/1) holding the current state
     int64_t steps;   // steps since the last initialisation
-    std::vector<double> params;  // host copy [M][24]
+    std::vector<double> params;       // host copy [M][24]
+    std::vector<double> init_coeffs;  // coefficients the initialisation evaluates (L params with the Leray option)
     size_t elem_bytes;
     bool twiddles_ready;  // FFT twiddle table computed in the work buffer
     mclbm::LaunchConfig launch;  // stepper variant (autotuned or default)
@@ -79,6 +80,7 @@ cudaError_t launch_levels(mclbm_ctx* const* levels, int nlev, const LaunchConfig
 bool vec_supported(int precision, int vec);
 bool launch_supported(int precision, const LaunchConfig& c);
 LaunchConfig default_launch(int precision, int pattern);
+void leray_map(const double* X, int M, bool transpose, double* Y);  // api.cu
 cudaError_t launch_get_populations(const mclbm_ctx* c, int sample, double* d_out);
 cudaError_t launch_set_populations(mclbm_ctx* c, int sample, const double* d_in);
 cudaError_t launch_moments(const mclbm_ctx* c, int sample, double* d_rho, double* d_u);

@@ -18,6 +18,7 @@ STATUS = {
 }
 FP64, FP32, FP16 = 0, 1, 2
 PULL, AA = 0, 1
+OPT_LERAY = 1
 Q = 19
 
 
@@ -33,7 +34,7 @@ class Config(ctypes.Structure):
         ("N", ctypes.c_int32), ("M", ctypes.c_int32), ("precision", ctypes.c_int32), ("pattern", ctypes.c_int32),
         ("nu", ctypes.c_double), ("Ma", ctypes.c_double), ("dt", ctypes.c_double), ("U_c", ctypes.c_double),
         ("width", ctypes.c_double), ("seed", ctypes.c_uint64), ("init_density", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("options", ctypes.c_int32),
     ]
 
 
@@ -80,6 +81,7 @@ _SIGNATURES = {
     "mclbm_w1_restricted": (_c.c_int, [_vp, _c.c_int32, _vp, _c.c_int32, _c.c_int32, _vp, _c.c_size_t, _vp, _dp, _dp]),
     "mclbm_w1_2pt_work_bytes": (_c.c_size_t, [_c.c_int32, _c.c_int32]),
     "mclbm_sample_error_work_bytes": (_c.c_size_t, [_c.c_int32]),
+    "mclbm_leray_params": (_c.c_int, [_dp, _c.c_int32, _c.c_int32, _dp]),
     "mclbm_sample_error": (_c.c_int, [_vp, _vp, _c.c_int32, _c.c_int32, _vp, _c.c_size_t, _vp, _dp]),
     "mclbm_w1_2pt": (_c.c_int, [_vp, _c.c_int32, _vp, _c.c_int32, _c.c_int32, _c.c_int32, _vp, _c.c_size_t, _vp, _dp,
                                 _vp]),
@@ -239,6 +241,15 @@ def mclbm_draw_params(seed, first_sample, M, width=0.025):
 
 def mclbm_init_tgv(ctx):
     _check(_L(ctx).mclbm_init_tgv(ctx))
+
+
+def mclbm_leray_params(X, transpose=False):
+    """Coefficients L X (or L^T X) of the Leray-projected perturbation, X [M][24] (host)."""
+    import numpy as np
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 24)
+    Y = np.zeros_like(X)
+    _check(load().mclbm_leray_params(_darr(X), X.shape[0], int(bool(transpose)), _darr(Y)))
+    return Y
 
 
 def mclbm_get_params(ctx, out):

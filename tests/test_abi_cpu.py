@@ -50,7 +50,7 @@ def test_lattice_matches_oracle_set(lib):
 
 def _cfg(N=64, M=4, Re=800.0, Ma=0.025, precision=mclbm.FP32, pattern=mclbm.PULL, dt=0.0):
     return mclbm.Config(N=N, M=M, precision=precision, pattern=pattern, nu=1.0 / Re, Ma=Ma, dt=dt, U_c=1.0,
-                        width=0.025, seed=1, init_density=0, reserved=0)
+                        width=0.025, seed=1, init_density=0, options=0)
 
 
 @pytest.mark.parametrize("N,Re,Ma", [(32, 1280, 0.05), (64, 2560, 0.025), (512, 20480, 0.003125), (64, 800, 0.025)])
@@ -75,7 +75,7 @@ def test_validation_errors(lib):
     assert e.value.status == "SHAPE"
     with pytest.raises(mclbm.MclbmError) as e:
         mclbm.mclbm_compute_units(mclbm.Config(N=32, M=1, precision=1, pattern=0, nu=-1e-3, Ma=0.1, dt=0, U_c=1,
-                                               width=0.025, seed=0, init_density=0, reserved=0))
+                                               width=0.025, seed=0, init_density=0, options=0))
     assert e.value.status == "UNSTABLE_TAU"
     with pytest.raises(mclbm.MclbmError) as e:
         mclbm.mclbm_compute_units(_cfg(precision=7))
@@ -120,3 +120,18 @@ def test_d3q27_library_exports_the_same_abi(lib):
     pop, _ = mclbm.mclbm_required_bytes(_cfg(N=64, M=8, precision=mclbm.FP32, pattern=mclbm.PULL), lattice=27)
     assert pop == 2 * 27 * 4 * 64**3 * 8
     assert "D3Q27" in mclbm.mclbm_version(27) and "D3Q19" in mclbm.mclbm_version()
+
+
+def test_leray_coefficient_map_against_fft_projection(lib):
+    """mclbm_leray_params (host) maps the 24 coefficients of the perturbation to those of its
+    Leray projection: evaluated on a 16^3 grid, L X reproduces the oracle's FFT projection of s;
+    the transpose option is the matrix transpose; the map is a projection (L L = L)."""
+    X = gen.draw_params(5, 3)
+    Y = mclbm.mclbm_leray_params(X)
+    _, s = oracle.rtgv_fields(16, X)
+    _, s_y = oracle.rtgv_fields(16, Y)
+    np.testing.assert_allclose(s_y, oracle.leray_project(s), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(mclbm.mclbm_leray_params(Y), Y, rtol=0, atol=1e-16)
+    E = np.eye(24)
+    L = mclbm.mclbm_leray_params(E).T  # column q = L e_q
+    np.testing.assert_allclose(mclbm.mclbm_leray_params(E, transpose=True).T, L.T, atol=0)

@@ -111,3 +111,24 @@ def test_philox_parameter_draw_matches_definition():
     assert np.all(np.abs(A) <= gen.RTGV_WIDTH)
     big = gen.draw_params(seed=1, M=400)
     assert abs(big.mean()) < 2e-3 and abs(big.var() - gen.RTGV_WIDTH**2 / 3) < 1e-5
+
+
+def test_leray_projection_pins():
+    """P v = v - grad Delta^-1 div v (Sec. "Discretization and well-prepared initial data"): the
+    projected perturbation is divergence free (spectrally), P is idempotent, the TGV field
+    (divergence free) is left unchanged, and the removed part is a gradient (its curl vanishes)."""
+    N = 16
+    X = gen.draw_params(8, 2)
+    udet, s = oracle.rtgv_fields(N, X)
+    ps = oracle.leray_project(s)
+    k = np.fft.fftfreq(N, d=1.0 / N)
+    KZ, KY, KX = np.meshgrid(k, k, k, indexing="ij")
+    h = np.fft.fftn(ps, axes=(-3, -2, -1))
+    assert np.abs(KX * h[:, 0] + KY * h[:, 1] + KZ * h[:, 2]).max() <= 1e-12 * np.abs(h).max()
+    np.testing.assert_allclose(oracle.leray_project(ps), ps, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(oracle.leray_project(udet[None]), udet[None], rtol=0, atol=1e-14)
+    g = np.fft.fftn(s - ps, axes=(-3, -2, -1))
+    curl = [KY * g[:, 2] - KZ * g[:, 1], KZ * g[:, 0] - KX * g[:, 2], KX * g[:, 1] - KY * g[:, 0]]
+    assert max(np.abs(c).max() for c in curl) <= 1e-12 * np.abs(g).max()
+    # the projected perturbation keeps about 2/3 of the energy of a mode with k = (2, 2, 2)
+    assert 0.3 < np.sum(ps**2) / np.sum(s**2) < 1.0
