@@ -9,5 +9,5 @@ live in ``stats.py`` (NumPy).  Neither shares code with the CUDA library.
 from .build import build_oracle, load_oracle  # noqa: F401
 from .stepper import (  # noqa: F401
     lattice, units, equilibrium, collide, shear_part, init_ensemble, step, run, moments, energy, hrel,
-    complex_step_grad, rtgv_fields, leray_project, init_ensemble_leray,
+    complex_step_grad, rtgv_fields, leray_project, init_ensemble_leray, exact_gamma,
 )

@@ -201,6 +201,39 @@ void SYM(shear_part)(const real_t *fneq, real_t *ds)
  *   gamma = 2/omega - (2 - 2/omega) <Ds|Dh> / <Dh|Dh>   (gamma = 2 if <Dh|Dh> = 0),
  *   f* = f - omega Ds - (omega gamma / 2) Dh.
  * Optional outputs gamma, ds, dh may be NULL. */
+#ifndef ORC_COMPLEX
+/* Exact entropic gamma of Eq. (kbc_entropy): the minimiser of H(f*(g)) = sum f*_i ln(f*_i / w_i)
+ * over g, f*(g) = f - omega Ds - (omega g / 2) Dh.  dH/dg = -(omega / 2) sum Dh_i (ln(f*_i / w_i)
+ * + 1) and sum Dh_i = 0, so the minimiser is the root of G(g) = sum Dh_i ln(f*_i(g) / w_i).
+ * G is decreasing (G' = -(omega / 2) sum Dh_i^2 / f*_i) on the interval where every f*_i > 0
+ * and runs from +inf to -inf across it; the root is found by bisection of that interval.
+ * Dh = 0: gamma = 2 (the paper's BGK value). */
+static int exact_gamma_mode = 0;
+
+void RSYM(set_exact_gamma)(int on) { exact_gamma_mode = on; }
+
+static double exact_gamma(const double *f, const double *ds, const double *dh, double omega)
+{
+    double A[Q], B[Q], lo = -INFINITY, hi = INFINITY;
+    int any = 0;
+    for (int i = 0; i < Q; ++i) {
+        A[i] = f[i] - omega * ds[i];
+        B[i] = 0.5 * omega * dh[i];
+        if (B[i] > 0) { double r = A[i] / B[i]; if (r < hi) hi = r; any = 1; }
+        if (B[i] < 0) { double r = A[i] / B[i]; if (r > lo) lo = r; any = 1; }
+    }
+    if (!any) return 2.0;
+    for (int it = 0; it < 400; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (!(mid > lo && mid < hi)) break;
+        double G = 0;
+        for (int i = 0; i < Q; ++i) G += dh[i] * log((A[i] - mid * B[i]) / W[i]);
+        if (G > 0) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+#endif
+
 void SYM(collide)(const real_t *f, double omega, real_t *fstar, real_t *gamma_out, real_t *ds_out,
                   real_t *dh_out)
 {
@@ -221,6 +254,9 @@ void SYM(collide)(const real_t *f, double omega, real_t *fstar, real_t *gamma_ou
         gamma = 2.0;
     else
         gamma = 2.0 / omega - (2.0 - 2.0 / omega) * sh / hh;
+#ifndef ORC_COMPLEX
+    if (exact_gamma_mode && hh != 0.0) gamma = exact_gamma(f, ds, dh, omega);
+#endif
     for (int i = 0; i < Q; ++i) fstar[i] = f[i] - omega * ds[i] - 0.5 * omega * gamma * dh[i];
     if (gamma_out) *gamma_out = gamma;
     if (ds_out) memcpy(ds_out, ds, sizeof ds);

@@ -67,6 +67,21 @@ def shear_part(fneq):
     return ds
 
 
+class exact_gamma:
+    """Context manager: within it the real oracle (both velocity sets) takes the exact entropic
+    gamma of Eq. (kbc_entropy) (bisection) instead of the closed form, Eq. (entropyControl)."""
+
+    def __enter__(self):
+        for q in (19, 27):
+            _fn("set_exact_gamma", lattice=q)(1)
+        return self
+
+    def __exit__(self, *exc):
+        for q in (19, 27):
+            _fn("set_exact_gamma", lattice=q)(0)
+        return False
+
+
 def collide(f, omega, cplx=False):
     """One-node KBC collision: returns (f*, gamma, Ds, Dh)."""
     f = _arr(f, cplx)

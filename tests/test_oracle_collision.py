@@ -206,3 +206,31 @@ def test_closed_form_gamma_approaches_exact_entropic_minimiser():
         gaps.append(max(gap_amp))
     r1, r2 = gaps[0] / gaps[1], gaps[1] / gaps[2]
     assert 5 < r1 < 20 and 5 < r2 < 20, gaps
+
+
+@pytest.mark.parametrize("seed", [50, 51, 52, 53])
+def test_exact_gamma_is_the_entropy_minimiser(seed):
+    """With oracle.exact_gamma(), gamma minimises H(f*) = sum f* ln(f*/w) (Eq. (kbc_entropy)):
+    the stationarity residual sum Dh ln(f*/w) vanishes, H is larger on both sides, and the value
+    agrees with an independent bisection of the same condition here; the closed form differs
+    from it at second order in the non-equilibrium amplitude."""
+    c, w, _ = oracle.lattice()
+    f = _random_node(seed, amp=2e-2)
+    omega = 1.9
+    fc, gc, ds, dh = oracle.collide(f, omega)
+    with oracle.exact_gamma():
+        fe, ge, _, _ = oracle.collide(f, omega)
+
+    def fstar(gp):
+        return f - omega * ds - 0.5 * omega * gp * dh
+
+    def H(gp):
+        x = fstar(gp)
+        return np.sum(x * np.log(x / w))
+
+    assert abs(np.sum(dh * np.log(fstar(ge) / w))) <= 1e-13 * np.sum(np.abs(dh))
+    assert H(ge - 1e-3) > H(ge) and H(ge + 1e-3) > H(ge)
+    root = _bisect(lambda gp: np.sum(dh * np.log(fstar(gp) / w)), ge - 1.0, ge + 1.0)
+    assert abs(root - ge) <= 1e-12 * abs(ge)
+    np.testing.assert_allclose(fe, fstar(ge), rtol=1e-15, atol=1e-17)
+    assert 0 < abs(ge - gc) < 0.1 * abs(gc)
