@@ -88,6 +88,11 @@ typedef struct {
  * parameters stay the 24 coefficients X of s; the gradient of mclbm_grad is with respect to
  * them (the projection's transpose is applied). */
 #define MCLBM_OPT_LERAY 1
+/* MCLBM_OPT_EXACT_GAMMA: gamma is the exact minimiser of Eq. (kbc_entropy), the root of
+ * sum Dh ln(f* / w) = 0 by safeguarded Newton iteration from the closed form (Eq.
+ * (entropyControl)), in FP64 (FP64 storage) or FP32; the stepper then runs launch kind 6 (the
+ * direct kernel).  mclbm_grad rejects contexts with this option. */
+#define MCLBM_OPT_EXACT_GAMMA 2
 
 /* Derived diffusive-scaling units (Table "frequencySummary", Tables "params1/2"). */
 typedef struct {
@@ -272,6 +277,10 @@ MCLBM_API int mclbm_leray_params(const double* X, int32_t M, int32_t transpose, 
  * run's arithmetic (same vec and block values as kind 0).
  * kind 3: kind 2 with the FP32 collision of two nodes at a time in the packed FP32
  * instructions of sm_100 and later (FP32 and FP16 storage, even vec).
+ * kinds 4 and 5: kind 3 with the runs ahead copied by cp.async into a shared-memory ring, one
+ * or two runs deep (FP32 and FP16 storage, block 128; not in the D3Q27 library).
+ * kind 6: the direct kernel with the exact entropic gamma (contexts with
+ * MCLBM_OPT_EXACT_GAMMA, and only they; vec = the first of the type's list, block 128).
  * Results do not depend on the shape (same arithmetic per node, every operation
  * rounded once in the same order). */
 MCLBM_API int mclbm_set_launch(mclbm_ctx* ctx, int32_t kind, int32_t vec, int32_t block);

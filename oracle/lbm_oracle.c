@@ -203,26 +203,37 @@ void SYM(shear_part)(const real_t *fneq, real_t *ds)
  * Optional outputs gamma, ds, dh may be NULL. */
 #ifndef ORC_COMPLEX
 /* Exact entropic gamma of Eq. (kbc_entropy): the minimiser of H(f*(g)) = sum f*_i ln(f*_i / w_i)
- * over g, f*(g) = f - omega Ds - (omega g / 2) Dh.  dH/dg = -(omega / 2) sum Dh_i (ln(f*_i / w_i)
- * + 1) and sum Dh_i = 0, so the minimiser is the root of G(g) = sum Dh_i ln(f*_i(g) / w_i).
- * G is decreasing (G' = -(omega / 2) sum Dh_i^2 / f*_i) on the interval where every f*_i > 0
- * and runs from +inf to -inf across it; the root is found by bisection of that interval.
- * Dh = 0: gamma = 2 (the paper's BGK value). */
+ * over g, f*(g) = f - omega Ds - (omega g / 2) Dh, taken over 0 <= g <= 4 / omega (the range in
+ * which the relaxation factor omega g / 2 of Dh stays in the stable [0, 2]; with the polynomial
+ * equilibrium the unconstrained minimiser grows like 1 / |Dh| near equilibrium).
+ * dH/dg = -(omega / 2) sum Dh_i (ln(f*_i / w_i) + 1) and sum Dh_i = 0, so the stationary point
+ * is the root of G(g) = sum Dh_i ln(f*_i(g) / w_i); G decreases (G' = -(omega / 2)
+ * sum Dh_i^2 / f*_i) where every f*_i > 0, so H is convex along the line and the constrained
+ * minimiser is the root if it lies inside the interval, else the nearer end point.  The root is
+ * found by bisection.  Dh = 0: gamma = 2 (the paper's BGK value). */
 static int exact_gamma_mode = 0;
 
 void RSYM(set_exact_gamma)(int on) { exact_gamma_mode = on; }
 
-static double exact_gamma(const double *f, const double *ds, const double *dh, double omega)
+static double exact_gamma(const double *f, const double *ds, const double *dh, double omega, double g_closed)
 {
-    double A[Q], B[Q], lo = -INFINITY, hi = INFINITY;
-    int any = 0;
+    double A[Q], B[Q], lo = 0.0, hi = 4.0 / omega;
     for (int i = 0; i < Q; ++i) {
         A[i] = f[i] - omega * ds[i];
         B[i] = 0.5 * omega * dh[i];
-        if (B[i] > 0) { double r = A[i] / B[i]; if (r < hi) hi = r; any = 1; }
-        if (B[i] < 0) { double r = A[i] / B[i]; if (r > lo) lo = r; any = 1; }
+        if (B[i] > 0) { double r = A[i] / B[i]; if (r < hi) hi = r; }
+        if (B[i] < 0) { double r = A[i] / B[i]; if (r > lo) lo = r; }
     }
-    if (!any) return 2.0;
+    if (!(lo < hi)) return g_closed;
+    /* H is convex along the line: the minimiser over [lo, hi] is an end point where G does not
+     * change sign inside, else the root */
+    double G_lo = 0, G_hi = 0;
+    for (int i = 0; i < Q; ++i) {
+        G_lo += dh[i] * log((A[i] - lo * B[i]) / W[i]);
+        G_hi += dh[i] * log((A[i] - hi * B[i]) / W[i]);
+    }
+    if (!(G_lo > 0)) return lo;
+    if (!(G_hi < 0)) return hi;
     for (int it = 0; it < 400; ++it) {
         double mid = 0.5 * (lo + hi);
         if (!(mid > lo && mid < hi)) break;
@@ -255,7 +266,7 @@ void SYM(collide)(const real_t *f, double omega, real_t *fstar, real_t *gamma_ou
     else
         gamma = 2.0 / omega - (2.0 - 2.0 / omega) * sh / hh;
 #ifndef ORC_COMPLEX
-    if (exact_gamma_mode && hh != 0.0) gamma = exact_gamma(f, ds, dh, omega);
+    if (exact_gamma_mode && hh != 0.0) gamma = exact_gamma(f, ds, dh, omega, gamma);
 #endif
     for (int i = 0; i < Q; ++i) fstar[i] = f[i] - omega * ds[i] - 0.5 * omega * gamma * dh[i];
     if (gamma_out) *gamma_out = gamma;

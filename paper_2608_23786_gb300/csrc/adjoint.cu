@@ -653,6 +653,8 @@ int mclbm_grad_required_bytes(const mclbm_ctx* ctx, int64_t nsteps, int32_t ckpt
 int mclbm_grad(mclbm_ctx* ctx, int32_t objective, int64_t nsteps, int32_t ckpt_every, void* d_buf, size_t buf_bytes,
                double* J, double* dJdX)
 {
+    if (ctx && (ctx->cfg.options & MCLBM_OPT_EXACT_GAMMA))
+        return set_error(MCLBM_ERR_INVALID_ARG, "the adjoint covers the closed-form gamma only (not MCLBM_OPT_EXACT_GAMMA)");
     if (!ctx || !d_buf || !J || !dJdX || nsteps < 0 || ckpt_every < 1 || (objective != 0 && objective != 1))
         return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
     if (ctx->cfg.pattern != MCLBM_PULL) return set_error(MCLBM_ERR_INVALID_ARG, "the adjoint needs pull streaming");

@@ -83,7 +83,8 @@ int validate(const mclbm_config* cfg, mclbm_units* u)
     if (!(cfg->width >= 0) || !std::isfinite(cfg->width)) return set_error(MCLBM_ERR_INVALID_ARG, "width must be >= 0");
     if (cfg->init_density != 0 && cfg->init_density != 1)
         return set_error(MCLBM_ERR_INVALID_ARG, "init_density must be 0 or 1");
-    if ((cfg->options & ~MCLBM_OPT_LERAY) != 0) return set_error(MCLBM_ERR_INVALID_ARG, "unknown option bits");
+    if ((cfg->options & ~(MCLBM_OPT_LERAY | MCLBM_OPT_EXACT_GAMMA)) != 0)
+        return set_error(MCLBM_ERR_INVALID_ARG, "unknown option bits");
     if (!std::isfinite(cfg->nu)) return set_error(MCLBM_ERR_INVALID_ARG, "nu must be finite");
     const double pi = 3.14159265358979323846;
     mclbm_units r;
@@ -152,8 +153,9 @@ void leray_map(const double* X, int M, bool transpose, double* Y)
 // ensembles (the autotuner may pick another).  D3Q19: FP32 packed collision, 2 nodes per
 // thread; FP16 pull shared-memory prefetch ring, 8 nodes per thread; FP16 AA packed
 // collision, 4 nodes per thread; FP64 (bound by the FP64 units) the direct kernel.
-LaunchConfig default_launch(int precision, int pattern)
+LaunchConfig default_launch(int precision, int pattern, int options)
 {
+    if (options & MCLBM_OPT_EXACT_GAMMA) return LaunchConfig{exact_vec(precision), 128, 6};
 #ifdef MCLBM_D3Q27
     // D3Q27 (measured): FP32 prefetching kernel (pull: one-node collision, AA: packed); FP16
     // pull the direct kernel, AA the prefetching one
@@ -301,7 +303,7 @@ int mclbm_create(const mclbm_config* cfg, void* d_pop, size_t pop_bytes, void* d
     c->params.assign((size_t)cfg->M * 24, 0.0);
     c->elem_bytes = elem_bytes_of(cfg->precision);
     c->twiddles_ready = false;
-    c->launch = default_launch(cfg->precision, cfg->pattern);
+    c->launch = default_launch(cfg->precision, cfg->pattern, cfg->options);
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
     c->num_sms = sms;

@@ -132,9 +132,13 @@ int time_ms(cudaStream_t s, F&& body, double* ms)
     return MCLBM_OK;
 }
 
-std::vector<LaunchConfig> candidates(int precision, int N)
+std::vector<LaunchConfig> candidates(int precision, int N, bool exact)
 {
     std::vector<LaunchConfig> v;
+    if (exact) {  // the exact entropic gamma runs in its one kernel
+        v.push_back(LaunchConfig{exact_vec(precision), 128, 6});
+        return v;
+    }
     const int* vecs;
     int nv;
     if (precision == MCLBM_FP64) {
@@ -168,6 +172,8 @@ int mclbm_set_launch(mclbm_ctx* ctx, int32_t kind, int32_t vec, int32_t block)
     if (!launch_supported(ctx->cfg.precision, c) || vec < 1 || ctx->N % vec)
         return set_error(MCLBM_ERR_INVALID_ARG, "unsupported launch shape (kind " + std::to_string(kind) + ", vec " +
                                                     std::to_string(vec) + ", block " + std::to_string(block) + ")");
+    if ((kind == 6) != ((ctx->cfg.options & MCLBM_OPT_EXACT_GAMMA) != 0))
+        return set_error(MCLBM_ERR_INVALID_ARG, "kind 6 is the launch of contexts with MCLBM_OPT_EXACT_GAMMA, and only it");
     ctx->launch = c;
     return MCLBM_OK;
 }
@@ -187,7 +193,7 @@ int mclbm_autotune(mclbm_ctx* ctx, int32_t trial_steps, int32_t* kind, int32_t* 
     if (ctx->steps != 0) return set_error(MCLBM_ERR_INVALID_ARG, "autotune must directly follow an initialisation");
     double best = 1e300;
     LaunchConfig bestc = ctx->launch;
-    for (const LaunchConfig& c : candidates(ctx->cfg.precision, ctx->N)) {
+    for (const LaunchConfig& c : candidates(ctx->cfg.precision, ctx->N, (ctx->cfg.options & MCLBM_OPT_EXACT_GAMMA) != 0)) {
         MCLBM_CUDA(launch_step_with(ctx, c));  // warm-up (first use also sizes the grid)
         double ms = 0;
         int st = time_ms(
@@ -227,6 +233,8 @@ int mclbm_batch_create(mclbm_ctx* const* levels, int32_t nlev, const int32_t* su
         if (substeps[l] > S) S = substeps[l];
         if (levels[l]->cfg.precision != levels[0]->cfg.precision || levels[l]->cfg.pattern != levels[0]->cfg.pattern)
             return set_error(MCLBM_ERR_INVALID_ARG, "levels of a batch share precision and streaming pattern");
+        if ((levels[l]->cfg.options & MCLBM_OPT_EXACT_GAMMA) != (levels[0]->cfg.options & MCLBM_OPT_EXACT_GAMMA))
+            return set_error(MCLBM_ERR_INVALID_ARG, "levels of a batch share the gamma option");
         if (levels[l]->stream != levels[0]->stream || levels[l]->device != levels[0]->device)
             return set_error(MCLBM_ERR_INVALID_ARG, "levels of a batch share device and stream");
         for (int k = 0; k < l; ++k)
@@ -316,7 +324,7 @@ int mclbm_batch_autotune(mclbm_batch* b, int32_t trials, int32_t* kind, int32_t*
     for (auto* c : b->lev) Nmin = c->N < Nmin ? c->N : Nmin;
     double best = 1e300;
     LaunchConfig bestc = b->launch;
-    for (const LaunchConfig& c : candidates(prec, Nmin)) {
+    for (const LaunchConfig& c : candidates(prec, Nmin, (b->lev[0]->cfg.options & MCLBM_OPT_EXACT_GAMMA) != 0)) {
         bool ok = true;
         for (auto* l : b->lev) ok = ok && (l->N % c.vec == 0);
         if (!ok) continue;

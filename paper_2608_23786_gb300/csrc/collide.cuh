@@ -450,4 +450,145 @@ __device__ __forceinline__ V kbc_shifted(V (&h)[Q], float omega, float a, float 
 
 #endif  // MCLBM_D3Q27
 
+// ---- Exact entropic gamma (option MCLBM_OPT_EXACT_GAMMA) -----------------------------------
+// gamma minimises H(f*(g)) = sum f*_i ln(f*_i / w_i), Eq. (kbc_entropy), over the line
+// f*(g) = f - omega Ds - (omega g / 2) Dh with 0 <= g <= 4 / omega (the relaxation factor
+// omega g / 2 of Dh in the stable [0, 2]; with the polynomial equilibrium the unconstrained
+// minimiser grows like 1 / |Dh| near equilibrium).  Since sum Dh = 0 the stationary point is
+// the root of G(g) = sum Dh_i ln(f*_i / w_i); G decreases (G' = -(omega / 2) sum Dh_i^2 / f*_i)
+// where every f*_i > 0, so the constrained minimiser is the root or the nearer end point.
+// Written with r_i = f*_i / w_i = 1 + am1_i - g b_i (b_i = (omega / 2) Dh_i / w_i):
+// safeguarded Newton from the closed form, keeping a bracket of the root and bisecting where a
+// Newton step leaves it.  T = double (FP64) or float (FP32).
+template <class T>
+__device__ __forceinline__ T log_ratio(T a_minus_one, T g, T b)
+{
+    // ln(r) with r - 1 = a_minus_one - g b formed first, so that r close to 1 keeps its digits
+    if constexpr (sizeof(T) == 8)
+        return log1p(a_minus_one - g * b);
+    else
+        return log1pf(a_minus_one - g * b);
+}
+
+template <class T>
+__device__ __forceinline__ T exact_gamma_refine(const T (&am1)[Q], const T (&b)[Q], T omega, T g0, int max_iter,
+                                                T rel_tol)
+{
+    // constrained interval: 0 <= g <= 4 / omega and every r_i = 1 + am1_i - g b_i > 0
+    T lo = T(0), hi = T(4) / omega;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (b[i] > T(0)) hi = fmin(hi, (T(1) + am1[i]) / b[i]);
+        else if (b[i] < T(0)) lo = fmax(lo, (T(1) + am1[i]) / b[i]);
+    }
+    if (!(lo < hi)) return g0;
+    T G_lo = 0, G_hi = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        G_lo += weight<T>(i) * b[i] * log_ratio<T>(am1[i], lo, b[i]);
+        G_hi += weight<T>(i) * b[i] * log_ratio<T>(am1[i], hi, b[i]);
+    }
+    if (!(G_lo > T(0))) return lo;  // H increases over the whole interval
+    if (!(G_hi < T(0))) return hi;  // H decreases over the whole interval
+    T g = (g0 > lo && g0 < hi) ? g0 : T(0.5) * (lo + hi);
+    for (int it = 0; it < max_iter; ++it) {
+        T G = 0, Gp = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const T r = T(1) + am1[i] - g * b[i];
+            G += weight<T>(i) * b[i] * log_ratio<T>(am1[i], g, b[i]);
+            Gp -= weight<T>(i) * b[i] * b[i] / r;
+        }
+        if (G > T(0)) lo = g;
+        else hi = g;
+        T gn = g - G / Gp;
+        if (!(gn > lo && gn < hi)) gn = T(0.5) * (lo + hi);
+        const bool done = fabs(gn - g) <= rel_tol * fabs(g) || !(gn > lo && gn < hi);
+        g = gn;
+        if (done) break;
+    }
+    return g;
+}
+
+// KBC with the exact gamma, one node, any velocity set, in the normalised deviations
+// h = f / w - 1 (raw FP64 populations are converted on entry and exit; FP32 storage holds h).
+// The equilibrium, shear part and closed-form gamma are those of kbc_shifted written over all
+// velocities; the closed form starts the Newton iteration.  Returns gamma.
+template <class T, bool SHIFTED>
+__device__ __forceinline__ T kbc_exact(T (&f)[Q], T omega)
+{
+    T h[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) h[i] = SHIFTED ? f[i] : f[i] * inv_weight<T>(i) - T(1);
+    T drho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const T wh = weight<T>(i) * h[i];
+        drho += wh;
+        MCLBM_SIGNED_ADD(jx, cx(i), wh);
+        MCLBM_SIGNED_ADD(jy, cy(i), wh);
+        MCLBM_SIGNED_ADD(jz, cz(i), wh);
+    }
+    const T rinv = T(1) / (T(1) + drho);
+    const T jj = jx * jx + jy * jy + jz * jz;
+    T heq[Q], n[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        T cj = 0;
+        MCLBM_SIGNED_ADD(cj, cx(i), jx);
+        MCLBM_SIGNED_ADD(cj, cy(i), jy);
+        MCLBM_SIGNED_ADD(cj, cz(i), jz);
+        heq[i] = drho + T(3) * cj + rinv * (T(4.5) * cj * cj - T(1.5) * jj);
+        n[i] = h[i] - heq[i];
+    }
+    T pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const T wn = weight<T>(i) * n[i];
+        if (cx(i) != 0) pxx += wn;
+        if (cy(i) != 0) pyy += wn;
+        if (cz(i) != 0) pzz += wn;
+        MCLBM_SIGNED_ADD(pxy, cx(i) * cy(i), wn);
+        MCLBM_SIGNED_ADD(pxz, cx(i) * cz(i), wn);
+        MCLBM_SIGNED_ADD(pyz, cy(i) * cz(i), wn);
+    }
+    const T tr3 = (pxx + pyy + pzz) / T(3);
+    T s[Q], k[Q];
+    T sh = 0, hh = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int n2 = norm2(i);
+        if (n2 == 0 || n2 == 3) s[i] = 0;
+        else if (n2 == 1) s[i] = T(0.5) * inv_weight<T>(i) * ((cx(i) ? pxx : (cy(i) ? pyy : pzz)) - tr3);
+        else {
+            const T p = (cz(i) == 0) ? pxy : ((cy(i) == 0) ? pxz : pyz);
+            const int sg = (cz(i) == 0) ? cx(i) * cy(i) : ((cy(i) == 0) ? cx(i) * cz(i) : cy(i) * cz(i));
+            s[i] = (sg > 0 ? T(0.25) : -T(0.25)) * inv_weight<T>(i) * p;
+        }
+        k[i] = n[i] - s[i];
+        const T wk = weight<T>(i) * k[i] / (T(1) + heq[i]);
+        sh += wk * s[i];
+        hh += wk * k[i];
+    }
+    const T guard = sizeof(T) == 8 ? T(0) : T(kHHGuard);
+    T gamma = (hh <= guard) ? T(2) : T(2) / omega - (T(2) - T(2) / omega) * sh / hh;
+    if (hh > guard) {
+        // f*_i / w_i = 1 + (h_i - omega s_i) - g (omega / 2) k_i
+        T am1[Q], b[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            am1[i] = h[i] - omega * s[i];
+            b[i] = T(0.5) * omega * k[i];
+        }
+        gamma = exact_gamma_refine<T>(am1, b, omega, gamma, sizeof(T) == 8 ? 60 : 30, sizeof(T) == 8 ? T(1e-15) : T(1e-7));
+    }
+    const T bo = T(0.5) * omega * gamma;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const T hs = h[i] - omega * s[i] - bo * k[i];
+        f[i] = SHIFTED ? hs : weight<T>(i) * (T(1) + hs);
+    }
+    return gamma;
+}
+
 }  // namespace mclbm

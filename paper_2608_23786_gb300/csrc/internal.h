@@ -79,7 +79,8 @@ cudaError_t launch_wait_selftest(mclbm_ctx* c);
 cudaError_t launch_levels(mclbm_ctx* const* levels, int nlev, const LaunchConfig& cfg, cudaStream_t s, int* occ);
 bool vec_supported(int precision, int vec);
 bool launch_supported(int precision, const LaunchConfig& c);
-LaunchConfig default_launch(int precision, int pattern);
+LaunchConfig default_launch(int precision, int pattern, int options);
+int exact_vec(int precision);  // the one VEC of the exact-gamma kernel (kind 6)
 void leray_map(const double* X, int M, bool transpose, double* Y);  // api.cu
 cudaError_t launch_get_populations(const mclbm_ctx* c, int sample, double* d_out);
 cudaError_t launch_set_populations(mclbm_ctx* c, int sample, const double* d_in);

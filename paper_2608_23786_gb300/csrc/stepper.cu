@@ -268,11 +268,17 @@ cudaError_t launch_set_populations(mclbm_ctx* c, int sample, const double* d_in)
 
 bool launch_supported(int precision, const LaunchConfig& c)
 {
+    if (c.kind == 6) return c.block == 128 && c.vec == exact_vec(precision);
     if (c.kind == 1) return c.vec == 1 || c.vec == 2;
     if (c.kind < 0 || c.kind > 5 || c.kind == 1 || (c.block != 128 && c.block != 256)) return false;
     if (c.kind == 3 && (precision == MCLBM_FP64 || c.vec % 2 != 0)) return false;
     if (c.kind >= 4 && (!kAsyncKinds || precision == MCLBM_FP64 || c.block != 128)) return false;
     return vec_supported(precision, c.vec);
+}
+
+int exact_vec(int precision)
+{
+    return precision == MCLBM_FP64 ? kVecF64[0] : (precision == MCLBM_FP32 ? kVecF32[0] : kVecF16[0]);
 }
 
 bool vec_supported(int precision, int vec)
@@ -317,7 +323,7 @@ cudaError_t launch_wait_selftest(mclbm_ctx* c)
 // pull layout, same shape as the context's); the context's own state is not touched.
 cudaError_t launch_pull_explicit(mclbm_ctx* c, const void* src, void* dst)
 {
-    const LaunchConfig cfg = c->launch.kind == 1 ? default_launch(c->cfg.precision, MCLBM_PULL) : c->launch;
+    const LaunchConfig cfg = c->launch.kind == 1 ? default_launch(c->cfg.precision, MCLBM_PULL, c->cfg.options) : c->launch;
     switch (c->cfg.precision) {
         case MCLBM_FP64: {
             BatchArgs<double> a;

@@ -202,12 +202,22 @@ __device__ __forceinline__ void scatter_row(E* row, int x0, int N, int lane, con
 // Collide the VEC nodes of a run.  PACK (shifted storage, VEC even) runs the FP32
 // collision on node pairs in the packed FP32 pipe; the results are bit-identical to the
 // one-node form.
-template <class E, int VEC, bool PACK = false>
+template <class E, int VEC, bool PACK = false, bool EXACT = false>
 __device__ __forceinline__ void collide_run(typename Storage<E>::compute (&v)[Q][VEC], const LevelArgs<E>& L)
 {
     const typename Storage<E>::compute omega = omega_of<E>(L);
     using C = typename Storage<E>::compute;
-    if constexpr (PACK) {
+    if constexpr (EXACT) {  // exact entropic gamma (kind 6), node by node
+#pragma unroll 1
+        for (int k = 0; k < VEC; ++k) {
+            C t[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) t[i] = v[i][k];
+            kbc_exact<C, Storage<E>::shifted>(t, omega);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) v[i][k] = t[i];
+        }
+    } else if constexpr (PACK) {
         static_assert(Storage<E>::shifted && VEC % 2 == 0, "packed collision needs FP32 lanes in pairs");
 #pragma unroll
         for (int k = 0; k < VEC; k += 2) {
@@ -291,8 +301,8 @@ __device__ __forceinline__ void store_own_opp(E* base, const Geom& g, int64_t no
     }
 }
 
-// PATTERN: 0 pull, 1 AA.
-template <class E, int VEC, int PATTERN, int BLOCK>
+// PATTERN: 0 pull, 1 AA.  EXACT: the exact entropic gamma (launch kind 6).
+template <class E, int VEC, int PATTERN, int BLOCK, bool EXACT = false>
 __global__ void __launch_bounds__(BLOCK) k_step_batch(const BatchArgs<E> args)
 {
     using C = typename Storage<E>::compute;
@@ -314,17 +324,17 @@ __global__ void __launch_bounds__(BLOCK) k_step_batch(const BatchArgs<E> args)
         C v[Q][VEC];
         if constexpr (PATTERN == 0) {
             gather_all<E, VEC, false>(L.src + (int64_t)m * Q * g.n, g, x0, y, z, lane, v);
-            collide_run<E, VEC>(v, L);
+            collide_run<E, VEC, false, EXACT>(v, L);
             scatter_all<E, VEC, 0>(L.dst + (int64_t)m * Q * g.n, g, x0, y, z, lane, v);
         } else {
             E* base = L.dst + (int64_t)m * Q * g.n;
             if (L.parity == 0) {
                 load_own<E, VEC>(base, g, node, v);
-                collide_run<E, VEC>(v, L);
+                collide_run<E, VEC, false, EXACT>(v, L);
                 store_own_opp<E, VEC>(base, g, node, v);
             } else {
                 gather_all<E, VEC, true>(base, g, x0, y, z, lane, v);
-                collide_run<E, VEC>(v, L);
+                collide_run<E, VEC, false, EXACT>(v, L);
                 scatter_all<E, VEC, 1>(base, g, x0, y, z, lane, v);
             }
         }

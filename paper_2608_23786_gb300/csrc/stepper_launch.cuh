@@ -9,10 +9,10 @@
 
 namespace mclbm {
 
-template <class E, int VEC, int PATTERN, int BLOCK>
+template <class E, int VEC, int PATTERN, int BLOCK, bool EXACT = false>
 cudaError_t launch_variant(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, int* occupancy_out)
 {
-    auto kern = k_step_batch<E, VEC, PATTERN, BLOCK>;
+    auto kern = k_step_batch<E, VEC, PATTERN, BLOCK, EXACT>;
     static int occ = -1;  // resident blocks per SM of this variant (device-independent enough)
     if (occ < 0) {
         int o = 0;
@@ -108,7 +108,8 @@ cudaError_t launch_async_variant(const BatchArgs<E>& a, int grid_cap, cudaStream
 }
 
 template <class E, int PATTERN, int... VECS>
-cudaError_t launch_vec_block(const BatchArgs<E>& a, const LaunchConfig& cfg, int grid_cap, cudaStream_t s, int* occ)
+cudaError_t launch_vec_block_rest(const BatchArgs<E>& a, const LaunchConfig& cfg, int grid_cap, cudaStream_t s,
+                                  int* occ)
 {
     cudaError_t e = cudaErrorInvalidConfiguration;
     bool found = false;
@@ -154,6 +155,17 @@ cudaError_t launch_vec_block(const BatchArgs<E>& a, const LaunchConfig& cfg, int
     };
     (try_one(std::integral_constant<int, VECS>{}), ...);
     return e;
+}
+
+template <class E, int PATTERN, int FIRST_VEC, int... VECS>
+cudaError_t launch_vec_block(const BatchArgs<E>& a, const LaunchConfig& cfg, int grid_cap, cudaStream_t s, int* occ)
+{
+    // kind 6 (exact entropic gamma): the direct kernel, the type's first VEC, 128 threads
+    if (cfg.kind == 6) {
+        if (cfg.vec != FIRST_VEC || cfg.block != 128) return cudaErrorInvalidConfiguration;
+        return launch_variant<E, FIRST_VEC, PATTERN, 128, true>(a, grid_cap, s, occ);
+    }
+    return launch_vec_block_rest<E, PATTERN, FIRST_VEC, VECS...>(a, cfg, grid_cap, s, occ);
 }
 
 // Staged kernel: pick the number of stages so that two blocks fit on an SM, size the

@@ -14,20 +14,22 @@ class Ensemble:
 
     precision: "fp64" | "fp32" | "fp16"; pattern: "pull" | "aa"; lattice: 19 (D3Q19, the
     paper's velocity set, libmclbm.so) or 27 (D3Q27, libmclbm_d3q27.so); leray: initialise
-    with the Leray-projected perturbation (the paper's runs omit the projection).
+    with the Leray-projected perturbation (the paper's runs omit the projection); exact_gamma:
+    the exact entropic gamma of Eq. (kbc_entropy) instead of the closed form.
     """
 
     PREC = {"fp64": _m.FP64, "fp32": _m.FP32, "fp16": _m.FP16}
     PAT = {"pull": _m.PULL, "aa": _m.AA}
 
     def __init__(self, N, M, Re=None, nu=None, Ma=None, dt=0.0, precision="fp32", pattern="pull", seed=1,
-                 width=0.025, U_c=1.0, init_density=0, device=None, stream=None, lattice=19, leray=False):
+                 width=0.025, U_c=1.0, init_density=0, device=None, stream=None, lattice=19, leray=False,
+                 exact_gamma=False):
         if not torch.cuda.is_available():
             raise RuntimeError("Ensemble needs a CUDA device (there is no CPU path)")
         if nu is None:
             nu = 1.0 / Re
         self.device = torch.device(device if device is not None else "cuda")
-        options = _m.OPT_LERAY if leray else 0
+        options = (_m.OPT_LERAY if leray else 0) | (_m.OPT_EXACT_GAMMA if exact_gamma else 0)
         self.cfg = _m.Config(N=N, M=M, precision=self.PREC[precision], pattern=self.PAT[pattern], nu=nu,
                              Ma=Ma if Ma is not None else 0.0, dt=dt, U_c=U_c, width=width, seed=seed,
                              init_density=init_density, options=options)

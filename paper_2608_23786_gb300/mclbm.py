@@ -19,6 +19,7 @@ STATUS = {
 FP64, FP32, FP16 = 0, 1, 2
 PULL, AA = 0, 1
 OPT_LERAY = 1
+OPT_EXACT_GAMMA = 2
 Q = 19
 
 

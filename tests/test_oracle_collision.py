@@ -234,3 +234,24 @@ def test_exact_gamma_is_the_entropy_minimiser(seed):
     assert abs(root - ge) <= 1e-12 * abs(ge)
     np.testing.assert_allclose(fe, fstar(ge), rtol=1e-15, atol=1e-17)
     assert 0 < abs(ge - gc) < 0.1 * abs(gc)
+
+
+def test_exact_gamma_is_the_constrained_minimiser_near_equilibrium():
+    """Close to equilibrium the unconstrained entropy minimiser grows like 1/|Dh| (the polynomial
+    equilibrium is not an entropy minimiser); the exact gamma is the minimiser of H over
+    0 <= gamma <= 4/omega: no grid point of that interval has a smaller H."""
+    c, w, _ = oracle.lattice()
+    omega = 1.95
+    for seed in (60, 61, 62):
+        f = _random_node(seed, amp=1e-7)
+        _, _, ds, dh = oracle.collide(f, omega)
+        with oracle.exact_gamma():
+            _, ge, _, _ = oracle.collide(f, omega)
+        assert 0.0 <= ge <= 4.0 / omega
+
+        def H(gp):
+            x = f - omega * ds - 0.5 * omega * gp * dh
+            return np.sum(x * np.log(x / w))
+
+        grid = np.linspace(0.0, 4.0 / omega, 401)
+        assert H(ge) <= min(H(g) for g in grid) + 1e-15
