@@ -97,14 +97,25 @@ cudaError_t launch_async_fixed(const BatchArgs<E>& a, int grid_cap, cudaStream_t
     return cudaGetLastError();
 }
 
-// The ring kernels take the parity at run time for AA (one kernel for both parities).
+// AA launches whose levels share a parity take the ring kernel specialised for it (the
+// two-stage ring only; the three-stage one takes the parity at run time).
 template <class E, int VEC, int PATTERN, int BLOCK, int STAGES>
 cudaError_t launch_async_variant(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, int* occ)
 {
-    if constexpr (PATTERN == 0)
+    if constexpr (PATTERN == 0) {
         return launch_async_fixed<E, VEC, 0, BLOCK, 0, STAGES>(a, grid_cap, s, occ);
-    else
+    } else if constexpr (STAGES == 2 && kParitySpecialised) {
+        bool all_even = true, all_odd = true;
+        for (int l = 0; l < a.nlev; ++l) {
+            all_even = all_even && a.lev[l].parity == 0;
+            all_odd = all_odd && a.lev[l].parity == 1;
+        }
+        if (all_even) return launch_async_fixed<E, VEC, 1, BLOCK, 1, STAGES>(a, grid_cap, s, occ);
+        if (all_odd) return launch_async_fixed<E, VEC, 1, BLOCK, 2, STAGES>(a, grid_cap, s, occ);
         return launch_async_fixed<E, VEC, 1, BLOCK, -1, STAGES>(a, grid_cap, s, occ);
+    } else {
+        return launch_async_fixed<E, VEC, 1, BLOCK, -1, STAGES>(a, grid_cap, s, occ);
+    }
 }
 
 template <class E, int PATTERN, int... VECS>
