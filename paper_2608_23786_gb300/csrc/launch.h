@@ -30,8 +30,7 @@ struct LaunchConfig {
 constexpr int kVecF64[] = {1};
 constexpr int kVecF32[] = {2};
 constexpr int kVecF16[] = {4};
-constexpr bool kAsyncKinds = false;       // kinds 4 and 5
-constexpr bool kParitySpecialised = true;  // AA kernels per parity
+constexpr bool kAsyncKinds = false;  // kinds 4 and 5
 #else
 #define MCLBM_VECS_F64 1, 2
 #define MCLBM_VECS_F32 1, 2, 4
@@ -40,7 +39,6 @@ constexpr int kVecF64[] = {1, 2};
 constexpr int kVecF32[] = {1, 2, 4};
 constexpr int kVecF16[] = {2, 4, 8};
 constexpr bool kAsyncKinds = true;
-constexpr bool kParitySpecialised = true;
 #endif
 constexpr int kBlocks[] = {128, 256};
 

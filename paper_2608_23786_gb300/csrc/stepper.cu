@@ -297,11 +297,26 @@ cudaError_t launch_levels(mclbm_ctx* const* lv, int nlev, const LaunchConfig& cf
 {
     if (nlev < 1 || nlev > kMaxLevels) return cudaErrorInvalidValue;
     const int grid_cap = lv[0]->num_sms;
+    auto run = [&](mclbm_ctx* const* group, int n) {
+        switch (lv[0]->cfg.precision) {
+            case MCLBM_FP64: return levels_t<double>(group, n, cfg, grid_cap, s, occ);
+            case MCLBM_FP32: return levels_t<float>(group, n, cfg, grid_cap, s, occ);
+            default: return levels_t<__half>(group, n, cfg, grid_cap, s, occ);
+        }
+    };
     cudaError_t e;
-    switch (lv[0]->cfg.precision) {
-        case MCLBM_FP64: e = levels_t<double>(lv, nlev, cfg, grid_cap, s, occ); break;
-        case MCLBM_FP32: e = levels_t<float>(lv, nlev, cfg, grid_cap, s, occ); break;
-        default: e = levels_t<__half>(lv, nlev, cfg, grid_cap, s, occ); break;
+    // AA levels of different parity: one launch per parity, so that each takes the kernel
+    // specialised for its parity (the levels are independent, so the order does not matter)
+    mclbm_ctx* even[kMaxLevels];
+    mclbm_ctx* odd[kMaxLevels];
+    int ne = 0, no = 0;
+    if (lv[0]->cfg.pattern == MCLBM_AA && cfg.kind != 1)
+        for (int k = 0; k < nlev; ++k) (lv[k]->steps & 1 ? odd[no++] : even[ne++]) = lv[k];
+    if (ne > 0 && no > 0) {
+        e = run(even, ne);
+        if (e == cudaSuccess) e = run(odd, no);
+    } else {
+        e = run(lv, nlev);
     }
     if (e != cudaSuccess) return e;
     for (int k = 0; k < nlev; ++k) {

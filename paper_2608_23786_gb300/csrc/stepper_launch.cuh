@@ -51,24 +51,27 @@ cudaError_t launch_prefetch_fixed(const BatchArgs<E>& a, int grid_cap, cudaStrea
     return cudaGetLastError();
 }
 
-// Pull launches take the pull-only kernel; AA launches whose levels all share a parity take the
-// even- or odd-only kernel, mixed parities the general one.
+// Parity of an AA launch: the host launches AA levels of different parity separately
+// (launch_levels), so every launch here has one parity; -1 if not (not launched).
+template <class E>
+int launch_parity(const BatchArgs<E>& a)
+{
+    for (int l = 1; l < a.nlev; ++l)
+        if (a.lev[l].parity != a.lev[0].parity) return -1;
+    return a.lev[0].parity;
+}
+
+// Pull launches take the pull-only kernel, AA launches the kernel of their parity.
 template <class E, int VEC, int PATTERN, int BLOCK, bool PACK>
 cudaError_t launch_prefetch_variant(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, int* occ)
 {
     if constexpr (PATTERN == 0) {
         return launch_prefetch_fixed<E, VEC, 0, BLOCK, 0, PACK>(a, grid_cap, s, occ);
-    } else if constexpr (!kParitySpecialised) {
-        return launch_prefetch_fixed<E, VEC, 1, BLOCK, -1, PACK>(a, grid_cap, s, occ);
     } else {
-        bool all_even = true, all_odd = true;
-        for (int l = 0; l < a.nlev; ++l) {
-            all_even = all_even && a.lev[l].parity == 0;
-            all_odd = all_odd && a.lev[l].parity == 1;
-        }
-        if (all_even) return launch_prefetch_fixed<E, VEC, 1, BLOCK, 1, PACK>(a, grid_cap, s, occ);
-        if (all_odd) return launch_prefetch_fixed<E, VEC, 1, BLOCK, 2, PACK>(a, grid_cap, s, occ);
-        return launch_prefetch_fixed<E, VEC, 1, BLOCK, -1, PACK>(a, grid_cap, s, occ);
+        const int par = launch_parity(a);
+        if (par == 0) return launch_prefetch_fixed<E, VEC, 1, BLOCK, 1, PACK>(a, grid_cap, s, occ);
+        if (par == 1) return launch_prefetch_fixed<E, VEC, 1, BLOCK, 2, PACK>(a, grid_cap, s, occ);
+        return cudaErrorInvalidValue;
     }
 }
 
@@ -97,24 +100,16 @@ cudaError_t launch_async_fixed(const BatchArgs<E>& a, int grid_cap, cudaStream_t
     return cudaGetLastError();
 }
 
-// AA launches whose levels share a parity take the ring kernel specialised for it (the
-// two-stage ring only; the three-stage one takes the parity at run time).
 template <class E, int VEC, int PATTERN, int BLOCK, int STAGES>
 cudaError_t launch_async_variant(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, int* occ)
 {
     if constexpr (PATTERN == 0) {
         return launch_async_fixed<E, VEC, 0, BLOCK, 0, STAGES>(a, grid_cap, s, occ);
-    } else if constexpr (STAGES == 2 && kParitySpecialised) {
-        bool all_even = true, all_odd = true;
-        for (int l = 0; l < a.nlev; ++l) {
-            all_even = all_even && a.lev[l].parity == 0;
-            all_odd = all_odd && a.lev[l].parity == 1;
-        }
-        if (all_even) return launch_async_fixed<E, VEC, 1, BLOCK, 1, STAGES>(a, grid_cap, s, occ);
-        if (all_odd) return launch_async_fixed<E, VEC, 1, BLOCK, 2, STAGES>(a, grid_cap, s, occ);
-        return launch_async_fixed<E, VEC, 1, BLOCK, -1, STAGES>(a, grid_cap, s, occ);
     } else {
-        return launch_async_fixed<E, VEC, 1, BLOCK, -1, STAGES>(a, grid_cap, s, occ);
+        const int par = launch_parity(a);
+        if (par == 0) return launch_async_fixed<E, VEC, 1, BLOCK, 1, STAGES>(a, grid_cap, s, occ);
+        if (par == 1) return launch_async_fixed<E, VEC, 1, BLOCK, 2, STAGES>(a, grid_cap, s, occ);
+        return cudaErrorInvalidValue;
     }
 }
 
