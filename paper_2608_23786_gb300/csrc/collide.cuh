@@ -320,47 +320,48 @@ __device__ __forceinline__ V kbc_shifted(V (&h)[Q], float omega, float a, float 
 
 #else  // MCLBM_D3Q27
 
-// D3Q27 form of kbc_shifted: the same operations written over the 13 opposite pairs by
-// velocity class (faces, edges, corners).  The shear part is D_aa / 2 on faces, s l P_ab / 4
-// on edges and 0 on corners; normalised by the weights, s = D_aa / (2 w1) and
-// s l P_ab / (4 w2).  P_ab includes the corners.
+// D3Q27 form of kbc_shifted: the same operations written out over the 13 opposite pairs
+// (p = 0..2 faces, 3..8 edges as in D3Q19, 9..12 corners (+++), (++-), (+-+), (+--)).  The
+// shear part is D_aa / 2 on faces, s l P_ab / 4 on edges and 0 on corners; normalised by the
+// weights, s = D_aa / (2 w1) = 6.75 D_aa and s l P_ab / (4 w2) = +-13.5 P_ab.  P_ab includes
+// the corners.  As in the D3Q19 form, constant factors enter as operands of single operations.
+constexpr bool d3q27_order_holds()
+{
+    return cx(19) == 1 && cy(19) == 1 && cz(19) == 1 && cx(21) == 1 && cy(21) == 1 && cz(21) == -1 &&
+           cx(23) == 1 && cy(23) == -1 && cz(23) == 1 && cx(25) == 1 && cy(25) == -1 && cz(25) == -1;
+}
+static_assert(d3q27_order_holds(), "kbc_shifted assumes the library's D3Q27 corner order");
+
 template <class V>
 __device__ __forceinline__ V kbc_shifted(V (&h)[Q], float omega, float a, float b)
 {
     using namespace lanes;
-    constexpr int NP = (Q - 1) / 2;
-    const V one = bc<V>(1.f), zero = bc<V>(0.f);
+    const V one = bc<V>(1.f);
+    const V W0 = bc<V>(8.0f / 27.0f), W1 = bc<V>(2.0f / 27.0f), W2 = bc<V>(1.0f / 54.0f), W3 = bc<V>(1.0f / 216.0f);
     const auto frcp = [](float x) { return rcp_approx(x); };
-    V S[4] = {zero, zero, zero, zero};   // sum of h per class (1 faces, 2 edges, 3 corners)
-    V J[4][3];                           // sum of c h per class and axis
-#pragma unroll
-    for (int k = 0; k < 4; ++k) J[k][0] = J[k][1] = J[k][2] = zero;
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-        const int i = 2 * p + 1, k = norm2(i);
-        S[k] = add(S[k], add(h[i], h[i + 1]));
-        const V d = sub(h[i], h[i + 1]);
-        if (cx(i) > 0) J[k][0] = add(J[k][0], d);
-        if (cy(i) > 0) J[k][1] = add(J[k][1], d);
-        else if (cy(i) < 0) J[k][1] = sub(J[k][1], d);
-        if (cz(i) > 0) J[k][2] = add(J[k][2], d);
-        else if (cz(i) < 0) J[k][2] = sub(J[k][2], d);
-    }
-    const V W0 = bc<V>(weight<float>(0)), W1 = bc<V>(weight<float>(1)), W2 = bc<V>(weight<float>(7)),
-            W3 = bc<V>(weight<float>(19));
-    const V drho = fma(W0, h[0], fma(W1, S[1], fma(W2, S[2], mul(W3, S[3]))));
+    // density deviation and momentum
+    const V s1 = add(add(add(h[1], h[2]), add(h[3], h[4])), add(h[5], h[6]));
+    const V s2 = add(add(add(add(h[7], h[8]), add(h[9], h[10])), add(add(h[11], h[12]), add(h[13], h[14]))),
+                     add(add(h[15], h[16]), add(h[17], h[18])));
+    const V s3 = add(add(add(h[19], h[20]), add(h[21], h[22])), add(add(h[23], h[24]), add(h[25], h[26])));
+    const V drho = fma(W0, h[0], fma(W1, s1, fma(W2, s2, mul(W3, s3))));
     const V rho = add(one, drho);
-    V j3[3];
+    V d[13];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) j3[c] = fma(W1, J[1][c], fma(W2, J[2][c], mul(W3, J[3][c])));
-    const V jx = j3[0], jy = j3[1], jz = j3[2];
+    for (int p = 0; p < 13; ++p) d[p] = sub(h[2 * p + 1], h[2 * p + 2]);
+    const V jx = fma(W1, d[0], fma(W2, add(add(d[3], d[4]), add(d[5], d[6])),
+                                   mul(W3, add(add(d[9], d[10]), add(d[11], d[12])))));
+    const V jy = fma(W1, d[1], fma(W2, add(sub(d[3], d[4]), add(d[7], d[8])),
+                                   mul(W3, sub(add(d[9], d[10]), add(d[11], d[12])))));
+    const V jz = fma(W1, d[2], fma(W2, add(sub(d[5], d[6]), sub(d[7], d[8])),
+                                   mul(W3, add(sub(d[9], d[10]), sub(d[11], d[12])))));
     const V rinv = map(rho, frcp);
     const V jj15 = mul(bc<V>(-1.5f), fma(jx, jx, fma(jy, jy, mul(jz, jz))));
     V heq[Q], n[Q];
     heq[0] = fma(jj15, rinv, drho);
     n[0] = sub(h[0], heq[0]);
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
+    for (int p = 0; p < 13; ++p) {
         const int i = 2 * p + 1;
         const V cj = c_dot(i, jx, jy, jz);
         const V q = fma(rinv, fma(bc<V>(4.5f), mul(cj, cj), jj15), drho);
@@ -369,81 +370,84 @@ __device__ __forceinline__ V kbc_shifted(V (&h)[Q], float omega, float a, float 
         n[i] = sub(h[i], heq[i]);
         n[i + 1] = sub(h[i + 1], heq[i + 1]);
     }
-    // second moments of f^neq (normalised): P_ab = sum w c_a c_b n, by class
-    V Pd[4][3], Po[4][3];  // diagonal (aa) and off-diagonal (xy, xz, yz) partial sums
+    // second moments of f^neq (normalised): pair sums A_p = n_i + n_{i+1}
+    V A[13];
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) Pd[k][c] = Po[k][c] = zero;
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-        const int i = 2 * p + 1, k = norm2(i);
-        const V s2 = add(n[i], n[i + 1]);
-        if (cx(i) != 0) Pd[k][0] = add(Pd[k][0], s2);
-        if (cy(i) != 0) Pd[k][1] = add(Pd[k][1], s2);
-        if (cz(i) != 0) Pd[k][2] = add(Pd[k][2], s2);
-        const int sxy = cx(i) * cy(i), sxz = cx(i) * cz(i), syz = cy(i) * cz(i);
-        if (sxy > 0) Po[k][0] = add(Po[k][0], s2);
-        else if (sxy < 0) Po[k][0] = sub(Po[k][0], s2);
-        if (sxz > 0) Po[k][1] = add(Po[k][1], s2);
-        else if (sxz < 0) Po[k][1] = sub(Po[k][1], s2);
-        if (syz > 0) Po[k][2] = add(Po[k][2], s2);
-        else if (syz < 0) Po[k][2] = sub(Po[k][2], s2);
-    }
-    V Pdd[3], Pod[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        Pdd[c] = fma(W1, Pd[1][c], fma(W2, Pd[2][c], mul(W3, Pd[3][c])));
-        Pod[c] = fma(W2, Po[2][c], mul(W3, Po[3][c]));
-    }
-    const V tr3 = mul(add(add(Pdd[0], Pdd[1]), Pdd[2]), bc<V>(1.0f / 3.0f));
-    // shear part normalised by w, per pair: faces D_aa / (2 w1), edges s l P_ab / (4 w2)
-    const float cf = 0.5f * inv_weight<float>(1), ce = 0.25f * inv_weight<float>(7);
-    V sp[NP];
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-        const int i = 2 * p + 1, k = norm2(i);
-        if (k == 1) {
-            const int c = cx(i) ? 0 : (cy(i) ? 1 : 2);
-            sp[p] = mul(bc<V>(cf), sub(Pdd[c], tr3));
-        } else if (k == 2) {
-            const int c = cz(i) == 0 ? 0 : (cy(i) == 0 ? 1 : 2);
-            const int sg = c == 0 ? cx(i) * cy(i) : (c == 1 ? cx(i) * cz(i) : cy(i) * cz(i));
-            sp[p] = mul(bc<V>(sg > 0 ? ce : -ce), Pod[c]);
-        } else {
-            sp[p] = zero;
-        }
-    }
+    for (int p = 0; p < 13; ++p) A[p] = add(n[2 * p + 1], n[2 * p + 2]);
+    const V exy = add(A[3], A[4]), exz = add(A[5], A[6]), eyz = add(A[7], A[8]);
+    const V cs = add(add(A[9], A[10]), add(A[11], A[12]));  // every corner has c_a^2 = 1
+    const V cxy = sub(add(A[9], A[10]), add(A[11], A[12]));
+    const V cxz = add(sub(A[9], A[10]), sub(A[11], A[12]));
+    const V cyz = sub(sub(A[9], A[10]), sub(A[11], A[12]));
+    const V pxx = fma(W1, A[0], fma(W2, add(exy, exz), mul(W3, cs)));
+    const V pyy = fma(W1, A[1], fma(W2, add(exy, eyz), mul(W3, cs)));
+    const V pzz = fma(W1, A[2], fma(W2, add(exz, eyz), mul(W3, cs)));
+    const V tr3 = mul(add(add(pxx, pyy), pzz), bc<V>(1.0f / 3.0f));
+    V D[6];
+    D[0] = sub(pxx, tr3);
+    D[1] = sub(pyy, tr3);
+    D[2] = sub(pzz, tr3);
+    D[3] = fma(W2, sub(A[3], A[4]), mul(W3, cxy));  // P_xy
+    D[4] = fma(W2, sub(A[5], A[6]), mul(W3, cxz));  // P_xz
+    D[5] = fma(W2, sub(A[7], A[8]), mul(W3, cyz));  // P_yz
     // k = n - s;  <Ds|Dh> = sum w s k / (1 + heq),  <Dh|Dh> = sum w k^2 / (1 + heq)
-    V k[Q];
+    V k[Q], B[9];
     k[0] = n[0];
     const V kr0 = mul(k[0], map(add(one, heq[0]), frcp));
-    V HH[4] = {zero, zero, zero, zero}, SH[4] = {zero, zero, zero, zero};
-    HH[0] = mul(kr0, k[0]);
+    V hf = bc<V>(0.f), he = bc<V>(0.f), hc = bc<V>(0.f);
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
-        const int i = 2 * p + 1, cl = norm2(i);
-        k[i] = sub(n[i], sp[p]);
-        k[i + 1] = sub(n[i + 1], sp[p]);
+    for (int p = 0; p < 13; ++p) {
+        const int i = 2 * p + 1;
+        if (p < 9) {
+            const V Dp = D[p < 3 ? p : 3 + (p - 3) / 2];
+            const float ms = p < 3 ? -6.75f : ((p - 3) % 2 == 1 ? 13.5f : -13.5f);  // -s / D
+            k[i] = fma(Dp, bc<V>(ms), n[i]);
+            k[i + 1] = fma(Dp, bc<V>(ms), n[i + 1]);
+        } else {
+            k[i] = n[i];
+            k[i + 1] = n[i + 1];
+        }
         const V ka = mul(k[i], map(add(one, heq[i]), frcp));
         const V kb = mul(k[i + 1], map(add(one, heq[i + 1]), frcp));
-        HH[cl] = fma(kb, k[i + 1], fma(ka, k[i], HH[cl]));
-        if (cl < 3) SH[cl] = fma(sp[p], add(ka, kb), SH[cl]);
+        if (p < 9) B[p] = add(ka, kb);
+        if (p == 0)
+            hf = fma(kb, k[i + 1], mul(ka, k[i]));
+        else if (p < 3)
+            hf = fma(kb, k[i + 1], fma(ka, k[i], hf));
+        else if (p == 3)
+            he = fma(kb, k[i + 1], mul(ka, k[i]));
+        else if (p < 9)
+            he = fma(kb, k[i + 1], fma(ka, k[i], he));
+        else if (p == 9)
+            hc = fma(kb, k[i + 1], mul(ka, k[i]));
+        else
+            hc = fma(kb, k[i + 1], fma(ka, k[i], hc));
     }
-    const V hh = fma(W0, HH[0], fma(W1, HH[1], fma(W2, HH[2], mul(W3, HH[3]))));
-    const V sh = fma(W1, SH[1], mul(W2, SH[2]));
+    // sh = w1 sum_faces 6.75 D (ka + kb) + w2 sum_edges (+-13.5 P)(ka + kb): w1 6.75 = 1/2,
+    // w2 13.5 = 1/4
+    const V sf = fma(D[0], B[0], fma(D[1], B[1], mul(D[2], B[2])));
+    const V se = fma(D[3], sub(B[3], B[4]), fma(D[4], sub(B[5], B[6]), mul(D[5], sub(B[7], B[8]))));
+    const V sh = fma(bc<V>(0.5f), sf, mul(bc<V>(0.25f), se));
+    const V hh = fma(W0, mul(kr0, k[0]), fma(W1, hf, fma(W2, he, mul(W3, hc))));
     const V gamma = map(hh, sh, [a, b](float hs, float ss) {
         return hs <= kHHGuard ? 2.0f : fma(-b, mul(ss, rcp_approx(hs)), a);
     });
     // f* = f^eq + (1 - omega) Ds + (1 - beta) Dh
     const V omb = fma(bc<V>(-0.5f * omega), gamma, one);
-    const V om1 = bc<V>(1.0f - omega);
     h[0] = fma(omb, k[0], heq[0]);
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
+    for (int p = 0; p < 13; ++p) {
         const int i = 2 * p + 1;
-        h[i] = fma(omb, k[i], fma(om1, sp[p], heq[i]));
-        h[i + 1] = fma(omb, k[i + 1], fma(om1, sp[p], heq[i + 1]));
+        if (p < 9) {
+            const float sd = p < 3 ? 6.75f : ((p - 3) % 2 == 1 ? -13.5f : 13.5f);  // s / D
+            const V cs1 = bc<V>(sd * (1.0f - omega));
+            const V Dp = D[p < 3 ? p : 3 + (p - 3) / 2];
+            h[i] = fma(omb, k[i], fma(Dp, cs1, heq[i]));
+            h[i + 1] = fma(omb, k[i + 1], fma(Dp, cs1, heq[i + 1]));
+        } else {
+            h[i] = fma(omb, k[i], heq[i]);
+            h[i + 1] = fma(omb, k[i + 1], heq[i + 1]);
+        }
     }
     return gamma;
 }

@@ -208,7 +208,7 @@ __device__ __forceinline__ void collide_run(typename Storage<E>::compute (&v)[Q]
     const typename Storage<E>::compute omega = omega_of<E>(L);
     using C = typename Storage<E>::compute;
     if constexpr (EXACT) {  // exact entropic gamma (kind 6), node by node
-#pragma unroll 1
+#pragma unroll
         for (int k = 0; k < VEC; ++k) {
             C t[Q];
 #pragma unroll
