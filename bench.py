@@ -308,13 +308,15 @@ def run_adjoint(args):
     import torch
     from paper_2608_23786_gb300 import Ensemble, mclbm
     import ensemble_inputs as gen
-    mclbm.load()
+    Q = args.lattice
+    mclbm.load(lattice=Q)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     M, T, K = args.M or 16, args.T, 50
     X = gen.draw_params(1, M)
-    ens = Ensemble(64, M, Re=800.0, Ma=0.025, precision="fp32", pattern="pull", device=dev, stream=stream).init(X)
+    ens = Ensemble(64, M, Re=800.0, Ma=0.025, precision="fp32", pattern="pull", device=dev, stream=stream,
+                   lattice=Q).init(X)
     need = mclbm.mclbm_grad_required_bytes(ens.ctx, T, K)
     gbuf = torch.empty(need + 256, dtype=torch.uint8, device=dev)
     gptr = (gbuf.data_ptr() + 255) // 256 * 256
@@ -333,17 +335,18 @@ def run_adjoint(args):
     ph /= args.steps
     lu = M * 64**3 * T
     peaks, peak_kind = measured_peaks()
-    rev_bytes = 3 * 19 * 4 * lu
+    rev_bytes = 3 * Q * 4 * lu
     achieved = rev_bytes / (ph[2] / 1e3) / 1e9
     out = {
         "metric": "adjoint_glups", "value": lu * args.steps / sec / 1e9, "unit": "GLUPS (whole gradient)",
         "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": sec / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"rtgv_64cube_x{M}_fp32_{T}steps_ckpt{K}_dE", "l2": "inputs larger than L2"},
+        "config": {"workload": f"rtgv_64cube_x{M}_fp32_{T}steps_ckpt{K}_dE", "lattice": f"D3Q{Q}",
+                   "l2": "inputs larger than L2"},
         "phases_ms": {"forward": ph[0], "recompute": ph[1], "reverse": ph[2], "reduction": ph[3]},
         "roofline": {"kernel": "k_adjoint_async<float,2,2>", "bound": "hbm", "achieved": achieved,
                      "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                     "peak_kind": peak_kind, "traffic": None, "algorithmic_bytes_per_lu": 3 * 19 * 4,
+                     "peak_kind": peak_kind, "traffic": None, "algorithmic_bytes_per_lu": 3 * Q * 4,
                      "reverse_glups": lu / (ph[2] / 1e3) / 1e9},
         "grad_finite": bool(np.all(np.isfinite(G))), "clocks": clk.summary(),
     }

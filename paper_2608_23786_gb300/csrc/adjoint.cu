@@ -81,12 +81,14 @@ constexpr int kRunBlock = 128;
 
 // Shared-memory ring of the adjoint run kernel: per stage, the Q state vectors, the Q lambda^{t+1}
 // vectors and the edge words (state and lambda, x-moving populations only) of every thread.
-template <class E, int VEC, int STAGES>
+// WRAP: every x-row lies within one warp (N <= 32 VEC), the periodic neighbours of a row's end
+// runs are in the same warp, and the ring holds no edge words.
+template <class E, int VEC, int STAGES, bool WRAP>
 struct AdjRing {
     static constexpr int kVS = VEC * (int)sizeof(E), kVL = VEC * 4;
     static constexpr int kStateBytes = STAGES * Q * kRunBlock * kVS;
     static constexpr int kLamBytes = STAGES * Q * kRunBlock * kVL;
-    static constexpr int kBytes = kStateBytes + kLamBytes + STAGES * 2 * kEdges * kRunBlock * 4;
+    static constexpr int kBytes = kStateBytes + kLamBytes + (WRAP ? 0 : STAGES * 2 * kEdges * kRunBlock * 4);
     __device__ __forceinline__ static int state_off(int stage, int i, int tid) { return ((stage * Q + i) * kRunBlock + tid) * kVS; }
     __device__ __forceinline__ static int lam_off(int stage, int i, int tid)
     {
@@ -116,12 +118,12 @@ __device__ __forceinline__ RunPos run_pos(const Geom& g, int64_t t, int vec)
 }
 
 // Issue the copies of one run: state f_i(x) from slot i of x - c_i, lambda^{t+1} from slot i of x + c_i.
-template <class E, int VEC, int STAGES, int I = 0>
+template <class E, int VEC, int STAGES, bool WRAP, int I = 0>
 __device__ __forceinline__ void adj_issue(const E* sbase, const float* lbase, const Geom& g, const RunPos& p, int lane,
                                           uint32_t smem, int stage)
 {
     if constexpr (I < Q) {
-        using Ring = AdjRing<E, VEC, STAGES>;
+        using Ring = AdjRing<E, VEC, STAGES, WRAP>;
         const int tid = threadIdx.x;
         const E* srow = sbase + (int64_t)I * g.n + g.node(0, g.wrap(p.y - Dir<I>::y), g.wrap(p.z - Dir<I>::z));
         const float* lrow = lbase + (int64_t)I * g.n + g.node(0, g.wrap(p.y + Dir<I>::y), g.wrap(p.z + Dir<I>::z));
@@ -129,25 +131,26 @@ __device__ __forceinline__ void adj_issue(const E* sbase, const float* lbase, co
         cp_async<Ring::kVL>(smem + Ring::lam_off(stage, I, tid), lrow + p.x0);
         const bool first = lane == 0 || p.x0 == 0, last = lane == 31 || p.x0 + VEC == g.N;
         const int before = (p.x0 - 1) & (g.N - 1), after = (p.x0 + VEC) & (g.N - 1);
-        if constexpr (Dir<I>::x > 0) {  // state from x - 1, lambda from x + 1
+        if constexpr (WRAP) {
+        } else if constexpr (Dir<I>::x > 0) {  // state from x - 1, lambda from x + 1
             if (first) cp_async<4>(smem + Ring::edge_off(stage, 0, I, tid), edge_word(srow, before));
             if (last) cp_async<4>(smem + Ring::edge_off(stage, 1, I, tid), lrow + after);
         } else if constexpr (Dir<I>::x < 0) {  // state from x + 1, lambda from x - 1
             if (last) cp_async<4>(smem + Ring::edge_off(stage, 0, I, tid), edge_word(srow, after));
             if (first) cp_async<4>(smem + Ring::edge_off(stage, 1, I, tid), lrow + before);
         }
-        adj_issue<E, VEC, STAGES, I + 1>(sbase, lbase, g, p, lane, smem, stage);
+        adj_issue<E, VEC, STAGES, WRAP, I + 1>(sbase, lbase, g, p, lane, smem, stage);
     }
 }
 
-template <class T, int VEC, int CXI>
+template <class T, int VEC, int CXI, bool WRAP>
 __device__ __forceinline__ RawRun<T, VEC> adj_raw(const unsigned char* smem, int vec_off, int edge_off)
 {
     using R = typename RawOf<VEC * sizeof(T)>::type;
     RawRun<T, VEC> r;
     const R w = *reinterpret_cast<const R*>(smem + vec_off);
     memcpy(r.w, &w, sizeof(R));
-    if constexpr (CXI != 0) {
+    if constexpr (CXI != 0 && !WRAP) {
         const unsigned int e = *reinterpret_cast<const unsigned int*>(smem + edge_off);
         if constexpr (sizeof(T) == 2) {  // source x - 1 is odd (high half), x + VEC even (low half)
             const unsigned short hv = CXI > 0 ? (unsigned short)(e >> 16) : (unsigned short)(e & 0xffffu);
@@ -159,20 +162,50 @@ __device__ __forceinline__ RawRun<T, VEC> adj_raw(const unsigned char* smem, int
     return r;
 }
 
-template <class E, int VEC, int STAGES, int I = 0>
+// The x-shift of a run when every x-row lies within one warp: a row is L = N / VEC consecutive
+// lanes (L divides 32, N being a power of two), and the element before (after) the row's first
+// (last) run is the row's last (first) element, read with one shuffle inside the row's lanes.
+template <class E, int VEC, int CXI>
+__device__ __forceinline__ void finish_row_wrap(const RawRun<E, VEC>& r, int L, int lane,
+                                                typename Storage<E>::compute (&v)[VEC])
+{
+    if constexpr (CXI == 0) {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) v[k] = to_c<E>(r.w[k]);
+    } else {
+        const int row = lane & ~(L - 1);
+        if constexpr (CXI > 0) {
+            const E prev = __shfl_sync(0xffffffffu, r.w[VEC - 1], row | ((lane - 1) & (L - 1)));
+            v[0] = to_c<E>(prev);
+#pragma unroll
+            for (int k = 1; k < VEC; ++k) v[k] = to_c<E>(r.w[k - 1]);
+        } else {
+            const E next = __shfl_sync(0xffffffffu, r.w[0], row | ((lane + 1) & (L - 1)));
+#pragma unroll
+            for (int k = 0; k < VEC - 1; ++k) v[k] = to_c<E>(r.w[k + 1]);
+            v[VEC - 1] = to_c<E>(next);
+        }
+    }
+}
+
+template <class E, int VEC, int STAGES, bool WRAP, int I = 0>
 __device__ __forceinline__ void adj_finish(const unsigned char* smem, int stage, const Geom& g, const RunPos& p,
                                            int lane, float (&hv)[Q][VEC], float (&mv)[Q][VEC])
 {
     if constexpr (I < Q) {
-        using Ring = AdjRing<E, VEC, STAGES>;
+        using Ring = AdjRing<E, VEC, STAGES, WRAP>;
         const int tid = threadIdx.x;
-        const RawRun<E, VEC> rs = adj_raw<E, VEC, Dir<I>::x>(smem, Ring::state_off(stage, I, tid),
-                                                             Ring::edge_off(stage, 0, I, tid));
-        finish_row<E, VEC, Dir<I>::x>(rs, p.x0, g.N, lane, hv[I]);
-        const RawRun<float, VEC> rl = adj_raw<float, VEC, -Dir<I>::x>(smem, Ring::lam_off(stage, I, tid),
-                                                                      Ring::edge_off(stage, 1, I, tid));
-        finish_row<float, VEC, -Dir<I>::x>(rl, p.x0, g.N, lane, mv[I]);
-        adj_finish<E, VEC, STAGES, I + 1>(smem, stage, g, p, lane, hv, mv);
+        const int eo0 = WRAP ? 0 : Ring::edge_off(stage, 0, I, tid), eo1 = WRAP ? 0 : Ring::edge_off(stage, 1, I, tid);
+        const RawRun<E, VEC> rs = adj_raw<E, VEC, Dir<I>::x, WRAP>(smem, Ring::state_off(stage, I, tid), eo0);
+        const RawRun<float, VEC> rl = adj_raw<float, VEC, -Dir<I>::x, WRAP>(smem, Ring::lam_off(stage, I, tid), eo1);
+        if constexpr (WRAP) {
+            finish_row_wrap<E, VEC, Dir<I>::x>(rs, g.N / VEC, lane, hv[I]);
+            finish_row_wrap<float, VEC, -Dir<I>::x>(rl, g.N / VEC, lane, mv[I]);
+        } else {
+            finish_row<E, VEC, Dir<I>::x>(rs, p.x0, g.N, lane, hv[I]);
+            finish_row<float, VEC, -Dir<I>::x>(rl, p.x0, g.N, lane, mv[I]);
+        }
+        adj_finish<E, VEC, STAGES, WRAP, I + 1>(smem, stage, g, p, lane, hv, mv);
     }
 }
 
@@ -182,7 +215,7 @@ __device__ __forceinline__ void adj_finish(const unsigned char* smem, int stage,
 // and lambda^{t+1} are copied into shared memory (cp.async, STAGES - 1 runs ahead) during the
 // current run's product; each thread reads back only its own slots after its own wait_group (no
 // block barrier, no spin).
-template <class E, int VEC, int STAGES>
+template <class E, int VEC, int STAGES, bool WRAP>
 __global__ void __launch_bounds__(kRunBlock) k_adjoint_async(const E* __restrict__ state,
                                                              const float* __restrict__ lam_next,
                                                              float* __restrict__ lam_out, Geom g, int64_t runs,
@@ -200,8 +233,8 @@ __global__ void __launch_bounds__(kRunBlock) k_adjoint_async(const E* __restrict
         const int64_t ts = t + s * stride;
         if (ts < runs) {
             const RunPos p = run_pos(g, ts, VEC);
-            adj_issue<E, VEC, STAGES>(state + (int64_t)p.m * Q * g.n, lam_next + (int64_t)p.m * Q * g.n, g, p, lane,
-                                      sbase, s);
+            adj_issue<E, VEC, STAGES, WRAP>(state + (int64_t)p.m * Q * g.n, lam_next + (int64_t)p.m * Q * g.n, g, p,
+                                            lane, sbase, s);
         }
         cp_async_commit();
     }
@@ -212,14 +245,14 @@ __global__ void __launch_bounds__(kRunBlock) k_adjoint_async(const E* __restrict
             const RunPos p = run_pos(g, ta, VEC);
             int sa = stage + STAGES - 1;
             if (sa >= STAGES) sa -= STAGES;
-            adj_issue<E, VEC, STAGES>(state + (int64_t)p.m * Q * g.n, lam_next + (int64_t)p.m * Q * g.n, g, p, lane,
-                                      sbase, sa);
+            adj_issue<E, VEC, STAGES, WRAP>(state + (int64_t)p.m * Q * g.n, lam_next + (int64_t)p.m * Q * g.n, g, p,
+                                            lane, sbase, sa);
         }
         cp_async_commit();
         cp_async_wait<STAGES - 1>();
         const RunPos p = run_pos(g, t, VEC);
         float hv[Q][VEC], mv[Q][VEC];
-        adj_finish<E, VEC, STAGES>(smem, stage, g, p, lane, hv, mv);
+        adj_finish<E, VEC, STAGES, WRAP>(smem, stage, g, p, lane, hv, mv);
         float2 h2[Q], m2[Q], l2[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
@@ -407,6 +440,31 @@ GradLayout grad_layout(const mclbm_ctx* c, int64_t nsteps, int K)
     return L;
 }
 
+// Occupancy-sized launch of the adjoint run kernel (two ring stages; resident blocks per SM
+// queried once per instantiation).
+template <class E, int VEC, bool WRAP>
+cudaError_t launch_adjoint_async(mclbm_ctx* c, const Geom& g, int64_t runs, const void* state, const void* lin,
+                                 void* lout, float om, float a, float b)
+{
+    constexpr int kStages = 2;
+    auto kern = k_adjoint_async<E, VEC, kStages, WRAP>;
+    constexpr int smem = AdjRing<E, VEC, kStages, WRAP>::kBytes;
+    static int occ = -1;
+    if (occ < 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        int o = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kRunBlock, smem);
+        if (e != cudaSuccess) return e;
+        occ = o > 0 ? o : 1;
+    }
+    int64_t blocks = (runs + kRunBlock - 1) / kRunBlock;
+    if (blocks > (int64_t)c->num_sms * occ) blocks = (int64_t)c->num_sms * occ;
+    kern<<<(unsigned)blocks, kRunBlock, smem, c->stream>>>((const E*)state, (const float*)lin, (float*)lout, g, runs,
+                                                           om, a, b);
+    return cudaGetLastError();
+}
+
 template <class E>
 cudaError_t adjoint_step_t(mclbm_ctx* c, const void* state, const void* lin, void* lout)
 {
@@ -417,25 +475,12 @@ cudaError_t adjoint_step_t(mclbm_ctx* c, const void* state, const void* lin, voi
     } else {
         constexpr int kVec = 2;
         const int64_t runs = (int64_t)c->M * c->n / kVec;
-        int64_t blocks = (runs + kRunBlock - 1) / kRunBlock;
-        if (blocks > (int64_t)c->num_sms * 16) blocks = (int64_t)c->num_sms * 16;
         const float om = (float)c->units.omega;
         const float a = (float)(2.0 / c->units.omega), b = (float)(2.0 - 2.0 / c->units.omega);
-        constexpr int kStages = 2;
-        auto kern = k_adjoint_async<E, kVec, kStages>;
-        constexpr int smem = AdjRing<E, kVec, kStages>::kBytes;
-        static int occ = -1;  // resident blocks per SM (per element type)
-        if (occ < 0) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (e != cudaSuccess) return e;
-            int o = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kRunBlock, smem);
-            if (e != cudaSuccess) return e;
-            occ = o > 0 ? o : 1;
-        }
-        if (blocks > (int64_t)c->num_sms * occ) blocks = (int64_t)c->num_sms * occ;
-        kern<<<(unsigned)blocks, kRunBlock, smem, c->stream>>>((const E*)state, (const float*)lin, (float*)lout, g,
-                                                               runs, om, a, b);
+        const cudaError_t e = c->N <= 32 * kVec
+                                  ? launch_adjoint_async<E, kVec, true>(c, g, runs, state, lin, lout, om, a, b)
+                                  : launch_adjoint_async<E, kVec, false>(c, g, runs, state, lin, lout, om, a, b);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }

@@ -371,33 +371,225 @@ __device__ __forceinline__ void kbc_vjp_shifted(const V (&h)[Q], const V (&mu)[Q
 
 #else  // MCLBM_D3Q27
 
-// D3Q27: the FP32 path applies the generic product node by node (the paired form above is
-// written for the D3Q19 pair structure).
+// D3Q27 form of the paired product: the operations of the D3Q19 form above with the 13 pairs
+// (faces p = 0..2, edges 3..8, corners 9..12 with zero shear part), the D3Q27 weights, the
+// corners in P_ab and in the equilibrium chain, and (A^T v)_j = Pxx + Pyy + Pzz + sum_{a<b}
+// c_ja c_jb P_ab on the corners.
 template <class V>
 __device__ __forceinline__ void kbc_vjp_shifted(const V (&h)[Q], const V (&mu)[Q], float omega, float a, float b,
                                                 V (&lam)[Q])
 {
-    (void)a;
-    (void)b;
-    if constexpr (std::is_same<V, float>::value) {
-        kbc_vjp<float>(h, mu, omega, kHHGuard, lam);
-    } else {
-        float h1[Q], m1[Q], l1[Q];
+    using namespace lanes;
+    const V one = bc<V>(1.f);
+    const V W0 = bc<V>(8.0f / 27.0f), W1 = bc<V>(2.0f / 27.0f), W2 = bc<V>(1.0f / 54.0f), W3 = bc<V>(1.0f / 216.0f);
+    const auto frcp = [](float x) { return rcp_approx(x); };
+    // ---- forward, as the D3Q27 kbc_shifted
+    const V s1 = add(add(add(h[1], h[2]), add(h[3], h[4])), add(h[5], h[6]));
+    const V s2 = add(add(add(add(h[7], h[8]), add(h[9], h[10])), add(add(h[11], h[12]), add(h[13], h[14]))),
+                     add(add(h[15], h[16]), add(h[17], h[18])));
+    const V s3 = add(add(add(h[19], h[20]), add(h[21], h[22])), add(add(h[23], h[24]), add(h[25], h[26])));
+    const V drho = fma(W0, h[0], fma(W1, s1, fma(W2, s2, mul(W3, s3))));
+    const V rho = add(one, drho);
+    V d[13];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            h1[i] = h[i].x;
-            m1[i] = mu[i].x;
+    for (int p = 0; p < 13; ++p) d[p] = sub(h[2 * p + 1], h[2 * p + 2]);
+    const V jx = fma(W1, d[0], fma(W2, add(add(d[3], d[4]), add(d[5], d[6])),
+                                   mul(W3, add(add(d[9], d[10]), add(d[11], d[12])))));
+    const V jy = fma(W1, d[1], fma(W2, add(sub(d[3], d[4]), add(d[7], d[8])),
+                                   mul(W3, sub(add(d[9], d[10]), add(d[11], d[12])))));
+    const V jz = fma(W1, d[2], fma(W2, add(sub(d[5], d[6]), sub(d[7], d[8])),
+                                   mul(W3, add(sub(d[9], d[10]), sub(d[11], d[12])))));
+    const V rinv = map(rho, frcp);
+    const V jj15 = mul(bc<V>(-1.5f), fma(jx, jx, fma(jy, jy, mul(jz, jz))));
+    V heq[Q], n[Q];
+    heq[0] = fma(jj15, rinv, drho);
+    n[0] = sub(h[0], heq[0]);
+#pragma unroll
+    for (int p = 0; p < 13; ++p) {
+        const int i = 2 * p + 1;
+        const V cj = c_dot(i, jx, jy, jz);
+        const V q = fma(rinv, fma(bc<V>(4.5f), mul(cj, cj), jj15), drho);
+        heq[i] = fma(bc<V>(3.f), cj, q);
+        heq[i + 1] = fma(bc<V>(-3.f), cj, q);
+        n[i] = sub(h[i], heq[i]);
+        n[i + 1] = sub(h[i + 1], heq[i + 1]);
+    }
+    V Ap[13];
+#pragma unroll
+    for (int p = 0; p < 13; ++p) Ap[p] = add(n[2 * p + 1], n[2 * p + 2]);
+    const V exy = add(Ap[3], Ap[4]), exz = add(Ap[5], Ap[6]), eyz = add(Ap[7], Ap[8]);
+    const V csum = add(add(Ap[9], Ap[10]), add(Ap[11], Ap[12]));
+    const V cxy = sub(add(Ap[9], Ap[10]), add(Ap[11], Ap[12]));
+    const V cxz = add(sub(Ap[9], Ap[10]), sub(Ap[11], Ap[12]));
+    const V cyz = sub(sub(Ap[9], Ap[10]), sub(Ap[11], Ap[12]));
+    const V pxx = fma(W1, Ap[0], fma(W2, add(exy, exz), mul(W3, csum)));
+    const V pyy = fma(W1, Ap[1], fma(W2, add(exy, eyz), mul(W3, csum)));
+    const V pzz = fma(W1, Ap[2], fma(W2, add(exz, eyz), mul(W3, csum)));
+    const V tr3 = mul(add(add(pxx, pyy), pzz), bc<V>(1.0f / 3.0f));
+    V D[6];
+    D[0] = sub(pxx, tr3);
+    D[1] = sub(pyy, tr3);
+    D[2] = sub(pzz, tr3);
+    D[3] = fma(W2, sub(Ap[3], Ap[4]), mul(W3, cxy));
+    D[4] = fma(W2, sub(Ap[5], Ap[6]), mul(W3, cxz));
+    D[5] = fma(W2, sub(Ap[7], Ap[8]), mul(W3, cyz));
+    // k = Dh / w, ie = 1 / (1 + heq), kr = k ie
+    V k[Q], ie[Q], kr[Q];
+    k[0] = n[0];
+    ie[0] = map(add(one, heq[0]), frcp);
+    kr[0] = mul(k[0], ie[0]);
+    V A[9];
+    V hf = bc<V>(0.f), he = bc<V>(0.f), hc = bc<V>(0.f), mf = bc<V>(0.f), me = bc<V>(0.f), mc = bc<V>(0.f);
+#pragma unroll
+    for (int p = 0; p < 13; ++p) {
+        const int i = 2 * p + 1;
+        if (p < 9) {
+            const V Dp = D[p < 3 ? p : 3 + (p - 3) / 2];
+            const float ms = p < 3 ? -6.75f : ((p - 3) % 2 == 1 ? 13.5f : -13.5f);  // -s / D
+            k[i] = fma(Dp, bc<V>(ms), n[i]);
+            k[i + 1] = fma(Dp, bc<V>(ms), n[i + 1]);
+        } else {
+            k[i] = n[i];
+            k[i + 1] = n[i + 1];
         }
-        kbc_vjp<float>(h1, m1, omega, kHHGuard, l1);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            lam[i].x = l1[i];
-            h1[i] = h[i].y;
-            m1[i] = mu[i].y;
+        ie[i] = map(add(one, heq[i]), frcp);
+        ie[i + 1] = map(add(one, heq[i + 1]), frcp);
+        kr[i] = mul(k[i], ie[i]);
+        kr[i + 1] = mul(k[i + 1], ie[i + 1]);
+        if (p < 9) A[p] = add(kr[i], kr[i + 1]);
+        const V hp = fma(kr[i + 1], k[i + 1], mul(kr[i], k[i]));
+        const V mp = fma(mu[i + 1], k[i + 1], mul(mu[i], k[i]));
+        if (p < 3) {
+            hf = p == 0 ? hp : add(hf, hp);
+            mf = p == 0 ? mp : add(mf, mp);
+        } else if (p < 9) {
+            he = p == 3 ? hp : add(he, hp);
+            me = p == 3 ? mp : add(me, mp);
+        } else {
+            hc = p == 9 ? hp : add(hc, hp);
+            mc = p == 9 ? mp : add(mc, mp);
         }
-        kbc_vjp<float>(h1, m1, omega, kHHGuard, l1);
+    }
+    // sh: w1 6.75 = 1/2, w2 13.5 = 1/4
+    const V sf = fma(D[0], A[0], fma(D[1], A[1], mul(D[2], A[2])));
+    const V se = fma(D[3], sub(A[3], A[4]), fma(D[4], sub(A[5], A[6]), mul(D[5], sub(A[7], A[8]))));
+    const V sh = fma(bc<V>(0.5f), sf, mul(bc<V>(0.25f), se));
+    const V hh = fma(W0, mul(kr[0], k[0]), fma(W1, hf, fma(W2, he, mul(W3, hc))));
+    const V mk = fma(W0, mul(mu[0], k[0]), fma(W1, mf, fma(W2, me, mul(W3, mc))));  // mu . Dh
+    const V ihh = map(hh, [](float x) { return x > kHHGuard ? rcp_approx(x) : 0.f; });
+    const V R2 = mul(sh, ihh);
+    const V R1 = mul(mk, ihh);
+    const V gamma = map(hh, R2, [a, b](float x, float r2) { return x > kHHGuard ? fma(-b, r2, a) : 2.0f; });
+    const V nbeta = mul(bc<V>(-0.5f * omega), gamma);
+    const V c1 = mul(bc<V>(0.5f * omega * b), R1);
+    const V c2 = mul(c1, mul(bc<V>(-1.f), R2));
+    const V tc2 = mul(bc<V>(2.f), c2);
+    const V nom = bc<V>(-omega);
+    // ---- coefficient vectors (corners: s = 0, like the rest velocity)
+    V gh[Q], ng[Q], dd[19];
+    gh[0] = fma(nbeta, mu[0], mul(mul(tc2, k[0]), ie[0]));
+    ng[0] = mul(mul(kr[0], ie[0]), mul(c2, k[0]));
 #pragma unroll
-        for (int i = 0; i < Q; ++i) lam[i].y = l1[i];
+    for (int p = 0; p < 13; ++p) {
+        const int i = 2 * p + 1;
+        if (p < 9) {
+            const float sd = p < 3 ? 6.75f : ((p - 3) % 2 == 1 ? -13.5f : 13.5f);  // s / D
+            const V c1s = mul(c1, mul(bc<V>(sd), D[p < 3 ? p : 3 + (p - 3) / 2]));
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {
+                const int j = i + o;
+                const V gs = fma(c1, kr[j], mul(nom, mu[j]));
+                gh[j] = fma(nbeta, mu[j], mul(fma(tc2, k[j], c1s), ie[j]));
+                ng[j] = mul(mul(kr[j], ie[j]), fma(c2, k[j], c1s));
+                dd[j] = sub(gs, gh[j]);
+            }
+        } else {
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {
+                const int j = i + o;
+                gh[j] = fma(nbeta, mu[j], mul(mul(tc2, k[j]), ie[j]));
+                ng[j] = mul(mul(kr[j], ie[j]), mul(c2, k[j]));
+            }
+        }
+    }
+    // ---- r = A^T dd + gh (faces and edges define the adjoint second moments)
+    const V F = add(add(add(dd[1], dd[2]), add(dd[3], dd[4])), add(dd[5], dd[6]));
+    const V nf6 = mul(bc<V>(-1.0f / 6.0f), F);
+    const V Pxx = fma(bc<V>(0.5f), add(dd[1], dd[2]), nf6);
+    const V Pyy = fma(bc<V>(0.5f), add(dd[3], dd[4]), nf6);
+    const V Pzz = fma(bc<V>(0.5f), add(dd[5], dd[6]), nf6);
+    const V Pxy = mul(bc<V>(0.25f), sub(add(dd[7], dd[8]), add(dd[9], dd[10])));
+    const V Pxz = mul(bc<V>(0.25f), sub(add(dd[11], dd[12]), add(dd[13], dd[14])));
+    const V Pyz = mul(bc<V>(0.25f), sub(add(dd[15], dd[16]), add(dd[17], dd[18])));
+    const V Pd3 = add(add(Pxx, Pyy), Pzz);
+    V r[Q];
+    r[0] = gh[0];
+#pragma unroll
+    for (int p = 0; p < 13; ++p) {
+        const int i = 2 * p + 1;
+        V at;
+        if (p == 0) at = Pxx;
+        else if (p == 1) at = Pyy;
+        else if (p == 2) at = Pzz;
+        else if (p < 5) at = p == 3 ? add(add(Pxx, Pyy), Pxy) : sub(add(Pxx, Pyy), Pxy);
+        else if (p < 7) at = p == 5 ? add(add(Pxx, Pzz), Pxz) : sub(add(Pxx, Pzz), Pxz);
+        else if (p < 9) at = p == 7 ? add(add(Pyy, Pzz), Pyz) : sub(add(Pyy, Pzz), Pyz);
+        else {
+            const int sxy = cx(i) * cy(i), sxz = cx(i) * cz(i), syz = cy(i) * cz(i);
+            at = sxy > 0 ? add(Pd3, Pxy) : sub(Pd3, Pxy);
+            at = sxz > 0 ? add(at, Pxz) : sub(at, Pxz);
+            at = syz > 0 ? add(at, Pyz) : sub(at, Pyz);
+        }
+        r[i] = add(at, gh[i]);
+        r[i + 1] = add(at, gh[i + 1]);
+    }
+    // ---- equilibrium chain
+    const V nq0 = add(ng[0], r[0]);
+    const V rinv3 = mul(bc<V>(3.f), rinv);
+    const V qf = mul(nq0, add(one, heq[0]));
+    V ef = bc<V>(0.f), ee = bc<V>(0.f), ec = bc<V>(0.f), sgf = bc<V>(0.f), sge = bc<V>(0.f), sgc = bc<V>(0.f);
+    V vf[3], vx = bc<V>(0.f), vy = bc<V>(0.f), vz = bc<V>(0.f), ux3 = bc<V>(0.f), uy3 = bc<V>(0.f), uz3 = bc<V>(0.f);
+#pragma unroll
+    for (int p = 0; p < 13; ++p) {
+        const int i = 2 * p + 1;
+        const V nqa = add(ng[i], r[i]), nqb = add(ng[i + 1], r[i + 1]);
+        const V ep = fma(nqb, add(one, heq[i + 1]), mul(nqa, add(one, heq[i])));
+        const V sg = add(nqa, nqb);
+        const V v = fma(sg, mul(c_dot(i, jx, jy, jz), rinv3), sub(nqa, nqb));
+        if (p < 3) {
+            ef = p == 0 ? ep : add(ef, ep);
+            sgf = p == 0 ? sg : add(sgf, sg);
+            vf[p] = v;
+        } else if (p < 9) {
+            ee = p == 3 ? ep : add(ee, ep);
+            sge = p == 3 ? sg : add(sge, sg);
+            if (cx(i) > 0) vx = add(vx, v);
+            if (cy(i) > 0) vy = add(vy, v);
+            else if (cy(i) < 0) vy = sub(vy, v);
+            if (cz(i) > 0) vz = add(vz, v);
+            else if (cz(i) < 0) vz = sub(vz, v);
+        } else {
+            ec = p == 9 ? ep : add(ec, ep);
+            sgc = p == 9 ? sg : add(sgc, sg);
+            ux3 = add(ux3, v);  // every corner has c_x = +1 on its odd member
+            uy3 = cy(i) > 0 ? add(uy3, v) : sub(uy3, v);
+            uz3 = cz(i) > 0 ? add(uz3, v) : sub(uz3, v);
+        }
+    }
+    const V NQr = fma(W0, qf, fma(W1, ef, fma(W2, ee, mul(W3, ec))));
+    const V Swnq = fma(W0, nq0, fma(W1, sgf, fma(W2, sge, mul(W3, sgc))));
+    const V nrinv = mul(bc<V>(-1.f), rinv);
+    const V NVx = mul(bc<V>(3.f), fma(mul(jx, nrinv), Swnq, fma(W1, vf[0], fma(W2, vx, mul(W3, ux3)))));
+    const V NVy = mul(bc<V>(3.f), fma(mul(jy, nrinv), Swnq, fma(W1, vf[1], fma(W2, vy, mul(W3, uy3)))));
+    const V NVz = mul(bc<V>(3.f), fma(mul(jz, nrinv), Swnq, fma(W1, vf[2], fma(W2, vz, mul(W3, uz3)))));
+    const V base = fma(rinv, fma(NVx, jx, fma(NVy, jy, mul(NVz, jz))), mul(NQr, nrinv));
+    lam[0] = add(add(mu[0], r[0]), base);
+#pragma unroll
+    for (int p = 0; p < 13; ++p) {
+        const int i = 2 * p + 1;
+        const V cN = c_dot(i, NVx, NVy, NVz);
+        lam[i] = add(add(mu[i], r[i]), sub(base, cN));
+        lam[i + 1] = add(add(mu[i + 1], r[i + 1]), add(base, cN));
     }
 }
 
