@@ -374,7 +374,10 @@ __device__ __forceinline__ void kbc_vjp_shifted(const V (&h)[Q], const V (&mu)[Q
 // D3Q27 form of the paired product: the operations of the D3Q19 form above with the 13 pairs
 // (faces p = 0..2, edges 3..8, corners 9..12 with zero shear part), the D3Q27 weights, the
 // corners in P_ab and in the equilibrium chain, and (A^T v)_j = Pxx + Pyy + Pzz + sum_{a<b}
-// c_ja c_jb P_ab on the corners.
+// c_ja c_jb P_ab on the corners.  To keep 27 pairs of values from exhausting the registers the
+// coefficients are written through kr_j = k_j / (1 + heq_j) (k dies after the forward sums):
+// gh_j = -beta mu_j + 2 c2 kr_j + c1s_j ie_j, ng_j = kr_j (c2 kr_j + c1s_j ie_j), and each
+// velocity keeps only u_j = mu_j + gh_j (for lambda) and v_j = ng_j + gh_j (for the chain).
 template <class V>
 __device__ __forceinline__ void kbc_vjp_shifted(const V (&h)[Q], const V (&mu)[Q], float omega, float a, float b,
                                                 V (&lam)[Q])
@@ -401,18 +404,22 @@ __device__ __forceinline__ void kbc_vjp_shifted(const V (&h)[Q], const V (&mu)[Q
                                    mul(W3, add(sub(d[9], d[10]), sub(d[11], d[12])))));
     const V rinv = map(rho, frcp);
     const V jj15 = mul(bc<V>(-1.5f), fma(jx, jx, fma(jy, jy, mul(jz, jz))));
-    V heq[Q], n[Q];
-    heq[0] = fma(jj15, rinv, drho);
-    n[0] = sub(h[0], heq[0]);
+    V eh[Q], n[Q];  // eh = 1 + heq
+    {
+        const V heq0 = fma(jj15, rinv, drho);
+        eh[0] = add(one, heq0);
+        n[0] = sub(h[0], heq0);
+    }
 #pragma unroll
     for (int p = 0; p < 13; ++p) {
         const int i = 2 * p + 1;
         const V cj = c_dot(i, jx, jy, jz);
         const V q = fma(rinv, fma(bc<V>(4.5f), mul(cj, cj), jj15), drho);
-        heq[i] = fma(bc<V>(3.f), cj, q);
-        heq[i + 1] = fma(bc<V>(-3.f), cj, q);
-        n[i] = sub(h[i], heq[i]);
-        n[i + 1] = sub(h[i + 1], heq[i + 1]);
+        const V ha = fma(bc<V>(3.f), cj, q), hb = fma(bc<V>(-3.f), cj, q);
+        eh[i] = add(one, ha);
+        eh[i + 1] = add(one, hb);
+        n[i] = sub(h[i], ha);
+        n[i + 1] = sub(h[i + 1], hb);
     }
     V Ap[13];
 #pragma unroll
@@ -433,32 +440,29 @@ __device__ __forceinline__ void kbc_vjp_shifted(const V (&h)[Q], const V (&mu)[Q
     D[3] = fma(W2, sub(Ap[3], Ap[4]), mul(W3, cxy));
     D[4] = fma(W2, sub(Ap[5], Ap[6]), mul(W3, cxz));
     D[5] = fma(W2, sub(Ap[7], Ap[8]), mul(W3, cyz));
-    // k = Dh / w, ie = 1 / (1 + heq), kr = k ie
-    V k[Q], ie[Q], kr[Q];
-    k[0] = n[0];
-    ie[0] = map(add(one, heq[0]), frcp);
-    kr[0] = mul(k[0], ie[0]);
+    // k = Dh / w (in n), ie = 1 / (1 + heq), kr = k ie
+    V ie[Q], kr[Q];
+    ie[0] = map(eh[0], frcp);
+    kr[0] = mul(n[0], ie[0]);
     V A[9];
     V hf = bc<V>(0.f), he = bc<V>(0.f), hc = bc<V>(0.f), mf = bc<V>(0.f), me = bc<V>(0.f), mc = bc<V>(0.f);
+    const V hh0 = mul(kr[0], n[0]), mk0 = mul(mu[0], n[0]);
 #pragma unroll
     for (int p = 0; p < 13; ++p) {
         const int i = 2 * p + 1;
         if (p < 9) {
             const V Dp = D[p < 3 ? p : 3 + (p - 3) / 2];
             const float ms = p < 3 ? -6.75f : ((p - 3) % 2 == 1 ? 13.5f : -13.5f);  // -s / D
-            k[i] = fma(Dp, bc<V>(ms), n[i]);
-            k[i + 1] = fma(Dp, bc<V>(ms), n[i + 1]);
-        } else {
-            k[i] = n[i];
-            k[i + 1] = n[i + 1];
+            n[i] = fma(Dp, bc<V>(ms), n[i]);
+            n[i + 1] = fma(Dp, bc<V>(ms), n[i + 1]);
         }
-        ie[i] = map(add(one, heq[i]), frcp);
-        ie[i + 1] = map(add(one, heq[i + 1]), frcp);
-        kr[i] = mul(k[i], ie[i]);
-        kr[i + 1] = mul(k[i + 1], ie[i + 1]);
+        ie[i] = map(eh[i], frcp);
+        ie[i + 1] = map(eh[i + 1], frcp);
+        kr[i] = mul(n[i], ie[i]);
+        kr[i + 1] = mul(n[i + 1], ie[i + 1]);
         if (p < 9) A[p] = add(kr[i], kr[i + 1]);
-        const V hp = fma(kr[i + 1], k[i + 1], mul(kr[i], k[i]));
-        const V mp = fma(mu[i + 1], k[i + 1], mul(mu[i], k[i]));
+        const V hp = fma(kr[i + 1], n[i + 1], mul(kr[i], n[i]));
+        const V mp = fma(mu[i + 1], n[i + 1], mul(mu[i], n[i]));
         if (p < 3) {
             hf = p == 0 ? hp : add(hf, hp);
             mf = p == 0 ? mp : add(mf, mp);
@@ -474,8 +478,8 @@ __device__ __forceinline__ void kbc_vjp_shifted(const V (&h)[Q], const V (&mu)[Q
     const V sf = fma(D[0], A[0], fma(D[1], A[1], mul(D[2], A[2])));
     const V se = fma(D[3], sub(A[3], A[4]), fma(D[4], sub(A[5], A[6]), mul(D[5], sub(A[7], A[8]))));
     const V sh = fma(bc<V>(0.5f), sf, mul(bc<V>(0.25f), se));
-    const V hh = fma(W0, mul(kr[0], k[0]), fma(W1, hf, fma(W2, he, mul(W3, hc))));
-    const V mk = fma(W0, mul(mu[0], k[0]), fma(W1, mf, fma(W2, me, mul(W3, mc))));  // mu . Dh
+    const V hh = fma(W0, hh0, fma(W1, hf, fma(W2, he, mul(W3, hc))));
+    const V mk = fma(W0, mk0, fma(W1, mf, fma(W2, me, mul(W3, mc))));  // mu . Dh
     const V ihh = map(hh, [](float x) { return x > kHHGuard ? rcp_approx(x) : 0.f; });
     const V R2 = mul(sh, ihh);
     const V R1 = mul(mk, ihh);
@@ -484,11 +488,15 @@ __device__ __forceinline__ void kbc_vjp_shifted(const V (&h)[Q], const V (&mu)[Q
     const V c1 = mul(bc<V>(0.5f * omega * b), R1);
     const V c2 = mul(c1, mul(bc<V>(-1.f), R2));
     const V tc2 = mul(bc<V>(2.f), c2);
-    const V nom = bc<V>(-omega);
-    // ---- coefficient vectors (corners: s = 0, like the rest velocity)
-    V gh[Q], ng[Q], dd[19];
-    gh[0] = fma(nbeta, mu[0], mul(mul(tc2, k[0]), ie[0]));
-    ng[0] = mul(mul(kr[0], ie[0]), mul(c2, k[0]));
+    const V gsd = sub(bc<V>(-omega), nbeta);  // gs - gh = (-omega + beta) mu + (c1 - 2 c2) kr - c1s ie
+    const V ktd = sub(c1, tc2);
+    // ---- per velocity: dd (faces and edges), u = mu + gh, v = ng + gh (corners: s = 0)
+    V u[Q], v[Q], dd[19];
+    {
+        const V g0 = fma(nbeta, mu[0], mul(tc2, kr[0]));
+        u[0] = add(mu[0], g0);
+        v[0] = fma(kr[0], mul(c2, kr[0]), g0);
+    }
 #pragma unroll
     for (int p = 0; p < 13; ++p) {
         const int i = 2 * p + 1;
@@ -498,21 +506,23 @@ __device__ __forceinline__ void kbc_vjp_shifted(const V (&h)[Q], const V (&mu)[Q
 #pragma unroll
             for (int o = 0; o < 2; ++o) {
                 const int j = i + o;
-                const V gs = fma(c1, kr[j], mul(nom, mu[j]));
-                gh[j] = fma(nbeta, mu[j], mul(fma(tc2, k[j], c1s), ie[j]));
-                ng[j] = mul(mul(kr[j], ie[j]), fma(c2, k[j], c1s));
-                dd[j] = sub(gs, gh[j]);
+                const V si = mul(c1s, ie[j]);
+                const V g = fma(nbeta, mu[j], fma(tc2, kr[j], si));
+                dd[j] = fma(gsd, mu[j], fma(ktd, kr[j], mul(bc<V>(-1.f), si)));
+                u[j] = add(mu[j], g);
+                v[j] = fma(kr[j], fma(c2, kr[j], si), g);
             }
         } else {
 #pragma unroll
             for (int o = 0; o < 2; ++o) {
                 const int j = i + o;
-                gh[j] = fma(nbeta, mu[j], mul(mul(tc2, k[j]), ie[j]));
-                ng[j] = mul(mul(kr[j], ie[j]), mul(c2, k[j]));
+                const V g = fma(nbeta, mu[j], mul(tc2, kr[j]));
+                u[j] = add(mu[j], g);
+                v[j] = fma(kr[j], mul(c2, kr[j]), g);
             }
         }
     }
-    // ---- r = A^T dd + gh (faces and edges define the adjoint second moments)
+    // ---- adjoint second moments from dd (faces and edges)
     const V F = add(add(add(dd[1], dd[2]), add(dd[3], dd[4])), add(dd[5], dd[6]));
     const V nf6 = mul(bc<V>(-1.0f / 6.0f), F);
     const V Pxx = fma(bc<V>(0.5f), add(dd[1], dd[2]), nf6);
@@ -522,58 +532,50 @@ __device__ __forceinline__ void kbc_vjp_shifted(const V (&h)[Q], const V (&mu)[Q
     const V Pxz = mul(bc<V>(0.25f), sub(add(dd[11], dd[12]), add(dd[13], dd[14])));
     const V Pyz = mul(bc<V>(0.25f), sub(add(dd[15], dd[16]), add(dd[17], dd[18])));
     const V Pd3 = add(add(Pxx, Pyy), Pzz);
-    V r[Q];
-    r[0] = gh[0];
-#pragma unroll
-    for (int p = 0; p < 13; ++p) {
+    const auto at_of = [&](int p) -> V {
         const int i = 2 * p + 1;
-        V at;
-        if (p == 0) at = Pxx;
-        else if (p == 1) at = Pyy;
-        else if (p == 2) at = Pzz;
-        else if (p < 5) at = p == 3 ? add(add(Pxx, Pyy), Pxy) : sub(add(Pxx, Pyy), Pxy);
-        else if (p < 7) at = p == 5 ? add(add(Pxx, Pzz), Pxz) : sub(add(Pxx, Pzz), Pxz);
-        else if (p < 9) at = p == 7 ? add(add(Pyy, Pzz), Pyz) : sub(add(Pyy, Pzz), Pyz);
-        else {
-            const int sxy = cx(i) * cy(i), sxz = cx(i) * cz(i), syz = cy(i) * cz(i);
-            at = sxy > 0 ? add(Pd3, Pxy) : sub(Pd3, Pxy);
-            at = sxz > 0 ? add(at, Pxz) : sub(at, Pxz);
-            at = syz > 0 ? add(at, Pyz) : sub(at, Pyz);
-        }
-        r[i] = add(at, gh[i]);
-        r[i + 1] = add(at, gh[i + 1]);
-    }
-    // ---- equilibrium chain
-    const V nq0 = add(ng[0], r[0]);
+        if (p == 0) return Pxx;
+        if (p == 1) return Pyy;
+        if (p == 2) return Pzz;
+        if (p < 5) return p == 3 ? add(add(Pxx, Pyy), Pxy) : sub(add(Pxx, Pyy), Pxy);
+        if (p < 7) return p == 5 ? add(add(Pxx, Pzz), Pxz) : sub(add(Pxx, Pzz), Pxz);
+        if (p < 9) return p == 7 ? add(add(Pyy, Pzz), Pyz) : sub(add(Pyy, Pzz), Pyz);
+        V at = cx(i) * cy(i) > 0 ? add(Pd3, Pxy) : sub(Pd3, Pxy);
+        at = cx(i) * cz(i) > 0 ? add(at, Pxz) : sub(at, Pxz);
+        return cy(i) * cz(i) > 0 ? add(at, Pyz) : sub(at, Pyz);
+    };
+    // ---- equilibrium chain on nq = ng + r = v + A^T dd
+    const V nq0 = v[0];
     const V rinv3 = mul(bc<V>(3.f), rinv);
-    const V qf = mul(nq0, add(one, heq[0]));
+    const V qf = mul(nq0, eh[0]);
     V ef = bc<V>(0.f), ee = bc<V>(0.f), ec = bc<V>(0.f), sgf = bc<V>(0.f), sge = bc<V>(0.f), sgc = bc<V>(0.f);
     V vf[3], vx = bc<V>(0.f), vy = bc<V>(0.f), vz = bc<V>(0.f), ux3 = bc<V>(0.f), uy3 = bc<V>(0.f), uz3 = bc<V>(0.f);
 #pragma unroll
     for (int p = 0; p < 13; ++p) {
         const int i = 2 * p + 1;
-        const V nqa = add(ng[i], r[i]), nqb = add(ng[i + 1], r[i + 1]);
-        const V ep = fma(nqb, add(one, heq[i + 1]), mul(nqa, add(one, heq[i])));
+        const V at = at_of(p);
+        const V nqa = add(v[i], at), nqb = add(v[i + 1], at);
+        const V ep = fma(nqb, eh[i + 1], mul(nqa, eh[i]));
         const V sg = add(nqa, nqb);
-        const V v = fma(sg, mul(c_dot(i, jx, jy, jz), rinv3), sub(nqa, nqb));
+        const V w = fma(sg, mul(c_dot(i, jx, jy, jz), rinv3), sub(nqa, nqb));
         if (p < 3) {
             ef = p == 0 ? ep : add(ef, ep);
             sgf = p == 0 ? sg : add(sgf, sg);
-            vf[p] = v;
+            vf[p] = w;
         } else if (p < 9) {
             ee = p == 3 ? ep : add(ee, ep);
             sge = p == 3 ? sg : add(sge, sg);
-            if (cx(i) > 0) vx = add(vx, v);
-            if (cy(i) > 0) vy = add(vy, v);
-            else if (cy(i) < 0) vy = sub(vy, v);
-            if (cz(i) > 0) vz = add(vz, v);
-            else if (cz(i) < 0) vz = sub(vz, v);
+            if (cx(i) > 0) vx = add(vx, w);
+            if (cy(i) > 0) vy = add(vy, w);
+            else if (cy(i) < 0) vy = sub(vy, w);
+            if (cz(i) > 0) vz = add(vz, w);
+            else if (cz(i) < 0) vz = sub(vz, w);
         } else {
             ec = p == 9 ? ep : add(ec, ep);
             sgc = p == 9 ? sg : add(sgc, sg);
-            ux3 = add(ux3, v);  // every corner has c_x = +1 on its odd member
-            uy3 = cy(i) > 0 ? add(uy3, v) : sub(uy3, v);
-            uz3 = cz(i) > 0 ? add(uz3, v) : sub(uz3, v);
+            ux3 = add(ux3, w);  // every corner has c_x = +1 on its odd member
+            uy3 = cy(i) > 0 ? add(uy3, w) : sub(uy3, w);
+            uz3 = cz(i) > 0 ? add(uz3, w) : sub(uz3, w);
         }
     }
     const V NQr = fma(W0, qf, fma(W1, ef, fma(W2, ee, mul(W3, ec))));
@@ -583,13 +585,15 @@ __device__ __forceinline__ void kbc_vjp_shifted(const V (&h)[Q], const V (&mu)[Q
     const V NVy = mul(bc<V>(3.f), fma(mul(jy, nrinv), Swnq, fma(W1, vf[1], fma(W2, vy, mul(W3, uy3)))));
     const V NVz = mul(bc<V>(3.f), fma(mul(jz, nrinv), Swnq, fma(W1, vf[2], fma(W2, vz, mul(W3, uz3)))));
     const V base = fma(rinv, fma(NVx, jx, fma(NVy, jy, mul(NVz, jz))), mul(NQr, nrinv));
-    lam[0] = add(add(mu[0], r[0]), base);
+    // lambda = mu + r + base - c . NV with mu + r = u + A^T dd
+    lam[0] = add(u[0], base);
 #pragma unroll
     for (int p = 0; p < 13; ++p) {
         const int i = 2 * p + 1;
+        const V at = at_of(p);
         const V cN = c_dot(i, NVx, NVy, NVz);
-        lam[i] = add(add(mu[i], r[i]), sub(base, cN));
-        lam[i + 1] = add(add(mu[i + 1], r[i + 1]), add(base, cN));
+        lam[i] = add(add(u[i], at), sub(base, cN));
+        lam[i + 1] = add(add(u[i + 1], at), add(base, cN));
     }
 }
 
