@@ -180,6 +180,102 @@ def run_reference(args, wl):
     }))
 
 
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_report_child(stats_too):
+    """The FP64 oracle as it stands, with the OpenMP thread count of this process: cfg1 (32^3 x 1
+    deterministic TGV, Re 100, U_lat 0.05, TGV pressure density) timed whole over 200 steps; cfg2
+    (64^3 RTGV, Re 800, Ma 0.025) as a per-update rate over the first 10 steps of a few samples;
+    with `stats_too`, one snapshot's statistics per sample."""
+    import oracle
+    from oracle import stats
+    import ensemble_inputs as gen
+    out = {"threads": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))}
+    un = oracle.units(32, 100.0, 0.05 * np.sqrt(3.0))
+    f = oracle.init_ensemble(32, None, un["ulat"], density_mode=1, M=1)
+    t0 = time.perf_counter()
+    oracle.run(f, un["omega"], 200)
+    dt = time.perf_counter() - t0
+    out["cfg1"] = {"mlups": 32**3 * 200 / dt / 1e6, "seconds": dt, "run": "32^3 x 1, 200 steps, whole"}
+    ms = 4 if out["threads"] > 1 else 1
+    un = oracle.units(64, 800.0, 0.025)
+    f = oracle.init_ensemble(64, gen.draw_params(1, ms), un["ulat"])
+    t0 = time.perf_counter()
+    oracle.run(f, un["omega"], 10)
+    dt = time.perf_counter() - t0
+    out["cfg2"] = {"mlups": ms * 64**3 * 10 / dt / 1e6, "seconds": dt,
+                   "run": f"{ms} of 64 samples x the first 10 steps of 64^3 (per-update rate)"}
+    if stats_too:
+        _, u = oracle.moments(f)
+        up = stats.to_physical(u, un["ulat"])
+        g = oracle.init_ensemble(64, gen.draw_params(2, ms), un["ulat"])
+        _, ub = oracle.moments(g)
+        ub = stats.to_physical(ub, un["ulat"])
+        times = {}
+        for name, fn in (("kinetic_energy", lambda: stats.kinetic_energy(up)),
+                         ("enstrophy", lambda: stats.enstrophy(up)),
+                         ("mean_var", lambda: stats.mean_var(up)),
+                         ("energy_spectrum", lambda: stats.energy_spectrum(up)),
+                         ("structure_function_trace", lambda: stats.structure_function_trace(up)),
+                         ("structure_function_axes_p2_6", lambda: stats.structure_function_axes(up, 6)),
+                         ("w1_one_point_8cube", lambda: stats.w1_one_point(stats.restrict(up), stats.restrict(ub)))):
+            t0 = time.perf_counter()
+            fn()
+            times[name] = (time.perf_counter() - t0) / ms * 1e3
+        out["stats_ms_per_sample_64cube"] = times
+    return out
+
+
+def run_oracle_report(args):
+    """The oracle's timings of the CPU baseline plan on the host (all cores, then one core, each in
+    a child process so that OpenMP starts with that thread count), the CPU model, and the GPU's
+    cfg1 run (32^3 x 1 x 200 steps: L2-resident, not an HBM figure) beside them."""
+    if args.oracle_child:
+        print(json.dumps(oracle_report_child(args.oracle_child == "all")))
+        return
+    nproc = os.cpu_count() or 1
+    rep = {"metric": "oracle_report", "cpu_model": _cpu_model(), "nproc": nproc, "oracle": {}}
+    for tag, threads in (("all_cores", nproc), ("one_core", 1)):
+        env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+        res = subprocess.run([sys.executable, os.path.abspath(__file__), "--workload", "oracle_report",
+                              "--oracle-child", "all" if tag == "all_cores" else "one"],
+                             env=env, capture_output=True, text=True, check=True)
+        rep["oracle"][tag] = json.loads(res.stdout.strip().splitlines()[-1])
+    import torch
+    if torch.cuda.is_available():
+        from paper_2608_23786_gb300 import Ensemble, mclbm
+        mclbm.load()
+        dev = torch.device("cuda", 0)
+        stream = torch.cuda.Stream(dev)
+        torch.cuda.set_stream(stream)
+        gpu = {}
+        for prec in ("fp64", "fp32", "fp16"):
+            ens = Ensemble(32, 1, Re=100.0, Ma=0.05 * np.sqrt(3.0), precision=prec, init_density=1, device=dev,
+                           stream=stream).init_tgv()
+            ens.step(200)
+            torch.cuda.synchronize()
+            ens.init_tgv()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ens.step(200)
+            b.record(stream)
+            torch.cuda.synchronize()
+            sec = a.elapsed_time(b) / 1e3
+            gpu[prec] = {"mlups": 32**3 * 200 / sec / 1e6, "ms": sec * 1e3, "memory": "L2-resident"}
+        rep["gpu_cfg1"] = gpu
+    print(json.dumps(rep))
+
+
 def run_levels(args, precision):
     """Uneven batch of the diffusive-scaling viscosity sequence in one graph-captured launch per
     sub-step: 64^3 x 64, 128^3 x 32, 256^3 x 8 at Re 400 / 1600 / 3200, Ma 0.025 / 0.0125 / 0.00625,
@@ -368,10 +464,12 @@ def main():
     ap.add_argument("--launch", default=None, help="kind,vec,block instead of the library default (e.g. 0,2,128)")
     ap.add_argument("--autotune", action="store_true", help="let the library's autotuner pick the launch shape")
     ap.add_argument("--workload", default="ensemble64",
-                    choices=["ensemble64", "levels_fp32", "levels_fp16", "large", "adjoint"],
+                    choices=["ensemble64", "levels_fp32", "levels_fp16", "large", "adjoint", "oracle_report"],
                     help="ensemble64 (default): 64^3 x 64 FP32; levels_*: 3-level batch; large: 512^3 x 4 FP16 AA; "
-                         "adjoint: gradient of E(T), 64^3 x 16, 500 steps")
+                         "adjoint: gradient of E(T), 64^3 x 16, 500 steps; oracle_report: the oracle on cfg1/cfg2 "
+                         "(all cores and one core), its statistics per snapshot, and the GPU on cfg1")
     ap.add_argument("--T", type=int, default=500, help="adjoint horizon (steps) of --workload adjoint")
+    ap.add_argument("--oracle-child", default=None, choices=["all", "one"], help=argparse.SUPPRESS)
     ap.add_argument("--lattice", type=int, default=19, choices=[19, 27],
                     help="velocity set of the ensemble64 workload: 19 (D3Q19, the paper's) or 27 (D3Q27)")
     args = ap.parse_args()
@@ -381,6 +479,8 @@ def main():
         return run_large(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
+    if args.workload == "oracle_report":
+        return run_oracle_report(args)
     wl = dict(WORKLOAD)
     if args.N or args.M:
         wl["N"] = args.N or wl["N"]
