@@ -180,6 +180,15 @@ def run_reference(args, wl):
     }))
 
 
+def launch_desc(even, odd=None):
+    """The launch shape(s) of a bench line: (kind, vec, block) of pull or AA even steps, and of
+    AA odd steps where they differ."""
+    d = {"kind": KINDS[even[0]], "vec": even[1], "block": even[2]}
+    if odd is not None and tuple(odd[:3]) != tuple(even[:3]):
+        d["odd_steps"] = {"kind": KINDS[odd[0]], "vec": odd[1], "block": odd[2]}
+    return d
+
+
 def _cpu_model():
     try:
         out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
@@ -331,7 +340,8 @@ def run_levels(args, precision):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if precision == "fp32" else "f16-storage/f32",
         "data": "synthetic",
         "config": {"workload": f"levels_64x64_128x32_256x8_{precision}_{pattern}", "substeps": subs,
-                   "launch": {"kind": KINDS[tuned[0]], "vec": tuned[1], "block": tuned[2]}, "graph": True,
+                   "launch": launch_desc(tuned, mclbm.mclbm_batch_get_launch_parity(b, 1) if pattern == "aa" else None),
+                   "graph": True,
                    "l2": "inputs larger than L2"},
         "roofline": {"kernel": KERNEL_NAMES[tuned[0]], "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "peak_kind": peak_kind, "traffic": None},
@@ -386,7 +396,7 @@ def run_large(args):
         "warmup": max(3, args.warmup), "ms_per_step": sec / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f16-storage/f32", "data": "synthetic",
         "config": {"workload": "rtgv_512cube_x4_fp16_aa", "updates_per_step": S, "footprint_gb": 38 * 512**3 * 4 / 1e9,
-                   "launch": {"kind": KINDS[tuned[0]], "vec": tuned[1], "block": tuned[2]},
+                   "launch": launch_desc(tuned, mclbm.mclbm_get_launch_parity(ens.ctx, 1)),
                    "l2": "inputs larger than L2"},
         "roofline": {"kernel": KERNEL_NAMES[tuned[0]], "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "peak_kind": peak_kind, "traffic": None},
@@ -675,8 +685,9 @@ def main():
                    "updates_per_step": S,
                    "reductions_per_step": ["E_m(t)", "mean/var fields"], "l2": f"inputs ({bpl / 1e9:.2f} GB moved per update) "
                          "larger than the 129 MB L2: no flush",
-                   "launch": {"kind": KINDS[tuned[0]], "vec": tuned[1], "block": tuned[2],
-                              "chosen_by": "explicit" if args.launch else ("autotuner" if args.autotune else "default")}},
+                   "launch": dict(launch_desc(tuned, mclbm.mclbm_get_launch_parity(ens.ctx, 1)
+                                              if wl["pattern"] == "aa" else None),
+                                  chosen_by="explicit" if args.launch else ("autotuner" if args.autotune else "default"))},
         "roofline": {"kernel": KERNEL_NAMES[tuned[0]] +
                      f"<{wl['precision']},{wl['pattern']},vec={tuned[1]},block={tuned[2]}>",
                      "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",

@@ -282,15 +282,32 @@ MCLBM_API int mclbm_leray_params(const double* X, int32_t M, int32_t transpose, 
  * kind 6: the direct kernel with the exact entropic gamma (contexts with
  * MCLBM_OPT_EXACT_GAMMA, and only they; vec = the first of the type's list, block 128).
  * Results do not depend on the shape (same arithmetic per node, every operation
- * rounded once in the same order). */
+ * rounded once in the same order).  mclbm_set_launch sets the shape of every step (under AA
+ * streaming, of both parities); mclbm_get_launch reports the shape of pull steps and AA even
+ * steps.  Errors: INVALID_ARG (unsupported shape, vec not dividing N, kind 6 on a context
+ * without MCLBM_OPT_EXACT_GAMMA or another kind on one with it). */
 MCLBM_API int mclbm_set_launch(mclbm_ctx* ctx, int32_t kind, int32_t vec, int32_t block);
 MCLBM_API int mclbm_get_launch(const mclbm_ctx* ctx, int32_t* kind, int32_t* vec, int32_t* block);
 
+/* Shape of one parity of an AA context: parity 0 the even steps (own node, no shifts),
+ * parity 1 the odd steps (shifted loads and shifted stores, which favour other shapes).
+ * Each AA step already runs as one launch per parity, so the two shapes never share a
+ * launch.  Kind 1 (staged) serves both parities: setting it for one sets it for both, and
+ * setting another kind for one parity while the other is staged replaces both.  The
+ * defaults are measured per parity.  Pull contexts: parity 0 only.  Errors: INVALID_ARG as
+ * for mclbm_set_launch, parity not 0 or 1, parity 1 on a pull context. */
+MCLBM_API int mclbm_set_launch_parity(mclbm_ctx* ctx, int32_t parity, int32_t kind, int32_t vec, int32_t block);
+MCLBM_API int mclbm_get_launch_parity(const mclbm_ctx* ctx, int32_t parity, int32_t* kind, int32_t* vec,
+                                      int32_t* block);
+
 /* Time every supported shape on this context for trial_steps steps each (CUDA events
- * on the context's stream), keep the fastest, and restore the initial state by
- * re-running the initialisation from the stored parameters.  Must directly follow
- * mclbm_init_ensemble / mclbm_init_tgv (INVALID_ARG otherwise).  Outputs may be NULL;
- * best_ms is the time per step.  Synchronises. */
+ * on the context's stream; AA: trial_steps steps of each parity, timed per parity), keep the
+ * fastest (AA: the fastest of each parity, or the staged kind for both where it is faster
+ * over a pair of steps), and restore the initial state by re-running the initialisation from
+ * the stored parameters.  Must directly follow mclbm_init_ensemble / mclbm_init_tgv
+ * (INVALID_ARG otherwise).  Outputs may be NULL; kind, vec and block report the shape of
+ * parity 0 (mclbm_get_launch_parity gives the other); best_ms is the time per step.
+ * Synchronises. */
 MCLBM_API int mclbm_autotune(mclbm_ctx* ctx, int32_t trial_steps, int32_t* kind, int32_t* vec, int32_t* block,
                              double* best_ms);
 
@@ -306,12 +323,20 @@ typedef struct mclbm_batch mclbm_batch;
 MCLBM_API int mclbm_batch_create(mclbm_ctx* const* levels, int32_t nlev, const int32_t* substeps, mclbm_batch** out);
 MCLBM_API void mclbm_batch_destroy(mclbm_batch* b);
 MCLBM_API int mclbm_batch_set_graph(mclbm_batch* b, int32_t enable);
+/* The batch's launch shape (initially that of levels[0]): mclbm_batch_set_launch for every
+ * step, the _parity forms per parity of AA batches, with the rules of
+ * mclbm_set_launch_parity; every level must accept the shape. */
 MCLBM_API int mclbm_batch_set_launch(mclbm_batch* b, int32_t kind, int32_t vec, int32_t block);
+MCLBM_API int mclbm_batch_set_launch_parity(mclbm_batch* b, int32_t parity, int32_t kind, int32_t vec, int32_t block);
+MCLBM_API int mclbm_batch_get_launch_parity(const mclbm_batch* b, int32_t parity, int32_t* kind, int32_t* vec,
+                                            int32_t* block);
 /* Enqueue macro_steps macro steps.  Enqueued only. */
 MCLBM_API int mclbm_batch_step(mclbm_batch* b, int64_t macro_steps);
 MCLBM_API int64_t mclbm_batch_macro_steps(const mclbm_batch* b);
 /* Autotune the batch's launch shape (one macro step per trial, trials trials per
- * shape), then re-initialise every level.  Must directly follow initialisation. */
+ * shape): one shape for both parities first, then for AA batches the odd steps' shape with
+ * that even shape (unless the staged kind won); then re-initialise every level.  Must
+ * directly follow initialisation.  kind, vec and block report parity 0. */
 MCLBM_API int mclbm_batch_autotune(mclbm_batch* b, int32_t trials, int32_t* kind, int32_t* vec, int32_t* block,
                                    double* best_ms);
 

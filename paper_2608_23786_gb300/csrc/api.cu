@@ -150,22 +150,37 @@ void leray_map(const double* X, int M, bool transpose, double* Y)
 }
 
 // Default launch shape: the fastest measured on a GB300 for the 64^3 x 64 and 128^3 x 32
-// ensembles (the autotuner may pick another).  D3Q19: FP32 packed collision, 2 nodes per
-// thread; FP16 pull shared-memory prefetch ring, 8 nodes per thread; FP16 AA packed
-// collision, 4 nodes per thread; FP64 (bound by the FP64 units) the direct kernel.
+// ensembles (the autotuner may pick another), for pull steps and AA even steps.  D3Q19: FP32
+// packed collision, 2 nodes per thread; FP16 shared-memory prefetch ring, 8 nodes per thread;
+// FP64 (bound by the FP64 units) the direct kernel.
 LaunchConfig default_launch(int precision, int pattern, int options)
 {
     if (options & MCLBM_OPT_EXACT_GAMMA) return LaunchConfig{exact_vec(precision), 128, 6};
 #ifdef MCLBM_D3Q27
-    // D3Q27 (measured): FP32 prefetching kernel (pull: one-node collision, AA: packed); FP16
-    // pull the direct kernel, AA the prefetching one
+    // D3Q27 (measured): FP32 prefetching kernel (AA even steps: blocks of 256); FP16 pull the
+    // direct kernel, AA even steps the packed prefetching one in blocks of 256
     if (precision == MCLBM_FP64) return LaunchConfig{1, 128, 0};
-    if (precision == MCLBM_FP32) return pattern == MCLBM_PULL ? LaunchConfig{2, 128, 2} : LaunchConfig{2, 128, 3};
-    return pattern == MCLBM_PULL ? LaunchConfig{4, 128, 0} : LaunchConfig{4, 128, 2};
+    if (precision == MCLBM_FP32) return pattern == MCLBM_PULL ? LaunchConfig{2, 128, 2} : LaunchConfig{2, 256, 2};
+    return pattern == MCLBM_PULL ? LaunchConfig{4, 128, 0} : LaunchConfig{4, 256, 3};
 #else
     if (precision == MCLBM_FP64) return LaunchConfig{2, 128, 0};
     if (precision == MCLBM_FP32) return LaunchConfig{2, 128, 3};
-    return pattern == MCLBM_PULL ? LaunchConfig{8, 128, 4} : LaunchConfig{4, 128, 3};
+    return LaunchConfig{8, 128, 4};
+#endif
+}
+
+// AA odd steps read and write shifted rows and favour other shapes (measured per parity at
+// 128^3 x 32 and 64^3 x 64): D3Q19 FP32 the two-stage cp.async ring with 4 nodes per thread,
+// FP16 the packed prefetching kernel with 4; D3Q27 FP32 the packed prefetching kernel, FP16 the
+// one-node prefetching kernel, both in blocks of 128.
+LaunchConfig default_launch_odd(int precision, int pattern, int options)
+{
+    const LaunchConfig even = default_launch(precision, pattern, options);
+    if (pattern != MCLBM_AA || even.kind == 6 || precision == MCLBM_FP64) return even;
+#ifdef MCLBM_D3Q27
+    return precision == MCLBM_FP32 ? LaunchConfig{2, 128, 3} : LaunchConfig{4, 128, 2};
+#else
+    return precision == MCLBM_FP32 ? LaunchConfig{4, 128, 5} : LaunchConfig{4, 128, 3};
 #endif
 }
 
@@ -304,6 +319,7 @@ int mclbm_create(const mclbm_config* cfg, void* d_pop, size_t pop_bytes, void* d
     c->elem_bytes = elem_bytes_of(cfg->precision);
     c->twiddles_ready = false;
     c->launch = default_launch(cfg->precision, cfg->pattern, cfg->options);
+    c->launch_odd = default_launch_odd(cfg->precision, cfg->pattern, cfg->options);
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
     c->num_sms = sms;

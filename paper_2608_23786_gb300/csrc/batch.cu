@@ -23,7 +23,8 @@ struct mclbm_batch {
     int S;
     int period;  // macro steps per captured graph
     cudaStream_t stream;
-    mclbm::LaunchConfig launch;
+    mclbm::LaunchConfig launch;      // pull steps and AA even steps
+    mclbm::LaunchConfig launch_odd;  // AA odd steps
     bool use_graph;
     bool warmed;
     std::map<std::vector<int64_t>, cudaGraphExec_t> graphs;
@@ -54,7 +55,7 @@ void clear_graphs(mclbm_batch* b)
     b->graphs.clear();
 }
 
-cudaError_t macro_direct(mclbm_batch* b, const LaunchConfig& cfg)
+cudaError_t macro_direct(mclbm_batch* b, const LaunchConfig& cfg, const LaunchConfig& cfg_odd)
 {
     std::vector<mclbm_ctx*> part;
     for (int s = 0; s < b->S; ++s) {
@@ -62,7 +63,7 @@ cudaError_t macro_direct(mclbm_batch* b, const LaunchConfig& cfg)
         for (size_t l = 0; l < b->lev.size(); ++l)
             if (s % (b->S / b->sub[l]) == 0) part.push_back(b->lev[l]);
         if (part.empty()) continue;
-        cudaError_t e = launch_levels(part.data(), (int)part.size(), cfg, b->stream, nullptr);
+        cudaError_t e = launch_levels(part.data(), (int)part.size(), cfg, cfg_odd, b->stream, nullptr);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -94,7 +95,7 @@ int capture(mclbm_batch* b, cudaGraphExec_t* out)
     const Saved before = save(b);
     MCLBM_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    for (int p = 0; p < b->period && e == cudaSuccess; ++p) e = macro_direct(b, b->launch);
+    for (int p = 0; p < b->period && e == cudaSuccess; ++p) e = macro_direct(b, b->launch, b->launch_odd);
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
     restore(b, before);
@@ -161,6 +162,36 @@ std::vector<LaunchConfig> candidates(int precision, int N, bool exact)
     return v;
 }
 
+int check_shape(const mclbm_ctx* ctx, const LaunchConfig& c)
+{
+    if (!launch_supported(ctx->cfg.precision, c) || c.vec < 1 || ctx->N % c.vec)
+        return set_error(MCLBM_ERR_INVALID_ARG, "unsupported launch shape (kind " + std::to_string(c.kind) + ", vec " +
+                                                    std::to_string(c.vec) + ", block " + std::to_string(c.block) + ")");
+    if ((c.kind == 6) != ((ctx->cfg.options & MCLBM_OPT_EXACT_GAMMA) != 0))
+        return set_error(MCLBM_ERR_INVALID_ARG, "kind 6 is the launch of contexts with MCLBM_OPT_EXACT_GAMMA, and only it");
+    return MCLBM_OK;
+}
+
+// Shape of one parity given as (kind, vec, block): parity 1 (AA odd steps) needs an AA context,
+// and the staged kind serves both parities, so it is set (or replaced) for both.
+int set_parity_shape(const std::vector<mclbm_ctx*>& lev, LaunchConfig& even, LaunchConfig& odd, int parity,
+                     const LaunchConfig& c)
+{
+    if (parity != 0 && parity != 1) return set_error(MCLBM_ERR_INVALID_ARG, "parity must be 0 or 1");
+    if (parity == 1 && lev[0]->cfg.pattern != MCLBM_AA)
+        return set_error(MCLBM_ERR_INVALID_ARG, "parity 1 (odd steps) has its own shape only under AA streaming");
+    for (auto* l : lev) {
+        int st = check_shape(l, c);
+        if (st != MCLBM_OK) return st;
+    }
+    if (c.kind == 1 || (parity == 0 ? odd.kind : even.kind) == 1) {
+        even = odd = c;
+    } else {
+        (parity == 0 ? even : odd) = c;
+    }
+    return MCLBM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -169,21 +200,32 @@ int mclbm_set_launch(mclbm_ctx* ctx, int32_t kind, int32_t vec, int32_t block)
 {
     if (!ctx) return set_error(MCLBM_ERR_INVALID_ARG, "ctx is NULL");
     const LaunchConfig c{vec, kind == 1 ? 0 : block, kind};
-    if (!launch_supported(ctx->cfg.precision, c) || vec < 1 || ctx->N % vec)
-        return set_error(MCLBM_ERR_INVALID_ARG, "unsupported launch shape (kind " + std::to_string(kind) + ", vec " +
-                                                    std::to_string(vec) + ", block " + std::to_string(block) + ")");
-    if ((kind == 6) != ((ctx->cfg.options & MCLBM_OPT_EXACT_GAMMA) != 0))
-        return set_error(MCLBM_ERR_INVALID_ARG, "kind 6 is the launch of contexts with MCLBM_OPT_EXACT_GAMMA, and only it");
-    ctx->launch = c;
+    int st = check_shape(ctx, c);
+    if (st != MCLBM_OK) return st;
+    ctx->launch = ctx->launch_odd = c;
     return MCLBM_OK;
 }
 
 int mclbm_get_launch(const mclbm_ctx* ctx, int32_t* kind, int32_t* vec, int32_t* block)
 {
+    return mclbm_get_launch_parity(ctx, 0, kind, vec, block);
+}
+
+int mclbm_set_launch_parity(mclbm_ctx* ctx, int32_t parity, int32_t kind, int32_t vec, int32_t block)
+{
     if (!ctx) return set_error(MCLBM_ERR_INVALID_ARG, "ctx is NULL");
-    if (kind) *kind = ctx->launch.kind;
-    if (vec) *vec = ctx->launch.vec;
-    if (block) *block = ctx->launch.block;
+    const std::vector<mclbm_ctx*> one{ctx};
+    return set_parity_shape(one, ctx->launch, ctx->launch_odd, parity, LaunchConfig{vec, kind == 1 ? 0 : block, kind});
+}
+
+int mclbm_get_launch_parity(const mclbm_ctx* ctx, int32_t parity, int32_t* kind, int32_t* vec, int32_t* block)
+{
+    if (!ctx) return set_error(MCLBM_ERR_INVALID_ARG, "ctx is NULL");
+    if (parity != 0 && parity != 1) return set_error(MCLBM_ERR_INVALID_ARG, "parity must be 0 or 1");
+    const LaunchConfig& c = parity == 0 ? ctx->launch : ctx->launch_odd;
+    if (kind) *kind = c.kind;
+    if (vec) *vec = c.vec;
+    if (block) *block = c.block;
     return MCLBM_OK;
 }
 
@@ -191,34 +233,56 @@ int mclbm_autotune(mclbm_ctx* ctx, int32_t trial_steps, int32_t* kind, int32_t* 
 {
     if (!ctx || trial_steps < 1) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
     if (ctx->steps != 0) return set_error(MCLBM_ERR_INVALID_ARG, "autotune must directly follow an initialisation");
-    double best = 1e300;
-    LaunchConfig bestc = ctx->launch;
+    // per candidate the time of its even and of its odd steps (one event pair per step; pull
+    // steps all count as even).  AA: the fastest shape of each parity, unless the staged
+    // kind (which serves both parities) is faster over a pair of steps.
+    const bool aa = ctx->cfg.pattern == MCLBM_AA;
+    double best[2] = {1e300, 1e300}, best_staged = 1e300;
+    LaunchConfig bestc[2] = {ctx->launch, ctx->launch_odd}, staged{};
     for (const LaunchConfig& c : candidates(ctx->cfg.precision, ctx->N, (ctx->cfg.options & MCLBM_OPT_EXACT_GAMMA) != 0)) {
-        MCLBM_CUDA(launch_step_with(ctx, c));  // warm-up (first use also sizes the grid)
-        double ms = 0;
-        int st = time_ms(
-            ctx->stream,
-            [&]() {
-                for (int s = 0; s < trial_steps; ++s) {
-                    cudaError_t e = launch_step_with(ctx, c);
-                    if (e != cudaSuccess) return e;
-                }
-                return cudaSuccess;
-            },
-            &ms);
-        if (st != MCLBM_OK) return st;
-        if (ms < best) {
-            best = ms;
-            bestc = c;
+        MCLBM_CUDA(launch_step_with(ctx, c, c));  // warm-up (first use also sizes the grid)
+        double t[2] = {0, 0};
+        int n[2] = {0, 0};
+        for (int s = 0; s < (aa ? 2 : 1) * trial_steps; ++s) {
+            const int par = aa ? (int)(ctx->steps & 1) : 0;
+            double ms = 0;
+            int st = time_ms(ctx->stream, [&]() { return launch_step_with(ctx, c, c); }, &ms);
+            if (st != MCLBM_OK) return st;
+            t[par] += ms;
+            n[par] += 1;
+        }
+        for (int p = 0; p < (aa ? 2 : 1); ++p) {
+            const double per = t[p] / n[p];
+            if (c.kind != 1 && per < best[p]) {
+                best[p] = per;
+                bestc[p] = c;
+            }
+        }
+        const double pair = aa ? t[0] / n[0] + t[1] / n[1] : t[0] / n[0];
+        if (c.kind == 1 && pair < best_staged) {
+            best_staged = pair;
+            staged = c;
         }
     }
-    ctx->launch = bestc;
+    double per_step;
+    if (!aa) {
+        if (best_staged < best[0]) bestc[0] = staged, best[0] = best_staged;
+        ctx->launch = ctx->launch_odd = bestc[0];
+        per_step = best[0];
+    } else if (best_staged < best[0] + best[1]) {
+        ctx->launch = ctx->launch_odd = staged;
+        per_step = best_staged / 2;
+    } else {
+        ctx->launch = bestc[0];
+        ctx->launch_odd = bestc[1];
+        per_step = (best[0] + best[1]) / 2;
+    }
     int st = reinit_ctx(ctx);
     if (st != MCLBM_OK) return st;
-    if (kind) *kind = bestc.kind;
-    if (vec) *vec = bestc.vec;
-    if (block) *block = bestc.block;
-    if (best_ms) *best_ms = best / trial_steps;
+    if (kind) *kind = ctx->launch.kind;
+    if (vec) *vec = ctx->launch.vec;
+    if (block) *block = ctx->launch.block;
+    if (best_ms) *best_ms = per_step;
     return MCLBM_OK;
 }
 
@@ -252,6 +316,7 @@ int mclbm_batch_create(mclbm_ctx* const* levels, int32_t nlev, const int32_t* su
     b->period = odd ? 2 : 1;
     b->stream = levels[0]->stream;
     b->launch = levels[0]->launch;
+    b->launch_odd = levels[0]->launch_odd;
     b->use_graph = b->stream != nullptr;
     b->warmed = false;
     b->macro_steps = 0;
@@ -279,12 +344,34 @@ int mclbm_batch_set_launch(mclbm_batch* b, int32_t kind, int32_t vec, int32_t bl
 {
     if (!b) return set_error(MCLBM_ERR_INVALID_ARG, "batch is NULL");
     const LaunchConfig lc{vec, kind == 1 ? 0 : block, kind};
-    for (auto* c : b->lev)
-        if (!launch_supported(c->cfg.precision, lc) || vec < 1 || c->N % vec)
-            return set_error(MCLBM_ERR_INVALID_ARG, "unsupported launch shape");
-    b->launch = lc;
+    for (auto* c : b->lev) {
+        int st = check_shape(c, lc);
+        if (st != MCLBM_OK) return st;
+    }
+    b->launch = b->launch_odd = lc;
     clear_graphs(b);
     b->warmed = false;
+    return MCLBM_OK;
+}
+
+int mclbm_batch_set_launch_parity(mclbm_batch* b, int32_t parity, int32_t kind, int32_t vec, int32_t block)
+{
+    if (!b) return set_error(MCLBM_ERR_INVALID_ARG, "batch is NULL");
+    int st = set_parity_shape(b->lev, b->launch, b->launch_odd, parity, LaunchConfig{vec, kind == 1 ? 0 : block, kind});
+    if (st != MCLBM_OK) return st;
+    clear_graphs(b);
+    b->warmed = false;
+    return MCLBM_OK;
+}
+
+int mclbm_batch_get_launch_parity(const mclbm_batch* b, int32_t parity, int32_t* kind, int32_t* vec, int32_t* block)
+{
+    if (!b) return set_error(MCLBM_ERR_INVALID_ARG, "batch is NULL");
+    if (parity != 0 && parity != 1) return set_error(MCLBM_ERR_INVALID_ARG, "parity must be 0 or 1");
+    const LaunchConfig& c = parity == 0 ? b->launch : b->launch_odd;
+    if (kind) *kind = c.kind;
+    if (vec) *vec = c.vec;
+    if (block) *block = c.block;
     return MCLBM_OK;
 }
 
@@ -306,7 +393,7 @@ int mclbm_batch_step(mclbm_batch* b, int64_t macro_steps)
             b->macro_steps += b->period;
             macro_steps -= b->period;
         } else {
-            MCLBM_CUDA(macro_direct(b, b->launch));
+            MCLBM_CUDA(macro_direct(b, b->launch, b->launch_odd));
             b->warmed = true;
             b->macro_steps += 1;
             macro_steps -= 1;
@@ -322,31 +409,55 @@ int mclbm_batch_autotune(mclbm_batch* b, int32_t trials, int32_t* kind, int32_t*
         if (c->steps != 0) return set_error(MCLBM_ERR_INVALID_ARG, "autotune must directly follow an initialisation");
     int prec = b->lev[0]->cfg.precision, Nmin = 1 << 30;
     for (auto* c : b->lev) Nmin = c->N < Nmin ? c->N : Nmin;
-    double best = 1e300;
-    LaunchConfig bestc = b->launch;
-    for (const LaunchConfig& c : candidates(prec, Nmin, (b->lev[0]->cfg.options & MCLBM_OPT_EXACT_GAMMA) != 0)) {
-        bool ok = true;
-        for (auto* l : b->lev) ok = ok && (l->N % c.vec == 0);
-        if (!ok) continue;
-        MCLBM_CUDA(macro_direct(b, c));
-        double ms = 0;
-        int st = time_ms(
+    const std::vector<LaunchConfig> cands =
+        candidates(prec, Nmin, (b->lev[0]->cfg.options & MCLBM_OPT_EXACT_GAMMA) != 0);
+    auto fits = [&](const LaunchConfig& c) {
+        for (auto* l : b->lev)
+            if (l->N % c.vec) return false;
+        return true;
+    };
+    auto trial = [&](const LaunchConfig& even, const LaunchConfig& odd, double* ms) {
+        cudaError_t e = macro_direct(b, even, odd);
+        if (e != cudaSuccess) return cuda_check(e, "autotune trial");
+        return time_ms(
             b->stream,
             [&]() {
                 for (int t = 0; t < trials; ++t) {
-                    cudaError_t e = macro_direct(b, c);
-                    if (e != cudaSuccess) return e;
+                    cudaError_t e2 = macro_direct(b, even, odd);
+                    if (e2 != cudaSuccess) return e2;
                 }
                 return cudaSuccess;
             },
-            &ms);
+            ms);
+    };
+    // pass 1: one shape for both parities; pass 2 (AA, unless the staged kind won): the odd
+    // steps' shape with the even steps' shape of pass 1
+    double best = 1e300;
+    LaunchConfig bestc = b->launch, besto = b->launch_odd;
+    for (const LaunchConfig& c : cands) {
+        if (!fits(c)) continue;
+        double ms = 0;
+        int st = trial(c, c, &ms);
         if (st != MCLBM_OK) return st;
         if (ms < best) {
             best = ms;
-            bestc = c;
+            bestc = besto = c;
         }
     }
+    if (b->lev[0]->cfg.pattern == MCLBM_AA && bestc.kind != 1)
+        for (const LaunchConfig& c : cands) {
+            if (!fits(c) || c.kind == 1 || (c.vec == bestc.vec && c.block == bestc.block && c.kind == bestc.kind))
+                continue;
+            double ms = 0;
+            int st = trial(bestc, c, &ms);
+            if (st != MCLBM_OK) return st;
+            if (ms < best) {
+                best = ms;
+                besto = c;
+            }
+        }
     b->launch = bestc;
+    b->launch_odd = besto;
     clear_graphs(b);
     b->warmed = false;
     for (auto* c : b->lev) {

@@ -49,7 +49,8 @@ struct mclbm_ctx {
     std::vector<double> init_coeffs;  // coefficients the initialisation evaluates (L params with the Leray option)
     size_t elem_bytes;
     bool twiddles_ready;  // FFT twiddle table computed in the work buffer
-    mclbm::LaunchConfig launch;  // stepper variant (autotuned or default)
+    mclbm::LaunchConfig launch;      // stepper variant of pull steps and AA even steps (autotuned or default)
+    mclbm::LaunchConfig launch_odd;  // AA odd steps (pull: equal to launch)
     int num_sms;
     double grad_ms[4];  // last mclbm_grad: forward, recompute, reverse (adjoint kernels), parameter reduction
 };
@@ -73,13 +74,16 @@ void* lattice_ptr(const mclbm_ctx* c, int which);
 // kernels (launchers return cudaError_t of the launch)
 cudaError_t launch_init(const mclbm_ctx* c, const double* d_params);
 cudaError_t launch_step(mclbm_ctx* c);  // one step of one context; updates cur and steps
-cudaError_t launch_step_with(mclbm_ctx* c, const LaunchConfig& cfg);
+cudaError_t launch_step_with(mclbm_ctx* c, const LaunchConfig& cfg, const LaunchConfig& cfg_odd);
 cudaError_t launch_wait_selftest(mclbm_ctx* c);
 // one step of several levels in one launch; updates each level's cur and steps
-cudaError_t launch_levels(mclbm_ctx* const* levels, int nlev, const LaunchConfig& cfg, cudaStream_t s, int* occ);
+// (AA levels at an odd step take cfg_odd, unless cfg is the staged kind, which serves both)
+cudaError_t launch_levels(mclbm_ctx* const* levels, int nlev, const LaunchConfig& cfg, const LaunchConfig& cfg_odd,
+                          cudaStream_t s, int* occ);
 bool vec_supported(int precision, int vec);
 bool launch_supported(int precision, const LaunchConfig& c);
 LaunchConfig default_launch(int precision, int pattern, int options);
+LaunchConfig default_launch_odd(int precision, int pattern, int options);  // AA odd steps
 int exact_vec(int precision);  // the one VEC of the exact-gamma kernel (kind 6)
 void leray_map(const double* X, int M, bool transpose, double* Y);  // api.cu
 cudaError_t launch_get_populations(const mclbm_ctx* c, int sample, double* d_out);

@@ -293,30 +293,30 @@ bool vec_supported(int precision, int vec)
     return in(kVecF16, sizeof(kVecF16) / sizeof(int));
 }
 
-cudaError_t launch_levels(mclbm_ctx* const* lv, int nlev, const LaunchConfig& cfg, cudaStream_t s, int* occ)
+cudaError_t launch_levels(mclbm_ctx* const* lv, int nlev, const LaunchConfig& cfg, const LaunchConfig& cfg_odd,
+                          cudaStream_t s, int* occ)
 {
     if (nlev < 1 || nlev > kMaxLevels) return cudaErrorInvalidValue;
     const int grid_cap = lv[0]->num_sms;
-    auto run = [&](mclbm_ctx* const* group, int n) {
+    auto run = [&](mclbm_ctx* const* group, int n, const LaunchConfig& c) {
         switch (lv[0]->cfg.precision) {
-            case MCLBM_FP64: return levels_t<double>(group, n, cfg, grid_cap, s, occ);
-            case MCLBM_FP32: return levels_t<float>(group, n, cfg, grid_cap, s, occ);
-            default: return levels_t<__half>(group, n, cfg, grid_cap, s, occ);
+            case MCLBM_FP64: return levels_t<double>(group, n, c, grid_cap, s, occ);
+            case MCLBM_FP32: return levels_t<float>(group, n, c, grid_cap, s, occ);
+            default: return levels_t<__half>(group, n, c, grid_cap, s, occ);
         }
     };
-    cudaError_t e;
-    // AA levels of different parity: one launch per parity, so that each takes the kernel
-    // specialised for its parity (the levels are independent, so the order does not matter)
-    mclbm_ctx* even[kMaxLevels];
-    mclbm_ctx* odd[kMaxLevels];
-    int ne = 0, no = 0;
-    if (lv[0]->cfg.pattern == MCLBM_AA && cfg.kind != 1)
+    cudaError_t e = cudaSuccess;
+    if (lv[0]->cfg.pattern == MCLBM_AA && cfg.kind != 1) {
+        // AA: one launch per parity, each with the kernel specialised for that parity and the
+        // parity's own launch shape (the levels are independent, so the order does not matter)
+        mclbm_ctx* even[kMaxLevels];
+        mclbm_ctx* odd[kMaxLevels];
+        int ne = 0, no = 0;
         for (int k = 0; k < nlev; ++k) (lv[k]->steps & 1 ? odd[no++] : even[ne++]) = lv[k];
-    if (ne > 0 && no > 0) {
-        e = run(even, ne);
-        if (e == cudaSuccess) e = run(odd, no);
+        if (ne > 0) e = run(even, ne, cfg);
+        if (e == cudaSuccess && no > 0) e = run(odd, no, cfg_odd);
     } else {
-        e = run(lv, nlev);
+        e = run(lv, nlev, cfg);
     }
     if (e != cudaSuccess) return e;
     for (int k = 0; k < nlev; ++k) {
@@ -326,7 +326,7 @@ cudaError_t launch_levels(mclbm_ctx* const* lv, int nlev, const LaunchConfig& cf
     return cudaSuccess;
 }
 
-cudaError_t launch_step(mclbm_ctx* c) { return launch_step_with(c, c->launch); }
+cudaError_t launch_step(mclbm_ctx* c) { return launch_step_with(c, c->launch, c->launch_odd); }
 
 cudaError_t launch_wait_selftest(mclbm_ctx* c)
 {
@@ -373,10 +373,10 @@ cudaError_t launch_pull_explicit(mclbm_ctx* c, const void* src, void* dst)
     }
 }
 
-cudaError_t launch_step_with(mclbm_ctx* c, const LaunchConfig& cfg)
+cudaError_t launch_step_with(mclbm_ctx* c, const LaunchConfig& cfg, const LaunchConfig& cfg_odd)
 {
     mclbm_ctx* one[1] = {c};
-    return launch_levels(one, 1, cfg, c->stream, nullptr);
+    return launch_levels(one, 1, cfg, cfg_odd, c->stream, nullptr);
 }
 
 }  // namespace mclbm

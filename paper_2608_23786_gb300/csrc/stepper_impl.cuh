@@ -135,66 +135,108 @@ __device__ __forceinline__ float omega_of<float>(const LevelArgs<float>& L) { re
 template <>
 __device__ __forceinline__ float omega_of<__half>(const LevelArgs<__half>& L) { return L.omega32; }
 
-// Gather the VEC values x0 - cxi .. x0 + VEC - 1 - cxi of one row (periodic in x).
+// Element offsets, within one population array, of the run at x0 in the rows y + d and the
+// planes z + d (d = -1, 0, +1; periodic): the run of slot s in row (y + dy, z + dz) starts at
+// s N^3 + z[1 + dz] + y[1 + dy].  They are formed once per run, so each access costs one 32-bit
+// add and one wide multiply-add (N^3 <= 2^30).  The AA odd step, whose loads and stores are both
+// shifted, addresses its rows this way; the pull and AA even kernels form each row address
+// where it is used, which keeps their register count (and resident blocks) lower.
+struct RowOffsets {
+    uint32_t y[3], z[3];
+};
+
+__device__ __forceinline__ RowOffsets row_offsets(const Geom& g, int x0, int y, int z)
+{
+    RowOffsets r;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        r.y[k] = ((uint32_t)g.wrap(y + k - 1) << g.logN) + (uint32_t)x0;
+        r.z[k] = (uint32_t)g.wrap(z + k - 1) << (2 * g.logN);
+    }
+    return r;
+}
+
+template <class P>
+__device__ __forceinline__ P run_at(P base, const Geom& g, int slot, const RowOffsets& r, int dy, int dz)
+{
+    return base + ((uint64_t)(uint32_t)slot * (uint32_t)g.n + (uint64_t)(r.z[1 + dz] + r.y[1 + dy]));
+}
+
+// The same run addressed directly: slot s of row (y + dy, z + dz), element x0.
+template <class P>
+__device__ __forceinline__ P run_direct(P base, const Geom& g, int slot, int x0, int y, int z, int dy, int dz)
+{
+    return base + (int64_t)slot * g.n + g.node(0, g.wrap(y + dy), g.wrap(z + dz)) + x0;
+}
+
+// Offsets from a run's first element (x0) to the element before it and after it in its
+// periodic row.
+__device__ __forceinline__ int before_run(int x0, int N) { return x0 == 0 ? N - 1 : -1; }
+template <int VEC>
+__device__ __forceinline__ int after_run(int x0, int N) { return x0 + VEC == N ? -x0 : VEC; }
+
+// Gather the VEC values x0 - cxi .. x0 + VEC - 1 - cxi of one row (periodic in x); run points
+// at element x0 of the row.
 template <class E, int VEC, int CXI>
-__device__ __forceinline__ void gather_row(const E* row, int x0, int N, int lane, typename Storage<E>::compute (&v)[VEC])
+__device__ __forceinline__ void gather_row(const E* run, int x0, int N, int lane, typename Storage<E>::compute (&v)[VEC])
 {
     E w[VEC];
-    vload<E, VEC>(row + x0, w);
+    vload<E, VEC>(run, w);
     if constexpr (CXI == 0) {
 #pragma unroll
         for (int k = 0; k < VEC; ++k) v[k] = to_c<E>(w[k]);
     } else if constexpr (CXI > 0) {  // source x - 1
         E prev = __shfl_up_sync(0xffffffffu, w[VEC - 1], 1);
-        if (lane == 0 || x0 == 0) prev = sload<E>(row + ((x0 - 1) & (N - 1)));
+        if (lane == 0 || x0 == 0) prev = sload<E>(run + before_run(x0, N));
         v[0] = to_c<E>(prev);
 #pragma unroll
         for (int k = 1; k < VEC; ++k) v[k] = to_c<E>(w[k - 1]);
     } else {  // source x + 1
         E next = __shfl_down_sync(0xffffffffu, w[0], 1);
-        if (lane == 31 || x0 + VEC == N) next = sload<E>(row + ((x0 + VEC) & (N - 1)));
+        if (lane == 31 || x0 + VEC == N) next = sload<E>(run + after_run<VEC>(x0, N));
 #pragma unroll
         for (int k = 0; k < VEC - 1; ++k) v[k] = to_c<E>(w[k + 1]);
         v[VEC - 1] = to_c<E>(next);
     }
 }
 
-// Scatter the VEC values of nodes x0..x0+VEC-1 to positions shifted by CXI in x.
+// Scatter the VEC values of nodes x0..x0+VEC-1 to positions shifted by CXI in x; run points
+// at element x0 of the destination row.
 template <class E, int VEC, int CXI>
-__device__ __forceinline__ void scatter_row(E* row, int x0, int N, int lane, const typename Storage<E>::compute (&v)[VEC])
+__device__ __forceinline__ void scatter_row(E* run, int x0, int N, int lane, const typename Storage<E>::compute (&v)[VEC])
 {
     E w[VEC];
 #pragma unroll
     for (int k = 0; k < VEC; ++k) w[k] = from_c<E>(v[k]);
     if constexpr (CXI == 0) {
-        vstore<E, VEC>(row + x0, w);
+        vstore<E, VEC>(run, w);
     } else if constexpr (CXI > 0) {  // node x goes to x + 1
         const E prev = __shfl_up_sync(0xffffffffu, w[VEC - 1], 1);
         const bool can_receive = lane != 0 && x0 != 0;
-        if (lane == 31 || x0 + VEC == N) row[(x0 + VEC) & (N - 1)] = w[VEC - 1];
+        if (lane == 31 || x0 + VEC == N) run[after_run<VEC>(x0, N)] = w[VEC - 1];
         if (can_receive) {
             E o[VEC];
             o[0] = prev;
 #pragma unroll
             for (int k = 1; k < VEC; ++k) o[k] = w[k - 1];
-            vstore<E, VEC>(row + x0, o);
+            vstore<E, VEC>(run, o);
         } else {
 #pragma unroll
-            for (int k = 1; k < VEC; ++k) row[x0 + k] = w[k - 1];
+            for (int k = 1; k < VEC; ++k) run[k] = w[k - 1];
         }
     } else {  // node x goes to x - 1
         const E next = __shfl_down_sync(0xffffffffu, w[0], 1);
         const bool can_receive = lane != 31 && x0 + VEC != N;
-        if (lane == 0 || x0 == 0) row[(x0 - 1) & (N - 1)] = w[0];
+        if (lane == 0 || x0 == 0) run[before_run(x0, N)] = w[0];
         if (can_receive) {
             E o[VEC];
 #pragma unroll
             for (int k = 0; k < VEC - 1; ++k) o[k] = w[k + 1];
             o[VEC - 1] = next;
-            vstore<E, VEC>(row + x0, o);
+            vstore<E, VEC>(run, o);
         } else {
 #pragma unroll
-            for (int k = 0; k < VEC - 1; ++k) row[x0 + k] = w[k + 1];
+            for (int k = 0; k < VEC - 1; ++k) run[k] = w[k + 1];
         }
     }
 }
@@ -254,27 +296,64 @@ struct Dir {
 
 // Load all Q populations of a run: slot SLOT(i) of the row shifted by -c_i.
 template <class E, int VEC, bool OPP_SLOT, int I = 0>
-__device__ __forceinline__ void gather_all(const E* base, const Geom& g, int x0, int y, int z, int lane,
-                                           typename Storage<E>::compute (&v)[Q][VEC])
+__device__ __forceinline__ void gather_rows(const E* base, const Geom& g, const RowOffsets& r, int x0, int lane,
+                                            typename Storage<E>::compute (&v)[Q][VEC])
 {
     if constexpr (I < Q) {
         constexpr int slot = OPP_SLOT ? Dir<I>::o : I;
-        const E* row = base + (int64_t)slot * g.n + g.node(0, g.wrap(y - Dir<I>::y), g.wrap(z - Dir<I>::z));
-        gather_row<E, VEC, Dir<I>::x>(row, x0, g.N, lane, v[I]);
-        gather_all<E, VEC, OPP_SLOT, I + 1>(base, g, x0, y, z, lane, v);
+        gather_row<E, VEC, Dir<I>::x>(run_at(base, g, slot, r, -Dir<I>::y, -Dir<I>::z), x0, g.N, lane, v[I]);
+        gather_rows<E, VEC, OPP_SLOT, I + 1>(base, g, r, x0, lane, v);
     }
+}
+template <class E, int VEC, int I = 0>
+__device__ __forceinline__ void gather_direct(const E* base, const Geom& g, int x0, int y, int z, int lane,
+                                              typename Storage<E>::compute (&v)[Q][VEC])
+{
+    if constexpr (I < Q) {
+        gather_row<E, VEC, Dir<I>::x>(run_direct(base, g, I, x0, y, z, -Dir<I>::y, -Dir<I>::z), x0, g.N, lane, v[I]);
+        gather_direct<E, VEC, I + 1>(base, g, x0, y, z, lane, v);
+    }
+}
+// OPP_SLOT: the AA odd step (row offsets); otherwise pull (direct addresses).
+template <class E, int VEC, bool OPP_SLOT>
+__device__ __forceinline__ void gather_all(const E* base, const Geom& g, int x0, int y, int z, int lane,
+                                           typename Storage<E>::compute (&v)[Q][VEC])
+{
+    if constexpr (OPP_SLOT)
+        gather_rows<E, VEC, true>(base, g, row_offsets(g, x0, y, z), x0, lane, v);
+    else
+        gather_direct<E, VEC>(base, g, x0, y, z, lane, v);
 }
 
 // Store all Q post-collision populations: slot I of the row shifted by SIGN * c_i.
 template <class E, int VEC, int SIGN, int I = 0>
+__device__ __forceinline__ void scatter_rows(E* base, const Geom& g, const RowOffsets& r, int x0, int lane,
+                                             const typename Storage<E>::compute (&v)[Q][VEC])
+{
+    if constexpr (I < Q) {
+        scatter_row<E, VEC, SIGN * Dir<I>::x>(run_at(base, g, I, r, SIGN * Dir<I>::y, SIGN * Dir<I>::z), x0, g.N,
+                                               lane, v[I]);
+        scatter_rows<E, VEC, SIGN, I + 1>(base, g, r, x0, lane, v);
+    }
+}
+template <class E, int VEC, int I = 0>
+__device__ __forceinline__ void scatter_direct(E* base, const Geom& g, int x0, int y, int z, int lane,
+                                               const typename Storage<E>::compute (&v)[Q][VEC])
+{
+    if constexpr (I < Q) {
+        scatter_row<E, VEC, 0>(run_direct(base, g, I, x0, y, z, 0, 0), x0, g.N, lane, v[I]);
+        scatter_direct<E, VEC, I + 1>(base, g, x0, y, z, lane, v);
+    }
+}
+// SIGN 1: the AA odd step (row offsets); 0: pull, own rows (direct addresses).
+template <class E, int VEC, int SIGN>
 __device__ __forceinline__ void scatter_all(E* base, const Geom& g, int x0, int y, int z, int lane,
                                             const typename Storage<E>::compute (&v)[Q][VEC])
 {
-    if constexpr (I < Q) {
-        E* row = base + (int64_t)I * g.n + g.node(0, g.wrap(y + SIGN * Dir<I>::y), g.wrap(z + SIGN * Dir<I>::z));
-        scatter_row<E, VEC, SIGN * Dir<I>::x>(row, x0, g.N, lane, v[I]);
-        scatter_all<E, VEC, SIGN, I + 1>(base, g, x0, y, z, lane, v);
-    }
+    if constexpr (SIGN != 0)
+        scatter_rows<E, VEC, SIGN>(base, g, row_offsets(g, x0, y, z), x0, lane, v);
+    else
+        scatter_direct<E, VEC>(base, g, x0, y, z, lane, v);
 }
 
 // Own-node aligned access with slot permutation (AA even step).
@@ -367,13 +446,13 @@ struct RunLoc {
 };
 
 template <class E, int VEC, int CXI>
-__device__ __forceinline__ void issue_row(const E* row, int x0, int N, int lane, RawRun<E, VEC>& r)
+__device__ __forceinline__ void issue_row(const E* run, int x0, int N, int lane, RawRun<E, VEC>& r)
 {
-    vload<E, VEC>(row + x0, r.w);
+    vload<E, VEC>(run, r.w);
     if constexpr (CXI > 0) {
-        if (lane == 0 || x0 == 0) r.edge = sload<E>(row + ((x0 - 1) & (N - 1)));
+        if (lane == 0 || x0 == 0) r.edge = sload<E>(run + before_run(x0, N));
     } else if constexpr (CXI < 0) {
-        if (lane == 31 || x0 + VEC == N) r.edge = sload<E>(row + ((x0 + VEC) & (N - 1)));
+        if (lane == 31 || x0 + VEC == N) r.edge = sload<E>(run + after_run<VEC>(x0, N));
     }
 }
 
@@ -400,22 +479,46 @@ __device__ __forceinline__ void finish_row(const RawRun<E, VEC>& r, int x0, int 
 }
 
 template <class E, int VEC, int FIX, int I = 0>
-__device__ __forceinline__ void issue_all(const E* base, const Geom& g, const RunLoc& p, int lane,
-                                          RawRun<E, VEC> (&raw)[Q])
+__device__ __forceinline__ void issue_rows(const E* base, const Geom& g, const RowOffsets& r, const RunLoc& p,
+                                           int lane, RawRun<E, VEC> (&raw)[Q])
 {
     if constexpr (I < Q) {
         const int mode = FIX >= 0 ? FIX : p.mode;
         const bool shift = mode != 1;
         const int slot = mode == 2 ? Dir<I>::o : I;
-        const int ry = shift ? g.wrap(p.y - Dir<I>::y) : p.y;
-        const int rz = shift ? g.wrap(p.z - Dir<I>::z) : p.z;
-        const E* row = base + (int64_t)slot * g.n + g.node(0, ry, rz);
+        const E* run = run_at(base, g, slot, r, shift ? -Dir<I>::y : 0, shift ? -Dir<I>::z : 0);
         if (shift)
-            issue_row<E, VEC, Dir<I>::x>(row, p.x0, g.N, lane, raw[I]);
+            issue_row<E, VEC, Dir<I>::x>(run, p.x0, g.N, lane, raw[I]);
         else
-            issue_row<E, VEC, 0>(row, p.x0, g.N, lane, raw[I]);
-        issue_all<E, VEC, FIX, I + 1>(base, g, p, lane, raw);
+            issue_row<E, VEC, 0>(run, p.x0, g.N, lane, raw[I]);
+        issue_rows<E, VEC, FIX, I + 1>(base, g, r, p, lane, raw);
     }
+}
+template <class E, int VEC, int FIX, int I = 0>
+__device__ __forceinline__ void issue_direct(const E* base, const Geom& g, const RunLoc& p, int lane,
+                                             RawRun<E, VEC> (&raw)[Q])
+{
+    if constexpr (I < Q) {
+        const int mode = FIX >= 0 ? FIX : p.mode;
+        const bool shift = mode != 1;
+        const int slot = mode == 2 ? Dir<I>::o : I;
+        const E* run = run_direct(base, g, slot, p.x0, p.y, p.z, shift ? -Dir<I>::y : 0, shift ? -Dir<I>::z : 0);
+        if (shift)
+            issue_row<E, VEC, Dir<I>::x>(run, p.x0, g.N, lane, raw[I]);
+        else
+            issue_row<E, VEC, 0>(run, p.x0, g.N, lane, raw[I]);
+        issue_direct<E, VEC, FIX, I + 1>(base, g, p, lane, raw);
+    }
+}
+// FIX 2 (AA odd): row offsets; pull, AA even and mixed launches: direct addresses.
+template <class E, int VEC, int FIX>
+__device__ __forceinline__ void issue_all(const E* base, const Geom& g, const RunLoc& p, int lane,
+                                          RawRun<E, VEC> (&raw)[Q])
+{
+    if constexpr (FIX == 2)
+        issue_rows<E, VEC, FIX>(base, g, row_offsets(g, p.x0, p.y, p.z), p, lane, raw);
+    else
+        issue_direct<E, VEC, FIX>(base, g, p, lane, raw);
 }
 
 template <class E, int VEC, int FIX, int I = 0>

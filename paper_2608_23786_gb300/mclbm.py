@@ -90,6 +90,8 @@ _SIGNATURES = {
     "mclbm_w1_restricted_noalloc": (_c.c_int, [_vp, _c.c_int32, _vp, _c.c_int32, _c.c_int32, _vp, _dp, _dp]),
     "mclbm_set_launch": (_c.c_int, [_ctx_p, _c.c_int32, _c.c_int32, _c.c_int32]),
     "mclbm_get_launch": (_c.c_int, [_ctx_p, _i32p, _i32p, _i32p]),
+    "mclbm_set_launch_parity": (_c.c_int, [_ctx_p, _c.c_int32, _c.c_int32, _c.c_int32, _c.c_int32]),
+    "mclbm_get_launch_parity": (_c.c_int, [_ctx_p, _c.c_int32, _i32p, _i32p, _i32p]),
     "mclbm_autotune": (_c.c_int, [_ctx_p, _c.c_int32, _i32p, _i32p, _i32p, _dp]),
     "mclbm_device_status": (_c.c_int, [_ctx_p]),
     "mclbm_grad_required_bytes": (_c.c_int, [_ctx_p, _c.c_int64, _c.c_int32, _size_p]),
@@ -103,6 +105,8 @@ _SIGNATURES = {
     "mclbm_batch_destroy": (None, [_vp]),
     "mclbm_batch_set_graph": (_c.c_int, [_vp, _c.c_int32]),
     "mclbm_batch_set_launch": (_c.c_int, [_vp, _c.c_int32, _c.c_int32, _c.c_int32]),
+    "mclbm_batch_set_launch_parity": (_c.c_int, [_vp, _c.c_int32, _c.c_int32, _c.c_int32, _c.c_int32]),
+    "mclbm_batch_get_launch_parity": (_c.c_int, [_vp, _c.c_int32, _i32p, _i32p, _i32p]),
     "mclbm_batch_step": (_c.c_int, [_vp, _c.c_int64]),
     "mclbm_batch_macro_steps": (_c.c_int64, [_vp]),
     "mclbm_batch_autotune": (_c.c_int, [_vp, _c.c_int32, _i32p, _i32p, _i32p, _dp]),
@@ -361,9 +365,20 @@ def mclbm_set_launch(ctx, vec, block=256, kind=0):
 
 
 def mclbm_get_launch(ctx):
-    """(kind, vec, block) of the context's stepper launch."""
+    """(kind, vec, block) of the context's stepper launch (pull steps, AA even steps)."""
     k, v, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     _check(_L(ctx).mclbm_get_launch(ctx, ctypes.byref(k), ctypes.byref(v), ctypes.byref(b)))
+    return k.value, v.value, b.value
+
+
+def mclbm_set_launch_parity(ctx, parity, vec, block=128, kind=0):
+    _check(_L(ctx).mclbm_set_launch_parity(ctx, int(parity), int(kind), int(vec), int(block)))
+
+
+def mclbm_get_launch_parity(ctx, parity):
+    """(kind, vec, block) of the context's AA steps of that parity (0 even, 1 odd)."""
+    k, v, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(_L(ctx).mclbm_get_launch_parity(ctx, int(parity), ctypes.byref(k), ctypes.byref(v), ctypes.byref(b)))
     return k.value, v.value, b.value
 
 
@@ -404,6 +419,16 @@ def mclbm_batch_set_graph(b, enable):
 
 def mclbm_batch_set_launch(b, vec, block=256, kind=0):
     _check(_L(b).mclbm_batch_set_launch(b, int(kind), int(vec), int(block)))
+
+
+def mclbm_batch_set_launch_parity(b, parity, vec, block=128, kind=0):
+    _check(_L(b).mclbm_batch_set_launch_parity(b, int(parity), int(kind), int(vec), int(block)))
+
+
+def mclbm_batch_get_launch_parity(b, parity):
+    k, v, bl = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(_L(b).mclbm_batch_get_launch_parity(b, int(parity), ctypes.byref(k), ctypes.byref(v), ctypes.byref(bl)))
+    return k.value, v.value, bl.value
 
 
 def mclbm_batch_step(b, macro_steps):

@@ -59,6 +59,52 @@ def test_every_launch_shape_gives_identical_states(precision, pattern, N, steps)
         assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_aa_parities_with_their_own_shapes_give_identical_states(precision):
+    """An AA context whose odd steps take another shape (row offsets, ring kernels) than its
+    even steps reaches the same state, bit for bit, as one shape for both; the shape rules:
+    parity 1 only under AA, the staged kind set for one parity serves both."""
+    N, steps = 32, 5
+    X = gen.draw_params(32, 2)
+    ref = Ensemble(N, 2, Re=300.0, Ma=0.1, precision=precision, pattern="aa").init(X)
+    mclbm.mclbm_set_launch(ref.ctx, 2, 128, 0)
+    ref.step(steps)
+    odd_shapes = [s for s in _shapes(precision, N) if s[0] != 1]
+    for even in [(3, 2, 128), (0, 4, 256)]:
+        for odd in odd_shapes[:: max(1, len(odd_shapes) // 6)]:
+            ens = Ensemble(N, 2, Re=300.0, Ma=0.1, precision=precision, pattern="aa").init(X)
+            mclbm.mclbm_set_launch_parity(ens.ctx, 0, even[1], even[2], even[0])
+            mclbm.mclbm_set_launch_parity(ens.ctx, 1, odd[1], odd[2], odd[0])
+            assert mclbm.mclbm_get_launch_parity(ens.ctx, 0) == even
+            assert mclbm.mclbm_get_launch_parity(ens.ctx, 1) == odd
+            ens.step(steps)
+            mclbm.mclbm_device_status(ens.ctx)
+            for a, b in zip(_states(ref), _states(ens)):
+                assert torch.equal(a, b), (even, odd)
+    ens = Ensemble(N, 2, Re=300.0, Ma=0.1, precision=precision, pattern="aa").init(X)
+    mclbm.mclbm_set_launch_parity(ens.ctx, 1, 2, 0, 1)  # staged: both parities
+    assert mclbm.mclbm_get_launch_parity(ens.ctx, 0) == (1, 2, 0)
+    mclbm.mclbm_set_launch_parity(ens.ctx, 0, 2, 128, 3)  # another kind on one parity replaces both
+    assert mclbm.mclbm_get_launch_parity(ens.ctx, 1) == (3, 2, 128)
+    pull = Ensemble(N, 2, Re=300.0, Ma=0.1, precision=precision, pattern="pull").init(X)
+    with pytest.raises(mclbm.MclbmError):
+        mclbm.mclbm_set_launch_parity(pull.ctx, 1, 2, 128, 3)
+    with pytest.raises(mclbm.MclbmError):
+        mclbm.mclbm_set_launch_parity(ens.ctx, 2, 2, 128, 3)
+
+
+def test_aa_autotune_tunes_each_parity_and_restores_the_initial_state():
+    ens = Ensemble(32, 4, Re=400.0, Ma=0.05, precision="fp16", pattern="aa", seed=9).init()
+    before = _states(ens)
+    kind, vec, block, ms = mclbm.mclbm_autotune(ens.ctx, 2)
+    odd = mclbm.mclbm_get_launch_parity(ens.ctx, 1)
+    assert (kind, vec, block) in _shapes("fp16", 32) and odd in _shapes("fp16", 32) and ms > 0
+    assert (kind == 1) == (odd[0] == 1)
+    assert ens.steps_taken == 0
+    for a, b in zip(before, _states(ens)):
+        assert torch.equal(a, b)
+
+
 def test_autotune_picks_a_supported_shape_and_restores_the_initial_state():
     ens = Ensemble(32, 4, Re=400.0, Ma=0.05, precision="fp32", seed=9).init()
     before = _states(ens)
