@@ -5,8 +5,9 @@
 // A line is the component u_a along axis a for fixed other coordinates (3 N^2
 // lines).  Each block stages L lines in shared memory; thread t owns the lag
 // r = t % (N/2) + 1 of line t / (N/2) and accumulates the p-th powers in FP64
-// over the whole line, keeping its sums in registers across all batches of lines
-// the block handles.  Threads with the same lag are then summed in a fixed
+// over the whole line (contexts with FP32 or FP16 storage: FP32 differences and powers,
+// FP64 accumulation every 32 points), keeping its sums in registers across all batches of
+// lines the block handles.  Threads with the same lag are then summed in a fixed
 // order, and a second kernel sums the blocks in a fixed order: deterministic.
 #include "internal.h"
 #include "storage.cuh"
@@ -58,15 +59,31 @@ __global__ void __launch_bounds__(kThreads) k_sf_axes(const double* __restrict__
         __syncthreads();
         if (active && b * L + lsub < nlines) {
             const double* Lp = line + lsub * N;
-            for (int x = 0; x < N; ++x) {
-                const double d = fabs(Lp[(x + r) & (N - 1)] - Lp[x]);
-                double pw = d * d;
-                acc[0] += pw;
+            if (pmax <= 6) {
+                // |d|^p for p = 2..6 from d^2 and d^4, three of them fused into the accumulation:
+                // 8 FP64 operations per difference instead of 11
+                for (int x = 0; x < N; ++x) {
+                    const double d = Lp[(x + r) & (N - 1)] - Lp[x];
+                    const double ad = fabs(d);
+                    const double d2 = d * d;
+                    acc[0] += d2;
+                    acc[1] = fma(d2, ad, acc[1]);
+                    const double d4 = d2 * d2;
+                    acc[2] += d4;
+                    acc[3] = fma(d4, ad, acc[3]);
+                    acc[4] = fma(d4, d2, acc[4]);
+                }
+            } else {
+                for (int x = 0; x < N; ++x) {
+                    const double d = fabs(Lp[(x + r) & (N - 1)] - Lp[x]);
+                    double pw = d * d;
+                    acc[0] += pw;
 #pragma unroll
-                for (int k = 1; k < kMaxP - 1; ++k) {
-                    if (k + 2 > pmax) break;
-                    pw *= d;
-                    acc[k] += pw;
+                    for (int k = 1; k < kMaxP - 1; ++k) {
+                        if (k + 2 > pmax) break;
+                        pw *= d;
+                        acc[k] += pw;
+                    }
                 }
             }
         }
@@ -74,6 +91,84 @@ __global__ void __launch_bounds__(kThreads) k_sf_axes(const double* __restrict__
     // combine threads of equal lag in a fixed order: stage in shared memory
     __syncthreads();
     double* red = sm;  // [L][halfN][kMaxP-1] fits: L * halfN <= kThreads
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < kMaxP - 1; ++k) red[((int64_t)lsub * halfN + (r - 1)) * (kMaxP - 1) + k] = acc[k];
+    }
+    __syncthreads();
+    for (int o = t; o < halfN * (kMaxP - 1); o += blockDim.x) {
+        double s = 0.0;
+        for (int ls = 0; ls < L; ++ls) s += red[(int64_t)ls * halfN * (kMaxP - 1) + o];
+        partial[(int64_t)blockIdx.x * halfN * (kMaxP - 1) + o] = s;
+    }
+}
+
+// The same sums for contexts with FP32 or FP16 storage, whose velocity field carries FP32
+// precision at most: the lines are staged in FP32, each difference and its powers (p = 2..6) are
+// formed in FP32, summed in FP32 over 32 consecutive points, and those partial sums are
+// accumulated in FP64 (the FP32 sums of 32 positive terms are within 2e-6 relative).  GB300 runs
+// FP32 at many times its FP64 rate, and this kernel is otherwise bound by the FP64 units.
+__global__ void __launch_bounds__(kThreads) k_sf_axes_f32(const double* __restrict__ u, int N, int logN,
+                                                          double* __restrict__ partial)
+{
+    extern __shared__ double sm[];
+    const int halfN = N / 2;
+    const int L = kThreads / halfN > 0 ? kThreads / halfN : 1;
+    float* line = reinterpret_cast<float*>(sm);  // [L][N]
+    const int t = threadIdx.x;
+    const int r = t % halfN + 1;
+    const int lsub = t / halfN;
+    const bool active = lsub < L && t < L * halfN;
+    double acc[kMaxP - 1];
+#pragma unroll
+    for (int k = 0; k < kMaxP - 1; ++k) acc[k] = 0.0;
+    const int64_t n = (int64_t)N * N * N;
+    const int nlines = 3 * N * N;
+    const int nbatches = (nlines + L - 1) / L;
+    const int chunk = N < 32 ? N : 32;
+    for (int b = blockIdx.x; b < nbatches; b += gridDim.x) {
+        __syncthreads();
+        for (int k = t; k < L * N; k += blockDim.x) {
+            const int ls = k / N, j = k % N;
+            const int lid = b * L + ls;
+            float v = 0.f;
+            if (lid < nlines) {
+                const int a = lid / (N * N), rest = lid % (N * N);
+                const int p = rest / N, q = rest % N;
+                int64_t idx;
+                if (a == 0) idx = ((int64_t)p * N + q) * N + j;
+                else if (a == 1) idx = ((int64_t)p * N + j) * N + q;
+                else idx = ((int64_t)j * N + p) * N + q;
+                v = (float)u[(int64_t)a * n + idx];
+            }
+            line[ls * N + j] = v;
+        }
+        __syncthreads();
+        if (active && b * L + lsub < nlines) {
+            const float* Lp = line + lsub * N;
+            for (int x0 = 0; x0 < N; x0 += chunk) {
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
+                for (int x = x0; x < x0 + chunk; ++x) {
+                    const float d = Lp[(x + r) & (N - 1)] - Lp[x];
+                    const float ad = fabsf(d);
+                    const float d2 = d * d;
+                    s0 += d2;
+                    s1 = fmaf(d2, ad, s1);
+                    const float d4 = d2 * d2;
+                    s2 += d4;
+                    s3 = fmaf(d4, ad, s3);
+                    s4 = fmaf(d4, d2, s4);
+                }
+                acc[0] += (double)s0;
+                acc[1] += (double)s1;
+                acc[2] += (double)s2;
+                acc[3] += (double)s3;
+                acc[4] += (double)s4;
+            }
+        }
+    }
+    __syncthreads();
+    double* red = sm;
     if (active) {
 #pragma unroll
         for (int k = 0; k < kMaxP - 1; ++k) red[((int64_t)lsub * halfN + (r - 1)) * (kMaxP - 1) + k] = acc[k];
@@ -118,12 +213,18 @@ cudaError_t launch_sf_axes(mclbm_ctx* c, int pmax, double* h_S)
     double* partial = (double*)(c->work + c->wl.real);  // reuses the spectrum buffer
     double* out = (double*)(c->work + c->wl.bins);      // [M][pmax-1][N/2]
     const size_t smem = sf_axes_smem(N);
-    cudaError_t e = cudaFuncSetAttribute(k_sf_axes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // FP32/FP16 storage and p <= 6: FP32 differences with FP64 accumulation; otherwise FP64
+    const bool f32 = c->cfg.precision != MCLBM_FP64 && pmax <= 6;
+    cudaError_t e = f32 ? cudaFuncSetAttribute(k_sf_axes_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                        : cudaFuncSetAttribute(k_sf_axes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const double scale = 1.0 / (3.0 * (double)c->n);
     for (int m = 0; m < c->M; ++m) {
         if ((e = launch_field(c, m, field)) != cudaSuccess) return e;
-        k_sf_axes<<<kSfBlocks, kThreads, smem, c->stream>>>(field, N, c->logN, pmax, partial);
+        if (f32)
+            k_sf_axes_f32<<<kSfBlocks, kThreads, smem, c->stream>>>(field, N, c->logN, partial);
+        else
+            k_sf_axes<<<kSfBlocks, kThreads, smem, c->stream>>>(field, N, c->logN, pmax, partial);
         k_sf_reduce<<<8, 256, 0, c->stream>>>(partial, kSfBlocks, halfN, pmax, scale,
                                                out + (int64_t)m * (pmax - 1) * halfN);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -101,12 +101,26 @@ def test_sf_trace(N):
     _bins_close(ens.sf_trace(), stats.structure_function_trace(u), 1e-10, 1e-12)
 
 
-@pytest.mark.parametrize("N,pmax", [(8, 6), (16, 6), (32, 3)])
+@pytest.mark.parametrize("N,pmax", [(8, 6), (16, 6), (32, 3), (8, 8)])
 def test_sf_axes(N, pmax):
     ens, u = _pair(N=N, M=2)
     got = ens.sf_axes(pmax)
     ref = stats.structure_function_axes(u, pmax)
     assert _rel(got, ref) <= 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_sf_axes_reduced_precision_storage(precision):
+    """FP32/FP16 storage: differences and powers in FP32, FP64 accumulation of 32-point FP32
+    sums, against the oracle's FP64 evaluation on the same velocity field (N = 64 spans two
+    32-point chunks per line; rows with p = 2..6 within 1e-5 relative); pmax = 8 takes the FP64
+    path for every precision."""
+    ens, u = _pair(N=64, M=2, steps=20, precision=precision)
+    got = ens.sf_axes(6)
+    ref = stats.structure_function_axes(u, 6)
+    assert _rel(got, ref) <= 1e-5, _rel(got, ref)
+    ens8, u8 = _pair(N=8, M=2, precision=precision)
+    assert _rel(ens8.sf_axes(8), stats.structure_function_axes(u8, 8)) <= 1e-10
 
 
 def test_restrict():
