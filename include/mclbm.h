@@ -179,7 +179,9 @@ MCLBM_API int mclbm_set_populations(mclbm_ctx* ctx, int32_t sample, const double
 
 /* Macroscopic moments at the current integer step, pre-collision (Definition of the
  * moments: rho = sum f, rho u = sum c f): d_rho [N^3] (may be NULL) and d_u [3][N^3]
- * physical velocity, FP64 device buffers, for one sample.  Enqueued only. */
+ * physical velocity, FP64 device buffers, for one sample, formed in the arithmetic of the
+ * stepper (FP64 for FP64 storage, FP32 from the stored deviations for FP32/FP16 storage), as
+ * are the fields behind the spectra, structure functions and mean/variance.  Enqueued only. */
 MCLBM_API int mclbm_moments(const mclbm_ctx* ctx, int32_t sample, double* d_rho, double* d_u);
 
 /* Kinetic energy E_m = N^-3 sum |u|^2 / 2 and (if Z != NULL) enstrophy

@@ -72,12 +72,12 @@ __global__ void __launch_bounds__(kBlock) k_moments(const E* __restrict__ lat, G
     for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < g.n; node += (int64_t)gridDim.x * blockDim.x) {
         int x, y, z;
         xyz_of(g, node, x, y, z);
-        double r, ux, uy, uz;
-        node_moments<E, double>(base, g, pattern, parity, x, y, z, r, ux, uy, uz);
-        if (rho_out) rho_out[node] = r;
-        u_out[node] = ux * uscale;
-        u_out[g.n + node] = uy * uscale;
-        u_out[2 * g.n + node] = uz * uscale;
+        typename Storage<E>::compute r, ux, uy, uz;  // FP32 arithmetic for FP32/FP16 storage, as the stepper's
+        node_moments<E, typename Storage<E>::compute>(base, g, pattern, parity, x, y, z, r, ux, uy, uz);
+        if (rho_out) rho_out[node] = (double)r;
+        u_out[node] = (double)ux * uscale;
+        u_out[g.n + node] = (double)uy * uscale;
+        u_out[2 * g.n + node] = (double)uz * uscale;
     }
 }
 

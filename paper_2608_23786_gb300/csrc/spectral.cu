@@ -9,10 +9,10 @@
 // writes the tile back.  Twiddles exp(-2 pi i k / N) come from a table made
 // once per context.
 //
-// Shell sums: one block per shell kappa (or lag radius r) enumerates its integer
+// Shell sums: the blocks of shell kappa (or lag radius r) enumerate its integer
 // points {k in K_N : round(|k|) = kappa}, K_N = {-N/2+1..N/2}^3, with an exact
 // integer test 4|k|^2 in [(2 kappa - 1)^2, (2 kappa + 1)^2), each thread over a
-// fixed subset of (k_z, k_y) rows, then a fixed reduction tree: deterministic.
+// fixed subset of (k_z, k_y) rows, then fixed reduction trees: deterministic.
 #include "internal.h"
 #include "storage.cuh"
 
@@ -134,28 +134,41 @@ __device__ __forceinline__ double block_sum(double v, double* sh)
 
 // Shell sums.  mode 0 (spectrum): out[kappa] = 4 pi / |S| sum |k|^2 psi / 2 * scale.
 // mode 1 (structure function): out[r] = 1/|C| sum 2 (R_0 - R_h), R_h = re(cbuf[h]) * scale.
+// Block (kappa, s) takes every kShellSplit-th thread stride of the rows (k_z, k_y) with
+// |k_z|, |k_y| <= kappa (no other row meets the shell) and, per row, the k_x >= 0 with
+// 4|k|^2 in [(2 kappa - 1)^2, (2 kappa + 1)^2), found in integers; partial[kappa][s] = (sum,
+// count), summed over s in order by k_shell_finish.
+constexpr int kShellSplit = 16;
+
 __global__ void k_shells(const double* __restrict__ psi, const double2* __restrict__ cbuf, int N, int mode, double scale,
-                         double* __restrict__ out)
+                         double* __restrict__ partial)
 {
     __shared__ double sh[32];
-    const int kap = blockIdx.x;
+    const int kap = blockIdx.x, s = blockIdx.y;
     const int64_t lo4 = kap == 0 ? 0 : (int64_t)(2 * kap - 1) * (2 * kap - 1);  // 4|k|^2 >= lo4
     const int64_t hi4 = (int64_t)(2 * kap + 1) * (2 * kap + 1);                   // 4|k|^2 <  hi4
     const int half = N / 2;
+    const int R = kap < half ? kap : half;
+    const int lo = -R > -half + 1 ? -R : -half + 1;  // K_N: -N/2+1..N/2
+    const int side = R - lo + 1;
+    const int64_t rows = (int64_t)side * side;
     const double R0 = mode == 1 ? cbuf[0].x * scale : 0.0;
     double acc = 0.0, cnt = 0.0;
-    for (int p = threadIdx.x; p < N * N; p += blockDim.x) {
-        const int iz = p / N, iy = p % N;
-        const int kz = iz > half ? iz - N : iz, ky = iy > half ? iy - N : iy;  // K_N: -N/2+1..N/2
+    for (int64_t p = (int64_t)s * blockDim.x + threadIdx.x; p < rows; p += (int64_t)gridDim.y * blockDim.x) {
+        const int kz = lo + (int)(p / side), ky = lo + (int)(p % side);
         const int64_t kzy = (int64_t)kz * kz + (int64_t)ky * ky;
-        if (4 * kzy >= hi4) continue;
-        // kx >= 0 with 4 (kzy + kx^2) in [lo4, hi4)
-        const double rem = (double)hi4 / 4.0 - (double)kzy;
-        int kmax = (int)sqrt(rem) + 1;
-        if (kmax > half) kmax = half;
-        for (int kx = 0; kx <= kmax; ++kx) {
+        const int64_t need = lo4 - 4 * kzy, below = hi4 - 4 * kzy;  // 4 kx^2 >= need, 4 kx^2 < below
+        if (below <= 0) continue;
+        int kx0 = need <= 0 ? 0 : (int)sqrt((double)need / 4.0);
+        while (kx0 > 0 && 4 * (int64_t)(kx0 - 1) * (kx0 - 1) >= need) --kx0;
+        while (4 * (int64_t)kx0 * kx0 < need) ++kx0;
+        int kx1 = (int)sqrt((double)below / 4.0);
+        while (kx1 >= 0 && 4 * (int64_t)kx1 * kx1 >= below) --kx1;
+        while (4 * (int64_t)(kx1 + 1) * (kx1 + 1) < below) ++kx1;
+        if (kx1 > half) kx1 = half;
+        const int iz = kz < 0 ? kz + N : kz, iy = ky < 0 ? ky + N : ky;
+        for (int kx = kx0; kx <= kx1; ++kx) {
             const int64_t k4 = 4 * (kzy + (int64_t)kx * kx);
-            if (k4 < lo4 || k4 >= hi4) continue;
             for (int sgn = 0; sgn < 2; ++sgn) {
                 int sx;
                 if (sgn == 0) sx = kx;
@@ -176,11 +189,34 @@ __global__ void k_shells(const double* __restrict__ psi, const double2* __restri
     acc = block_sum(acc, sh);
     cnt = block_sum(cnt, sh);
     if (threadIdx.x == 0) {
+        partial[((int64_t)kap * gridDim.y + s) * 2] = acc;
+        partial[((int64_t)kap * gridDim.y + s) * 2 + 1] = cnt;
+    }
+}
+
+__global__ void k_shell_finish(const double* __restrict__ partial, int nb, int split, int mode, double scale,
+                               double* __restrict__ out)
+{
+    for (int kap = blockIdx.x * blockDim.x + threadIdx.x; kap < nb; kap += gridDim.x * blockDim.x) {
+        double acc = 0.0, cnt = 0.0;
+        for (int s = 0; s < split; ++s) {
+            acc += partial[((int64_t)kap * split + s) * 2];
+            cnt += partial[((int64_t)kap * split + s) * 2 + 1];
+        }
         if (mode == 0)
             out[kap] = cnt > 0 ? 4.0 * 3.14159265358979323846 / cnt * acc * scale : 0.0;
         else
             out[kap] = cnt > 0 ? acc / cnt : 0.0;
     }
+}
+
+cudaError_t shells(const mclbm_ctx* c, const double* psi, const double2* cbuf, int mode, double scale, double* out)
+{
+    const int nb = c->N / 2 + 1;
+    double* partial = (double*)(c->work + c->wl.partial);
+    k_shells<<<dim3(nb, kShellSplit), 256, 0, c->stream>>>(psi, cbuf, c->N, mode, scale, partial);
+    k_shell_finish<<<(nb + 255) / 256, 256, 0, c->stream>>>(partial, nb, kShellSplit, mode, mode == 0 ? scale : 1.0, out);
+    return cudaGetLastError();
 }
 
 int grid_for(int64_t total)
@@ -235,13 +271,13 @@ cudaError_t launch_spectral(mclbm_ctx* c, double* h_E, double* h_S2)
             k_accum_power<<<grid_for(n), 256, 0, c->stream>>>(cb, psi, n, a == 0);
         }
         // Phi = |u~|^2 with u~ = F(u) / N^3, so Phi = psi / N^6
-        if (h_E) k_shells<<<nb, 256, 0, c->stream>>>(psi, nullptr, c->N, 0, 1.0 / (N3 * N3), bins + (int64_t)m * nb);
+        if (h_E && (e = shells(c, psi, nullptr, 0, 1.0 / (N3 * N3), bins + (int64_t)m * nb)) != cudaSuccess) return e;
         if (h_S2) {
             // R = N^-3 F^-1(psi), F^-1 with the factor N^-3: R_h = re(sum_k psi_k e^{+2 pi i k.h/N}) / N^6
             k_real_to_complex<<<grid_for(n), 256, 0, c->stream>>>(psi, cb, n);
             if ((e = fft3d(c, cb, tw, 1)) != cudaSuccess) return e;
-            k_shells<<<nb, 256, 0, c->stream>>>(nullptr, cb, c->N, 1, 1.0 / (N3 * N3),
-                                                bins + (int64_t)(c->M + m) * nb);
+            if ((e = shells(c, nullptr, cb, 1, 1.0 / (N3 * N3), bins + (int64_t)(c->M + m) * nb)) != cudaSuccess)
+                return e;
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
