@@ -109,6 +109,30 @@ __global__ void k_real_to_complex(const double* __restrict__ in, double2* __rest
         out[k] = make_double2(in[k], 0.0);
 }
 
+// Two real fields in one complex transform: out = a + i b.
+__global__ void k_pack_complex(const double* __restrict__ a, const double* __restrict__ b, double2* __restrict__ out,
+                               int64_t n)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = make_double2(a[k], b[k]);
+}
+
+// Power of the two real fields packed as Z = a + i b: with A, B their transforms,
+// A_k = (Z_k + conj(Z_-k)) / 2 and B_k = (Z_k - conj(Z_-k)) / (2i), so
+// |A_k|^2 + |B_k|^2 = (|Z_k|^2 + |Z_-k|^2) / 2 (index -k taken mod N per axis).
+__global__ void k_accum_power_pair(const double2* __restrict__ in, double* __restrict__ psi, int N, int logN, int first)
+{
+    const int64_t n = (int64_t)N << (2 * logN);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(k & (N - 1)), iy = (int)((k >> logN) & (N - 1)), iz = (int)(k >> (2 * logN));
+        const int64_t km = ((int64_t)((N - iz) & (N - 1)) << (2 * logN)) | ((int64_t)((N - iy) & (N - 1)) << logN) |
+                           (int64_t)((N - ix) & (N - 1));
+        const double2 v = in[k], w = in[km];
+        const double p = 0.5 * ((v.x * v.x + v.y * v.y) + (w.x * w.x + w.y * w.y));
+        psi[k] = first ? p : psi[k] + p;
+    }
+}
+
 __global__ void k_accum_power(const double2* __restrict__ in, double* __restrict__ psi, int64_t n, int first)
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
@@ -265,11 +289,13 @@ cudaError_t launch_spectral(mclbm_ctx* c, double* h_E, double* h_S2)
     cudaError_t e;
     for (int m = 0; m < c->M; ++m) {
         if ((e = launch_field(c, m, field)) != cudaSuccess) return e;
-        for (int a = 0; a < 3; ++a) {
-            k_real_to_complex<<<grid_for(n), 256, 0, c->stream>>>(field + a * n, cb, n);
-            if ((e = fft3d(c, cb, tw, 0)) != cudaSuccess) return e;
-            k_accum_power<<<grid_for(n), 256, 0, c->stream>>>(cb, psi, n, a == 0);
-        }
+        // psi = sum_a |F(u_a)|^2: u_x and u_y share one complex transform, u_z takes one
+        k_pack_complex<<<grid_for(n), 256, 0, c->stream>>>(field, field + n, cb, n);
+        if ((e = fft3d(c, cb, tw, 0)) != cudaSuccess) return e;
+        k_accum_power_pair<<<grid_for(n), 256, 0, c->stream>>>(cb, psi, c->N, c->logN, 1);
+        k_real_to_complex<<<grid_for(n), 256, 0, c->stream>>>(field + 2 * n, cb, n);
+        if ((e = fft3d(c, cb, tw, 0)) != cudaSuccess) return e;
+        k_accum_power<<<grid_for(n), 256, 0, c->stream>>>(cb, psi, n, 0);
         // Phi = |u~|^2 with u~ = F(u) / N^3, so Phi = psi / N^6
         if (h_E && (e = shells(c, psi, nullptr, 0, 1.0 / (N3 * N3), bins + (int64_t)m * nb)) != cudaSuccess) return e;
         if (h_S2) {
