@@ -541,7 +541,7 @@ def main():
     mean = torch.empty((3,) + (wl["N"],) * 3, dtype=torch.float64, device=dev)
     var = torch.empty_like(mean)
     E = np.zeros(wl["M"])
-    kernels_per_step = S + 2 + 1  # S stepper launches, energy (partials + reduce), mean/var
+    kernels_per_step = S + 2  # S stepper launches, one pass for E(t) and the mean/var fields, its energy reduce
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
 
@@ -551,8 +551,7 @@ def main():
         mclbm.mclbm_step(ens.ctx, S)
         if i is not None:
             ev[i][1].record(stream)
-        mclbm.mclbm_mean_var(ens.ctx, mean.data_ptr(), var.data_ptr())
-        mclbm.mclbm_energy(ens.ctx, E)  # synchronises the stream (returns host data)
+        mclbm.mclbm_energy_mean_var(ens.ctx, E, mean.data_ptr(), var.data_ptr())  # synchronises (host E)
 
     for _ in range(max(3, args.warmup)):
         one_step()
@@ -589,9 +588,8 @@ def main():
     def e2e_step():
         mclbm.mclbm_init_ensemble(ens.ctx, params_h.numpy())  # host parameters, H2D inside the call
         mclbm.mclbm_step(ens.ctx, S)
-        mclbm.mclbm_mean_var(ens.ctx, mean.data_ptr(), var.data_ptr())
         e = np.zeros(wl["M"])
-        mclbm.mclbm_energy(ens.ctx, e)
+        mclbm.mclbm_energy_mean_var(ens.ctx, e, mean.data_ptr(), var.data_ptr())
         E_h.copy_(torch.from_numpy(e))
         mv_h[0].copy_(mean, non_blocking=True)
         mv_h[1].copy_(var, non_blocking=True)

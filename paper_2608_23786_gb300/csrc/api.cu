@@ -440,6 +440,19 @@ int mclbm_mean_var(mclbm_ctx* ctx, double* d_mean, double* d_var)
     return MCLBM_OK;
 }
 
+int mclbm_energy_mean_var(mclbm_ctx* ctx, double* E, double* d_mean, double* d_var)
+{
+    if (!ctx || !E || !d_mean || !d_var) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    if (ctx->M < 2) return set_error(MCLBM_ERR_SHAPE, "variance needs M >= 2");
+    if (ctx->M > 1024) {  // the one-pass kernel reduces up to 1024 energies in shared memory
+        MCLBM_CUDA(launch_mean_var(ctx, d_mean, d_var));
+        MCLBM_CUDA(launch_energy(ctx, false, E, nullptr));
+        return MCLBM_OK;
+    }
+    MCLBM_CUDA(launch_energy_mean_var(ctx, E, d_mean, d_var));
+    return MCLBM_OK;
+}
+
 static int ensure_twiddles(mclbm_ctx* ctx)
 {
     if (!ctx->twiddles_ready) {

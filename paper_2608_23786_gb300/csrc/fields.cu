@@ -144,32 +144,114 @@ __global__ void k_reduce_rows(const double* __restrict__ partial, int rows, int 
     if (threadIdx.x == 0) out[k] = acc * scale;
 }
 
-// Ensemble mean and unbiased variance of the physical velocity (Welford, fixed sample order).
-template <class E>
-__global__ void __launch_bounds__(kBlock) k_mean_var(const E* __restrict__ lat, Geom g, int M, int pattern, int parity,
-                                                     double uscale, double* __restrict__ mean, double* __restrict__ var)
+// ---- one pass over the ensemble: mean and unbiased variance fields, optionally E_m(t) ----
+// Thread t takes the run of kRunVec nodes x0 = kRunVec t .. of one row and walks the samples.
+// Its pre-collision populations are gathered with six row offsets per run (rows y - 1..y + 1,
+// planes z - 1..z + 1); MODE 0 pull (slot i of x - c_i), 1 AA even (slot i of x), 2 AA odd
+// (slot opp(i) of x - c_i).  The moments are formed in the storage's compute type, as the
+// stepper's.  Per node the sums of d_m = u_m - u_0 and d_m^2 (m >= 1) are accumulated in FP64
+// (one-pass variance about the first sample: mean = u_0 + S1 / M, var = (S2 - S1^2 / M) / (M - 1),
+// free of the cancellation of raw sums because d is of the size of the spread).  WANT_E: each
+// sample's sum of |u|^2 over the run is reduced across the warp in FP64 and accumulated per warp
+// in shared memory, then per block in a fixed order: partial[m][block].
+constexpr int kRunVec = 2;
+
+template <class E, int MODE>
+__device__ __forceinline__ void gather_run(const E* base, const Geom& g, int x0, int y, int z,
+                                           typename Storage<E>::compute (&f)[Q][kRunVec])
 {
     using C = typename Storage<E>::compute;
-    for (int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; node < g.n; node += (int64_t)gridDim.x * blockDim.x) {
-        int x, y, z;
-        xyz_of(g, node, x, y, z);
-        double mu[3] = {0, 0, 0}, m2[3] = {0, 0, 0};
-        for (int m = 0; m < M; ++m) {
-            C r, ux, uy, uz;
-            node_moments<E, C>(lat + (int64_t)m * Q * g.n, g, pattern, parity, x, y, z, r, ux, uy, uz);
-            const double v[3] = {(double)ux * uscale, (double)uy * uscale, (double)uz * uscale};
-            const double inv = 1.0 / (m + 1);
+    uint32_t yo[3], zo[3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const double d = v[a] - mu[a];
-                mu[a] += d * inv;
-                m2[a] += d * (v[a] - mu[a]);
+    for (int k = 0; k < 3; ++k) {
+        yo[k] = (uint32_t)g.wrap(y + k - 1) << g.logN;
+        zo[k] = (uint32_t)g.wrap(z + k - 1) << (2 * g.logN);
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int slot = MODE == 2 ? opp(i) : i;
+        const int dx = MODE == 1 ? 0 : -cx(i), dy = MODE == 1 ? 0 : -cy(i), dz = MODE == 1 ? 0 : -cz(i);
+        const E* row = base + ((uint64_t)(uint32_t)slot * (uint32_t)g.n + (uint64_t)(zo[1 + dz] + yo[1 + dy]));
+#pragma unroll
+        for (int k = 0; k < kRunVec; ++k) f[i][k] = (C)Storage<E>::load(row + ((x0 + k + dx) & (g.N - 1)));
+    }
+}
+
+template <class E, int MODE, bool WANT_E>
+__global__ void __launch_bounds__(kBlock) k_stats_pass(const E* __restrict__ lat, Geom g, int M, double uscale,
+                                                       double* __restrict__ mean, double* __restrict__ var,
+                                                       double* __restrict__ epart)
+{
+    using C = typename Storage<E>::compute;
+    extern __shared__ double ered[];  // WANT_E: [M][warps of the block]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if constexpr (WANT_E) {
+        for (int k = threadIdx.x; k < M * nw; k += blockDim.x) ered[k] = 0.0;
+        __syncthreads();
+    }
+    const int64_t runs = g.n / kRunVec;
+    const double invM = 1.0 / M;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < runs; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t node = t * kRunVec;
+        int x0, y, z;
+        xyz_of(g, node, x0, y, z);
+        C u0[3][kRunVec];
+        double s1[3][kRunVec], s2[3][kRunVec];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int k = 0; k < kRunVec; ++k) s1[a][k] = s2[a][k] = 0.0;
+        for (int m = 0; m < M; ++m) {
+            C f[Q][kRunVec];
+            gather_run<E, MODE>(lat + (int64_t)m * Q * g.n, g, x0, y, z, f);
+            C e = C(0);
+#pragma unroll
+            for (int k = 0; k < kRunVec; ++k) {
+                C r = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const C v = Storage<E>::shifted ? weight<C>(i) * f[i][k] : f[i][k];
+                    r += v;
+                    if (cx(i) > 0) jx += v; else if (cx(i) < 0) jx -= v;
+                    if (cy(i) > 0) jy += v; else if (cy(i) < 0) jy -= v;
+                    if (cz(i) > 0) jz += v; else if (cz(i) < 0) jz -= v;
+                }
+                if (Storage<E>::shifted) r += C(1);
+                const C ri = C(1) / r;
+                const C u[3] = {jx * ri, jy * ri, jz * ri};
+                if constexpr (WANT_E) e += u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (m == 0) {
+                        u0[a][k] = u[a];
+                    } else {
+                        const double d = (double)(u[a] - u0[a][k]);
+                        s1[a][k] += d;
+                        s2[a][k] = fma(d, d, s2[a][k]);
+                    }
+                }
+            }
+            if constexpr (WANT_E) {
+                double es = (double)e;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) es += __shfl_xor_sync(0xffffffffu, es, o);
+                if (lane == 0) ered[m * nw + warp] += es;
             }
         }
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            mean[a * g.n + node] = mu[a];
-            var[a * g.n + node] = m2[a] / (M - 1);
+        for (int k = 0; k < kRunVec; ++k)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                mean[a * g.n + node + k] = fma(s1[a][k], invM, (double)u0[a][k]) * uscale;
+                var[a * g.n + node + k] = M > 1 ? fma(-s1[a][k] * invM, s1[a][k], s2[a][k]) / (M - 1) * uscale * uscale : 0.0;
+            }
+    }
+    if constexpr (WANT_E) {
+        __syncthreads();
+        for (int m = threadIdx.x; m < M; m += blockDim.x) {
+            double acc = 0.0;
+            for (int w = 0; w < nw; ++w) acc += ered[m * nw + w];
+            epart[(int64_t)m * gridDim.x + blockIdx.x] = 0.5 * uscale * uscale * acc;
         }
     }
 }
@@ -261,13 +343,48 @@ cudaError_t energy_t(mclbm_ctx* c, bool with_z, double* h_E, double* h_Z)
     return cudaStreamSynchronize(c->stream);
 }
 
+constexpr int kStatsBlocks = 152 * 6;  // persistent grid of the statistics pass (fixed: deterministic sums)
+constexpr int kStatsMaxM = 1024;        // samples whose energies the pass reduces in shared memory
+
+template <class E>
+cudaError_t stats_pass_t(const mclbm_ctx* c, double* d_mean, double* d_var, double* h_E)
+{
+    const Geom g = geom_of(c);
+    const E* lat = (const E*)lattice_ptr(c, c->cur);
+    const int mode = c->cfg.pattern == MCLBM_PULL ? 0 : (parity_of(c) == 0 ? 1 : 2);
+    int64_t blocks = (g.n / kRunVec + kBlock - 1) / kBlock;
+    if (blocks > kStatsBlocks) blocks = kStatsBlocks;
+    const double us = uscale_of(c);
+    if (!h_E) {
+        if (mode == 0) k_stats_pass<E, 0, false><<<(int)blocks, kBlock, 0, c->stream>>>(lat, g, c->M, us, d_mean, d_var, nullptr);
+        else if (mode == 1) k_stats_pass<E, 1, false><<<(int)blocks, kBlock, 0, c->stream>>>(lat, g, c->M, us, d_mean, d_var, nullptr);
+        else k_stats_pass<E, 2, false><<<(int)blocks, kBlock, 0, c->stream>>>(lat, g, c->M, us, d_mean, d_var, nullptr);
+        return cudaGetLastError();
+    }
+    double* partial = (double*)(c->work + c->wl.partial);
+    double* res = (double*)(c->work + c->wl.bins);
+    const size_t smem = (size_t)c->M * (kBlock / 32) * sizeof(double);
+    cudaError_t e;
+    if (mode == 0) {
+        if ((e = cudaFuncSetAttribute(k_stats_pass<E, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+        k_stats_pass<E, 0, true><<<(int)blocks, kBlock, smem, c->stream>>>(lat, g, c->M, us, d_mean, d_var, partial);
+    } else if (mode == 1) {
+        if ((e = cudaFuncSetAttribute(k_stats_pass<E, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+        k_stats_pass<E, 1, true><<<(int)blocks, kBlock, smem, c->stream>>>(lat, g, c->M, us, d_mean, d_var, partial);
+    } else {
+        if ((e = cudaFuncSetAttribute(k_stats_pass<E, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+        k_stats_pass<E, 2, true><<<(int)blocks, kBlock, smem, c->stream>>>(lat, g, c->M, us, d_mean, d_var, partial);
+    }
+    k_reduce_rows<<<c->M, kBlock, 0, c->stream>>>(partial, c->M, (int)blocks, 1, 0, 1.0 / (double)c->n, res);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(h_E, res, sizeof(double) * c->M, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess) return e;
+    return cudaStreamSynchronize(c->stream);
+}
+
 template <class E>
 cudaError_t mean_var_t(const mclbm_ctx* c, double* d_mean, double* d_var)
 {
-    k_mean_var<E><<<grid_for(c->n, 1 << 30), kBlock, 0, c->stream>>>((const E*)lattice_ptr(c, c->cur), geom_of(c), c->M,
-                                                                    c->cfg.pattern, parity_of(c), uscale_of(c), d_mean,
-                                                                    d_var);
-    return cudaGetLastError();
+    return stats_pass_t<E>(c, d_mean, d_var, nullptr);
 }
 
 template <class E>
@@ -308,6 +425,11 @@ cudaError_t launch_energy(mclbm_ctx* c, bool with_z, double* h_E, double* h_Z)
 {
     MCLBM_DISPATCH(c, energy_t, c, with_z, h_E, h_Z);
 }
+cudaError_t launch_energy_mean_var(const mclbm_ctx* c, double* h_E, double* d_mean, double* d_var)
+{
+    MCLBM_DISPATCH(c, stats_pass_t, c, d_mean, d_var, h_E);
+}
+
 cudaError_t launch_mean_var(const mclbm_ctx* c, double* d_mean, double* d_var)
 {
     MCLBM_DISPATCH(c, mean_var_t, c, d_mean, d_var);

@@ -92,6 +92,8 @@ cudaError_t launch_moments(const mclbm_ctx* c, int sample, double* d_rho, double
 cudaError_t launch_field(const mclbm_ctx* c, int sample, double* d_u);  // physical u [3][n]
 cudaError_t launch_energy(mclbm_ctx* c, bool with_enstrophy, double* h_E, double* h_Z);
 cudaError_t launch_mean_var(const mclbm_ctx* c, double* d_mean, double* d_var);
+// mean/var fields and E_m in one pass over the populations (M <= 1024)
+cudaError_t launch_energy_mean_var(const mclbm_ctx* c, double* h_E, double* d_mean, double* d_var);
 cudaError_t launch_restrict(const mclbm_ctx* c, int Q, double* d_out);
 cudaError_t launch_check_finite(mclbm_ctx* c, int* h_bad);
 cudaError_t launch_spectral(mclbm_ctx* c, double* h_E, double* h_S2);

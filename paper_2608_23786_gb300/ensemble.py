@@ -141,6 +141,16 @@ class Ensemble:
         self._exit()
         return mean, var
 
+    def energy_mean_var(self):
+        """(E [M] numpy, mean, var [3][N][N][N] FP64 CUDA tensors) in one pass over the populations."""
+        E = np.zeros(self.M)
+        mean = torch.empty((3,) + (self.N,) * 3, dtype=torch.float64, device=self.device)
+        var = torch.empty_like(mean)
+        self._enter(mean, var)
+        _m.mclbm_energy_mean_var(self.ctx, E, mean.data_ptr(), var.data_ptr())
+        self._exit()
+        return E, mean, var
+
     def spectrum(self):
         E = np.zeros((self.M, self.N // 2 + 1))
         _m.mclbm_spectrum(self.ctx, E)

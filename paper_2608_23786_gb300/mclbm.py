@@ -73,6 +73,7 @@ _SIGNATURES = {
     "mclbm_moments": (_c.c_int, [_ctx_p, _c.c_int32, _vp, _vp]),
     "mclbm_energy": (_c.c_int, [_ctx_p, _dp, _dp]),
     "mclbm_mean_var": (_c.c_int, [_ctx_p, _vp, _vp]),
+    "mclbm_energy_mean_var": (_c.c_int, [_ctx_p, _dp, _vp, _vp]),
     "mclbm_spectrum": (_c.c_int, [_ctx_p, _dp]),
     "mclbm_sf_trace": (_c.c_int, [_ctx_p, _dp]),
     "mclbm_sf_axes": (_c.c_int, [_ctx_p, _c.c_int32, _dp]),
@@ -288,6 +289,10 @@ def mclbm_energy(ctx, E, Z=None):
 
 def mclbm_mean_var(ctx, d_mean, d_var):
     _check(_L(ctx).mclbm_mean_var(ctx, d_mean, d_var))
+
+
+def mclbm_energy_mean_var(ctx, E, d_mean, d_var):
+    _check(_L(ctx).mclbm_energy_mean_var(ctx, _darr(E), d_mean, d_var))
 
 
 def mclbm_spectrum(ctx, E):

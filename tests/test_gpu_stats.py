@@ -3,6 +3,7 @@ C ABI: kinetic energy, enstrophy, mean/variance fields, shell spectrum, trace S2
 axis S_p, restriction and the one-point W1."""
 import numpy as np
 import pytest
+import torch
 
 import ensemble_inputs as gen
 import oracle
@@ -129,6 +130,33 @@ def test_sf_axes_reduced_precision_storage(precision):
     assert _rel(got, stats.structure_function_axes(ug, 6)) <= 1e-5
     ens8, _ = _pair(N=8, M=2, precision=precision)
     assert _rel(ens8.sf_axes(8), stats.structure_function_axes(_gpu_field(ens8), 8)) <= 1e-10
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-6), ("fp16", 2e-6)])
+@pytest.mark.parametrize("pattern,steps", [("pull", 7), ("aa", 6), ("aa", 7)])
+def test_energy_mean_var_one_pass(precision, tol, pattern, steps):
+    """The one-pass E_m + mean/var: energies as mclbm_energy (FP64 storage 1e-12; FP32/FP16
+    storage, whose moments are FP32, within 2e-6), mean and variance bit-identical to
+    mclbm_mean_var, and FP64 storage against the oracle; AA at even and odd parity."""
+    ens, u = _pair(N=16, M=5, steps=steps, precision=precision, pattern=pattern)
+    E, mean, var = ens.energy_mean_var()
+    assert _rel(E, ens.energy()) <= tol
+    m2, v2 = ens.mean_var()
+    assert torch.equal(mean, m2) and torch.equal(var, v2)
+    if precision == "fp64":
+        rm, rv = stats.mean_var(u)
+        np.testing.assert_allclose(mean.cpu().numpy(), rm, rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(var.cpu().numpy(), rv, rtol=1e-9, atol=1e-18)
+        assert _rel(E, stats.kinetic_energy(u)) <= 1e-12
+
+
+def test_energy_mean_var_one_pass_full_warp_rows():
+    """64^3 x 4 (a row spans a full warp and more), FP32 pull: the same agreement."""
+    ens = Ensemble(64, 4, Re=800.0, Ma=0.025, precision="fp32", seed=3).init().step(5)
+    E, mean, var = ens.energy_mean_var()
+    assert _rel(E, ens.energy()) <= 2e-6
+    m2, v2 = ens.mean_var()
+    assert torch.equal(mean, m2) and torch.equal(var, v2)
 
 
 def test_restrict():
