@@ -28,8 +28,9 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(name="rtgv_64cube_x64_fp32_pull", N=64, M=64, Re=800.0, Ma=0.025, precision="fp32",
                 pattern="pull", updates_per_step=50, seed=1)
-KINDS = ["direct", "staged", "prefetch", "prefetch_packed", "async_ring2", "async_ring3"]
-KERNEL_NAMES = ["k_step_batch", "k_step_staged", "k_step_prefetch", "k_step_prefetch", "k_step_async", "k_step_async"]
+KINDS = ["direct", "staged", "prefetch", "prefetch_packed", "async_ring2", "async_ring3", "exact_gamma"]
+KERNEL_NAMES = ["k_step_batch", "k_step_staged", "k_step_prefetch", "k_step_prefetch", "k_step_async", "k_step_async",
+                "k_step_batch"]
 BYTES_PER_LU = {"fp64": 2 * 19 * 8, "fp32": 2 * 19 * 4, "fp16": 2 * 19 * 2}
 STEPPER_SOURCES = ["paper_2608_23786_gb300/csrc/stepper.cu", "paper_2608_23786_gb300/csrc/collide.cuh",
                    "paper_2608_23786_gb300/csrc/storage.cuh", "paper_2608_23786_gb300/csrc/lattice.cuh",
@@ -480,6 +481,8 @@ def main():
                          "(all cores and one core), its statistics per snapshot, and the GPU on cfg1")
     ap.add_argument("--T", type=int, default=500, help="adjoint horizon (steps) of --workload adjoint")
     ap.add_argument("--oracle-child", default=None, choices=["all", "one"], help=argparse.SUPPRESS)
+    ap.add_argument("--exact-gamma", action="store_true",
+                    help="ensemble workload with the exact entropic gamma (Newton per node) instead of the closed form")
     ap.add_argument("--lattice", type=int, default=19, choices=[19, 27],
                     help="velocity set of the ensemble64 workload: 19 (D3Q19, the paper's) or 27 (D3Q27)")
     args = ap.parse_args()
@@ -505,6 +508,8 @@ def main():
     wl["lattice"] = args.lattice
     if args.lattice == 27:
         wl["name"] += "_d3q27"
+    if args.exact_gamma:
+        wl["name"] += "_exact_gamma"
     if args.impl == "reference":
         return run_reference(args, wl)
 
@@ -527,7 +532,8 @@ def main():
     # each rank owns an independent ensemble: samples rank*M .. rank*M + M - 1 of the Philox stream
     X = gen.draw_params(wl["seed"], wl["M"], first_sample=rank * wl["M"])
     ens = Ensemble(wl["N"], wl["M"], Re=wl["Re"], Ma=wl["Ma"], precision=wl["precision"], pattern=wl["pattern"],
-                   seed=wl["seed"], device=dev, stream=stream, lattice=wl["lattice"]).init(X)
+                   seed=wl["seed"], device=dev, stream=stream, lattice=wl["lattice"],
+                   exact_gamma=args.exact_gamma).init(X)
     # launch shape: the library default, an explicit one, or the autotuner's pick on this ensemble
     # (the autotuner restores the initial state)
     if args.launch:

@@ -486,30 +486,40 @@ __device__ __forceinline__ T exact_gamma_refine(const T (&am1)[Q], const T (&b)[
         else if (b[i] < T(0)) lo = fmax(lo, (T(1) + am1[i]) / b[i]);
     }
     if (!(lo < hi)) return g0;
-    T G_lo = 0, G_hi = 0;
+    // H is convex along the line, G = dH/dg (up to a positive factor) increases with g.  Near
+    // equilibrium the minimiser lies beyond the interval (reading of the constrained exact gamma),
+    // so the upper end is tested first; the lower end only when the root lies below the start.
+    T G_hi = 0;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        G_lo += weight<T>(i) * b[i] * log_ratio<T>(am1[i], lo, b[i]);
-        G_hi += weight<T>(i) * b[i] * log_ratio<T>(am1[i], hi, b[i]);
-    }
-    if (!(G_lo > T(0))) return lo;  // H increases over the whole interval
+    for (int i = 0; i < Q; ++i) G_hi += weight<T>(i) * b[i] * log_ratio<T>(am1[i], hi, b[i]);
     if (!(G_hi < T(0))) return hi;  // H decreases over the whole interval
+    const T eps = sizeof(T) == 8 ? T(2.220446049250313e-16) : T(1.1920929e-7);
     T g = (g0 > lo && g0 < hi) ? g0 : T(0.5) * (lo + hi);
+    bool lo_tested = false;
     for (int it = 0; it < max_iter; ++it) {
-        T G = 0, Gp = 0;
+        T G = 0, Gp = 0, S = 0;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const T r = T(1) + am1[i] - g * b[i];
-            G += weight<T>(i) * b[i] * log_ratio<T>(am1[i], g, b[i]);
+            const T t = weight<T>(i) * b[i] * log_ratio<T>(am1[i], g, b[i]);
+            G += t;
+            S += fabs(t);
             Gp -= weight<T>(i) * b[i] * b[i] / r;
+        }
+        if (fabs(G) <= T(4 * Q) * eps * S) return g;  // G at the rounding level of its own terms
+        if (G < T(0) && !lo_tested) {  // the root, if any, lies below g: does H increase from lo?
+            lo_tested = true;
+            T G_lo = 0;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) G_lo += weight<T>(i) * b[i] * log_ratio<T>(am1[i], lo, b[i]);
+            if (!(G_lo > T(0))) return lo;
         }
         if (G > T(0)) lo = g;
         else hi = g;
         T gn = g - G / Gp;
         if (!(gn > lo && gn < hi)) gn = T(0.5) * (lo + hi);
-        const bool done = fabs(gn - g) <= rel_tol * fabs(g) || !(gn > lo && gn < hi);
+        if (fabs(gn - g) <= rel_tol * fabs(g)) return gn;
         g = gn;
-        if (done) break;
     }
     return g;
 }
