@@ -39,9 +39,9 @@ STEPPER_SOURCES = ["paper_2608_23786_gb300/csrc/stepper.cu", "paper_2608_23786_g
                    "paper_2608_23786_gb300/csrc/stepper_f32_pull.cu"]
 # DRAM bytes (read + write) per launch of the stepper on this workload, from one ncu capture of the
 # kernel built from sources with this digest and launched with this shape (kind, vec, block); the
-# capture ran 16 of the 64 samples (318.8 MB read + 267.9 MB written) and is scaled by 64/16.
+# capture ran 16 of the 64 samples (318.9 MB read + 268.1 MB written) and is scaled by 64/16.
 # Reported as null when the sources or the launch shape differ.
-NCU_TRAFFIC = {"sha256": "8b6fd49799a0a2de", "launch": (3, 2, 128), "bytes_per_launch": 4 * (318.808576e6 + 267.861248e6)}
+NCU_TRAFFIC = {"sha256": "ad9450f884c45175", "launch": (3, 2, 128), "bytes_per_launch": 4 * (318.875136e6 + 268.124672e6)}
 
 
 def stepper_digest():
@@ -422,7 +422,11 @@ def run_adjoint(args):
     torch.cuda.set_stream(stream)
     M, T, K = args.M or 16, args.T, 50
     X = gen.draw_params(1, M)
-    ens = Ensemble(64, M, Re=800.0, Ma=0.025, precision="fp32", pattern="pull", device=dev, stream=stream,
+    prec = args.precision or "fp32"
+    if prec == "fp64":
+        raise SystemExit("the adjoint workload times the FP32 reverse sweep (FP32 or FP16 state)")
+    b_state = {"fp32": 4, "fp16": 2}[prec]
+    ens = Ensemble(64, M, Re=800.0, Ma=0.025, precision=prec, pattern="pull", device=dev, stream=stream,
                    lattice=Q).init(X)
     need = mclbm.mclbm_grad_required_bytes(ens.ctx, T, K)
     gbuf = torch.empty(need + 256, dtype=torch.uint8, device=dev)
@@ -442,18 +446,20 @@ def run_adjoint(args):
     ph /= args.steps
     lu = M * 64**3 * T
     peaks, peak_kind = measured_peaks()
-    rev_bytes = 3 * Q * 4 * lu
+    rev_bytes = Q * (b_state + 4 + 4) * lu  # state read, lambda^{t+1} read, lambda^t written
     achieved = rev_bytes / (ph[2] / 1e3) / 1e9
     out = {
         "metric": "adjoint_glups", "value": lu * args.steps / sec / 1e9, "unit": "GLUPS (whole gradient)",
         "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": sec / args.steps * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"rtgv_64cube_x{M}_fp32_{T}steps_ckpt{K}_dE", "lattice": f"D3Q{Q}",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == "fp32" else "f16-storage/f32", "data": "synthetic",
+        "config": {"workload": f"rtgv_64cube_x{M}_{prec}_{T}steps_ckpt{K}_dE", "lattice": f"D3Q{Q}",
                    "l2": "inputs larger than L2"},
         "phases_ms": {"forward": ph[0], "recompute": ph[1], "reverse": ph[2], "reduction": ph[3]},
-        "roofline": {"kernel": "k_adjoint_async<float,2,2>", "bound": "hbm", "achieved": achieved,
+        "roofline": {"kernel": f"k_adjoint_async<{'float' if prec == 'fp32' else '__half'},2,2>", "bound": "hbm",
+                     "achieved": achieved,
                      "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                     "peak_kind": peak_kind, "traffic": None, "algorithmic_bytes_per_lu": 3 * Q * 4,
+                     "peak_kind": peak_kind, "traffic": None, "algorithmic_bytes_per_lu": Q * (b_state + 8),
                      "reverse_glups": lu / (ph[2] / 1e3) / 1e9},
         "grad_finite": bool(np.all(np.isfinite(G))), "clocks": clk.summary(),
     }
