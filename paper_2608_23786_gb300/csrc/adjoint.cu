@@ -127,8 +127,11 @@ __device__ __forceinline__ void adj_issue(const E* sbase, const float* lbase, co
         const int tid = threadIdx.x;
         const E* srow = sbase + (int64_t)I * g.n + g.node(0, g.wrap(p.y - Dir<I>::y), g.wrap(p.z - Dir<I>::z));
         const float* lrow = lbase + (int64_t)I * g.n + g.node(0, g.wrap(p.y + Dir<I>::y), g.wrap(p.z + Dir<I>::z));
-        cp_async<Ring::kVS>(smem + Ring::state_off(stage, I, tid), srow + p.x0);
-        cp_async<Ring::kVL>(smem + Ring::lam_off(stage, I, tid), lrow + p.x0);
+        // one 16-byte copy per group of lanes: consecutive lanes hold consecutive runs of the same
+        // row in consecutive slots, and the group's first run starts on a 16-byte boundary
+        constexpr int kLS = 16 / Ring::kVS, kLL = 16 / Ring::kVL;  // lanes per 16-byte copy
+        if (lane % kLS == 0) cp_async<16>(smem + Ring::state_off(stage, I, tid), srow + p.x0);
+        if (lane % kLL == 0) cp_async<16>(smem + Ring::lam_off(stage, I, tid), lrow + p.x0);
         const bool first = lane == 0 || p.x0 == 0, last = lane == 31 || p.x0 + VEC == g.N;
         const int before = (p.x0 - 1) & (g.N - 1), after = (p.x0 + VEC) & (g.N - 1);
         if constexpr (WRAP) {
@@ -250,9 +253,11 @@ __global__ void __launch_bounds__(kRunBlock) k_adjoint_async(const E* __restrict
         }
         cp_async_commit();
         cp_async_wait<STAGES - 1>();
+        __syncwarp();  // the copies of the lane groups (issued by their first lanes) are complete
         const RunPos p = run_pos(g, t, VEC);
         float hv[Q][VEC], mv[Q][VEC];
         adj_finish<E, VEC, STAGES, WRAP>(smem, stage, g, p, lane, hv, mv);
+        __syncwarp();  // every lane has read this stage before a group's next copy overwrites it
         float2 h2[Q], m2[Q], l2[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
