@@ -157,10 +157,10 @@ LaunchConfig default_launch(int precision, int pattern, int options)
 {
     if (options & MCLBM_OPT_EXACT_GAMMA) return LaunchConfig{exact_vec(precision), 128, 6};
 #ifdef MCLBM_D3Q27
-    // D3Q27 (measured): FP32 prefetching kernel (AA even steps: blocks of 256); FP16 pull the
-    // direct kernel, AA even steps the packed prefetching one in blocks of 256
+    // D3Q27 (measured): FP32 prefetching kernel in blocks of 256; FP16 pull the direct kernel,
+    // AA even steps the packed prefetching one in blocks of 256
     if (precision == MCLBM_FP64) return LaunchConfig{1, 128, 0};
-    if (precision == MCLBM_FP32) return pattern == MCLBM_PULL ? LaunchConfig{2, 128, 2} : LaunchConfig{2, 256, 2};
+    if (precision == MCLBM_FP32) return LaunchConfig{2, 256, 2};
     return pattern == MCLBM_PULL ? LaunchConfig{4, 128, 0} : LaunchConfig{4, 256, 3};
 #else
     if (precision == MCLBM_FP64) return LaunchConfig{2, 128, 0};
