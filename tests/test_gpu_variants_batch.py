@@ -161,6 +161,33 @@ def test_batch_equals_separate_levels(precision, pattern, substeps, graph, macro
         mclbm.mclbm_batch_destroy(b)
 
 
+@pytest.mark.parametrize("precision,even,odd", [("fp32", (3, 2, 128), (5, 4, 128)), ("fp16", (4, 8, 128), (3, 4, 128)),
+                                                ("fp16", (0, 2, 256), (2, 4, 128))])
+def test_aa_batch_with_a_shape_per_parity_equals_separate_levels(precision, even, odd):
+    """An AA batch whose odd steps take another launch shape (the levels' parities differ within
+    a sub-step, so each sub-step splits into one launch per parity), replayed from its graph,
+    equals stepping each level on its own, bit for bit; the shapes read back per parity."""
+    stream = torch.cuda.Stream()
+    lv = _levels(precision, "aa", stream)
+    ref = _levels(precision, "aa", stream)
+    substeps, macro = (1, 4, 16), 3
+    b = mclbm.mclbm_batch_create([e.ctx for e in lv], substeps)
+    try:
+        mclbm.mclbm_batch_set_launch_parity(b, 0, even[1], even[2], even[0])
+        mclbm.mclbm_batch_set_launch_parity(b, 1, odd[1], odd[2], odd[0])
+        assert mclbm.mclbm_batch_get_launch_parity(b, 0) == even
+        assert mclbm.mclbm_batch_get_launch_parity(b, 1) == odd
+        mclbm.mclbm_batch_step(b, macro)
+        stream.synchronize()
+        for e, r, sub in zip(lv, ref, substeps):
+            r.step(macro * sub)
+            mclbm.mclbm_device_status(e.ctx)
+            for a_, c in zip(_states(e), _states(r)):
+                assert torch.equal(a_, c)
+    finally:
+        mclbm.mclbm_batch_destroy(b)
+
+
 def test_batch_autotune_and_validation():
     stream = torch.cuda.Stream()
     lv = _levels("fp32", "pull", stream)
