@@ -504,13 +504,12 @@ def main():
     if args.N or args.M:
         wl["N"] = args.N or wl["N"]
         wl["M"] = args.M or wl["M"]
-        wl["name"] = f"rtgv_{wl['N']}cube_x{wl['M']}_{wl['precision']}_{wl['pattern']}"
     if args.precision:
         wl["precision"] = args.precision
     if args.pattern:
         wl["pattern"] = args.pattern
-    if args.precision or args.pattern:
-        wl["name"] = f"rtgv_64cube_x64_{wl['precision']}_{wl['pattern']}"
+    if args.N or args.M or args.precision or args.pattern:
+        wl["name"] = f"rtgv_{wl['N']}cube_x{wl['M']}_{wl['precision']}_{wl['pattern']}"
     wl["lattice"] = args.lattice
     if args.lattice == 27:
         wl["name"] += "_d3q27"
