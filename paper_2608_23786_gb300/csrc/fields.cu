@@ -1,6 +1,6 @@
 // Macroscopic fields and ensemble reductions read from the population lattice:
-// moments, kinetic energy / enstrophy, ensemble mean and variance, restriction to
-// the common Q^3 grid, and the finiteness scan.
+// moments, kinetic energy / enstrophy, ensemble mean and variance (with the energies in
+// the same pass when asked), restriction to the common Q^3 grid, and the finiteness scan.
 //
 // All sums use a fixed assignment of nodes to threads and a fixed reduction tree,
 // so results are bitwise reproducible from run to run (no floating-point atomics).

@@ -7,7 +7,8 @@
 // global access is a coalesced run of T complex values), applies the
 // bit-reversal permutation on load and log2 N butterfly stages in place, and
 // writes the tile back.  Twiddles exp(-2 pi i k / N) come from a table made
-// once per context.
+// once per context.  The spectrum of a real field pair (u_x, u_y) comes from one
+// transform of u_x + i u_y.
 //
 // Shell sums: the blocks of shell kappa (or lag radius r) enumerate its integer
 // points {k in K_N : round(|k|) = kappa}, K_N = {-N/2+1..N/2}^3, with an exact
