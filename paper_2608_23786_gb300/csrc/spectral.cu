@@ -72,11 +72,19 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pass(double2* __restrict__ 
             const int pos = q & (half - 1);
             const int i0 = ((q >> s) << (s + 1)) + pos;
             const int i1 = i0 + half;
-            double2 w = tw[pos * twstep];
-            if (inverse) w.y = -w.y;
             double2* L = buf + t * N;
             const double2 u = L[i0];
-            const double2 v = cmul(L[i1], w);
+            const double2 x = L[i1];
+            double2 v;
+            if (s == 0) {  // twiddle 1
+                v = x;
+            } else if (s == 1) {  // twiddle 1 or -i (forward) / +i (inverse): a swap, exactly
+                v = pos == 0 ? x : (inverse ? make_double2(-x.y, x.x) : make_double2(x.y, -x.x));
+            } else {
+                double2 w = tw[pos * twstep];
+                if (inverse) w.y = -w.y;
+                v = cmul(x, w);
+            }
             L[i0] = make_double2(u.x + v.x, u.y + v.y);
             L[i1] = make_double2(u.x - v.x, u.y - v.y);
         }
