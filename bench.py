@@ -141,6 +141,127 @@ def oracle_sample(wl, budget_s=10.0, max_samples=2):
     return lu / dt / 1e9, desc, cores
 
 
+# Spec target and the other large configurations, measured after the default timed region
+# (each entry times its own stepper launches with CUDA events on the ensemble's stream, for about
+# half a second, with its own clock record).  (name, N, M, Re, Ma, precision, pattern)
+TARGETS = [("rtgv_128cube_x32_fp32_pull", 128, 32, 1600.0, 0.0125, "fp32", "pull"),
+           ("rtgv_128cube_x32_fp32_aa", 128, 32, 1600.0, 0.0125, "fp32", "aa"),
+           ("rtgv_128cube_x32_fp16_pull", 128, 32, 1600.0, 0.0125, "fp16", "pull"),
+           ("rtgv_128cube_x32_fp16_aa", 128, 32, 1600.0, 0.0125, "fp16", "aa"),
+           ("rtgv_512cube_x4_fp16_aa", 512, 4, 6400.0, 0.003125, "fp16", "aa")]
+LEVELS = [(64, 64, 400.0, 0.025, 1, 1), (128, 32, 1600.0, 0.0125, 4, 2), (256, 8, 3200.0, 0.00625, 16, 3)]
+ALU_KINDS = [("fp64_fma", 2.0), ("fp32_fma", 2.0), ("fp32x2_fma", 2.0), ("half2_fma", 2.0), ("fp32_rcp", 1.0)]
+
+
+def _timed_steps(stream, fn, est_s, target_s=0.5, lo=4, hi=2000):
+    """Number of calls of `fn` (one step or macro step) that fill about target_s seconds, from
+    a first estimate of one call's time est_s."""
+    return int(min(hi, max(lo, round(target_s / max(est_s, 1e-6)))))
+
+
+def _event_time(stream, fn, n):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    fn(n)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3
+
+
+def measure_targets(dev, stream, peaks, peak_kind, lattice=19):
+    """The benchmark spec's target configuration (128^3 x 32, FP32 and FP16 shifted storage, pull and
+    AA), the 512^3 x 4 FP16 AA configuration, and the three-level batch (FP32 pull, FP16 AA),
+    each with the library's default launch shape: GLUPS and HBM fraction of the stepper from
+    CUDA events over whole steps (every step is one stepper launch; a batch macro step is one
+    graph replay of its sub-steps)."""
+    import torch
+    from paper_2608_23786_gb300 import Ensemble, mclbm
+    import ensemble_inputs as gen
+    out = {}
+    for name, N, M, Re, Ma, prec, pat in TARGETS:
+        ens = Ensemble(N, M, Re=Re, Ma=Ma, precision=prec, pattern=pat, seed=2, device=dev, stream=stream,
+                       lattice=lattice).init(gen.draw_params(2, M))
+        step = lambda n: ens.step(n)  # noqa: E731
+        step(4)
+        est = _event_time(stream, step, 4) / 4
+        n = _timed_steps(stream, step, est)
+        n += n % 2  # whole AA step pairs
+        with ClockSampler(dev.index or 0) as clk:
+            sec = _event_time(stream, step, n)
+        mclbm.mclbm_device_status(ens.ctx)
+        lu = M * N**3 * n
+        bpl = BYTES_PER_LU[prec] * lattice // 19
+        ach = bpl * lu / sec / 1e9
+        launch = launch_desc(mclbm.mclbm_get_launch_parity(ens.ctx, 0),
+                             mclbm.mclbm_get_launch_parity(ens.ctx, 1) if pat == "aa" else None)
+        out[name] = {"glups": lu / sec / 1e9, "avg_launch_ms": sec / n * 1e3, "steps_timed": n,
+                     "bytes_per_lu": bpl, "achieved_gbs": ach, "peak_gbs": peaks["hbm_gbs"], "peak_kind": peak_kind,
+                     "frac": ach / peaks["hbm_gbs"], "launch": dict(launch, chosen_by="default"),
+                     "clocks": clk.summary()}
+        del ens
+        torch.cuda.empty_cache()
+    for prec, pat in (("fp32", "pull"), ("fp16", "aa")):
+        levels = [Ensemble(N, M, Re=Re, Ma=Ma, precision=prec, pattern=pat, seed=seed, device=dev, stream=stream,
+                           lattice=lattice).init(gen.draw_params(seed, M)) for N, M, Re, Ma, _, seed in LEVELS]
+        subs = [lv[4] for lv in LEVELS]
+        b = mclbm.mclbm_batch_create([e.ctx for e in levels], subs)
+        macro = lambda n: mclbm.mclbm_batch_step(b, n)  # noqa: E731
+        macro(3)
+        est = _event_time(stream, macro, 2) / 2
+        n = _timed_steps(stream, macro, est, lo=3, hi=200)
+        with ClockSampler(dev.index or 0) as clk:
+            sec = _event_time(stream, macro, n)
+        for e in levels:
+            mclbm.mclbm_device_status(e.ctx)
+        lu = sum(M * N**3 * sub for (N, M, _, _, sub, _) in LEVELS) * n
+        bpl = BYTES_PER_LU[prec] * lattice // 19
+        ach = bpl * lu / sec / 1e9
+        launch = launch_desc(mclbm.mclbm_batch_get_launch_parity(b, 0),
+                             mclbm.mclbm_batch_get_launch_parity(b, 1) if pat == "aa" else None)
+        out[f"levels_64x64_128x32_256x8_{prec}_{pat}"] = {
+            "glups": lu / sec / 1e9, "ms_per_macro_step": sec / n * 1e3, "macro_steps_timed": n, "substeps": subs,
+            "bytes_per_lu": bpl, "achieved_gbs": ach, "peak_gbs": peaks["hbm_gbs"], "peak_kind": peak_kind,
+            "frac": ach / peaks["hbm_gbs"], "launch": dict(launch, chosen_by="default"), "graph": True,
+            "clocks": clk.summary()}
+        mclbm.mclbm_batch_destroy(b)
+        del levels
+        torch.cuda.empty_cache()
+    return out
+
+
+def measure_alu(dev, stream):
+    """Measured arithmetic ceilings of this GPU (fma chains per type, the reciprocal unit):
+    results and floating-point operations per second."""
+    import torch
+    from paper_2608_23786_gb300 import mclbm
+    sink = torch.zeros(1, dtype=torch.float64, device=dev)
+    out = {}
+    for kind, flops_per_result in ALU_KINDS:
+        iters = 64
+        r, ms = mclbm.mclbm_alu_rate(kind, iters, sink.data_ptr(), stream.cuda_stream)
+        iters = int(min(1 << 16, max(64, iters * 50.0 / max(ms, 1e-3))))  # about 50 ms per timed launch
+        r, ms = mclbm.mclbm_alu_rate(kind, iters, sink.data_ptr(), stream.cuda_stream)
+        out[kind] = {"results_per_s": r, "flops": r * flops_per_result, "ms": ms}
+    return out
+
+
+def run_peaks(args):
+    """Measured arithmetic ceilings (FP64, FP32, packed FP32x2 and half2 fma, FP32 reciprocal)
+    with the clocks seen while they ran."""
+    import torch
+    from paper_2608_23786_gb300 import mclbm
+    mclbm.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    measure_alu(dev, stream)  # warm-up
+    with ClockSampler(0) as clk:
+        alu = measure_alu(dev, stream)
+    print(json.dumps({"metric": "alu_peaks", "unit": "results/s", "alu": alu, "clocks": clk.summary(),
+                      "how": "8 blocks x 256 threads per SM, 8 independent chains per thread, CUDA events"}))
+
+
 def run_reference(args, wl):
     """Reference arm: the FP64 oracle timed on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -476,12 +597,15 @@ def main():
     ap.add_argument("--pattern", default=None, choices=["pull", "aa"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end and plain-FP64 legs (profiling)")
+    ap.add_argument("--no-targets", action="store_true",
+                    help="skip the target-configuration entries (128^3 x 32, 512^3 x 4, three-level batches)")
     ap.add_argument("--N", type=int, default=None, help="override the lattice size (profiling of small cases)")
     ap.add_argument("--M", type=int, default=None, help="override the number of samples (profiling of small cases)")
     ap.add_argument("--launch", default=None, help="kind,vec,block instead of the library default (e.g. 0,2,128)")
     ap.add_argument("--autotune", action="store_true", help="let the library's autotuner pick the launch shape")
     ap.add_argument("--workload", default="ensemble64",
-                    choices=["ensemble64", "levels_fp32", "levels_fp16", "large", "adjoint", "oracle_report"],
+                    choices=["ensemble64", "levels_fp32", "levels_fp16", "large", "adjoint", "oracle_report",
+                             "peaks"],
                     help="ensemble64 (default): 64^3 x 64 FP32; levels_*: 3-level batch; large: 512^3 x 4 FP16 AA; "
                          "adjoint: gradient of E(T), 64^3 x 16, 500 steps; oracle_report: the oracle on cfg1/cfg2 "
                          "(all cores and one core), its statistics per snapshot, and the GPU on cfg1")
@@ -500,6 +624,8 @@ def main():
         return run_adjoint(args)
     if args.workload == "oracle_report":
         return run_oracle_report(args)
+    if args.workload == "peaks":
+        return run_peaks(args)
     wl = dict(WORKLOAD)
     if args.N or args.M:
         wl["N"] = args.N or wl["N"]
@@ -668,11 +794,24 @@ def main():
                    "grad_finite": bool(np.all(np.isfinite(G4)))}
         del gbuf, ens4
 
+    peaks, peak_kind = measured_peaks()
+    mclbm.mclbm_device_status(ens.ctx)
+    main_odd = mclbm.mclbm_get_launch_parity(ens.ctx, 1) if wl["pattern"] == "aa" else None
+    targets = alu = plain_ratio = None
+    if not args.no_e2e and not args.no_targets:
+        del ens
+        torch.cuda.empty_cache()
+        targets = measure_targets(dev, stream, peaks, peak_kind, lattice=wl["lattice"])
+        alu = measure_alu(dev, stream)
+        if plain_glups is not None:
+            # the plain FP64 stepper's bandwidth against the copy bandwidth (its arithmetic
+            # ceiling is the measured FP64 fma rate in alu_measured)
+            plain_gbs = plain_glups * BYTES_PER_LU["fp64"] * wl["lattice"] // 19
+            plain_ratio = {"achieved_gbs": plain_gbs, "frac_of_hbm": plain_gbs / peaks["hbm_gbs"]}
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
-    peaks, peak_kind = measured_peaks()
     bpl = BYTES_PER_LU[wl["precision"]] * wl["lattice"] // 19 * wl["M"] * wl["N"] ** 3
     achieved = bpl / stepper_s / 1e9
     digest = stepper_digest()
@@ -694,8 +833,7 @@ def main():
                    "updates_per_step": S,
                    "reductions_per_step": ["E_m(t)", "mean/var fields"], "l2": f"inputs ({bpl / 1e9:.2f} GB moved per update) "
                          "larger than the 129 MB L2: no flush",
-                   "launch": dict(launch_desc(tuned, mclbm.mclbm_get_launch_parity(ens.ctx, 1)
-                                              if wl["pattern"] == "aa" else None),
+                   "launch": dict(launch_desc(tuned, main_odd),
                                   chosen_by="explicit" if args.launch else ("autotuner" if args.autotune else "default"))},
         "roofline": {"kernel": KERNEL_NAMES[tuned[0]] +
                      f"<{wl['precision']},{wl['pattern']},vec={tuned[1]},block={tuned[2]}>",
@@ -708,12 +846,14 @@ def main():
                                          "h2d_bytes_per_step": int(params_h.numel() * 8),
                                          "d2h_bytes_per_step": int(E_h.numel() * 8 + mv_h.numel() * 8)},
         "gpu_launches": kernels_per_step * args.steps,
-        "fp64_plain_single_sample": {"value": plain_glups, "unit": "GLUPS", "N": wl["N"], "M": 1},
+        "fp64_plain_single_sample": dict({"value": plain_glups, "unit": "GLUPS", "N": wl["N"], "M": 1},
+                                         **(plain_ratio or {})),
+        "targets": targets,
+        "alu_measured": alu,
         "adjoint": adjoint,
         "clocks": clk.summary(),
         "stepper_sources_sha256": digest,
     }
-    mclbm.mclbm_device_status(ens.ctx)
     print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()

@@ -399,16 +399,33 @@ MCLBM_API int mclbm_device_status(mclbm_ctx* ctx);
 MCLBM_API int mclbm_w1_restricted_noalloc(const double* d_a, int32_t MA, const double* d_b, int32_t MB, int32_t G,
                                           void* cuda_stream, double* W, double* per_point);
 
+/* Arithmetic throughput of the current device, for setting kernels that are bound by
+ * arithmetic rather than memory against a measured ceiling (the paper has no counterpart:
+ * this is measurement support).  kind 0: FP64 fma; 1: FP32 fma; 2: packed FP32x2 fma (two
+ * results per instruction); 3: packed half2 fma; 4: FP32 reciprocal approximation
+ * (rcp.approx, the special-function unit).  One launch of 8 blocks of 256 threads per SM,
+ * each thread running 8 independent chains of 16 * iters operations, timed with CUDA events
+ * after one untimed launch on cuda_stream.  results_per_s: host, results (lane operations)
+ * per second (an fma result is two floating-point operations); ms: host or NULL, the timed
+ * launch.  d_sink: device, at least 8 bytes, written only if a chain reaches an impossible
+ * value.  Synchronises.  Errors: INVALID_ARG, CUDA. */
+MCLBM_API int mclbm_alu_rate(int32_t kind, int32_t iters, double* d_sink, void* cuda_stream, double* results_per_s,
+                             double* ms);
+
 /* Failure-path self-test: runs one bounded wait on a barrier that nothing completes, so
  * the wait runs out and records MCLBM_ERR_TIMEOUT exactly as a stepper wait would; the
  * next mclbm_device_status reports it and the next initialisation clears it.  No GPU
  * fault, trap or hang is involved.  Enqueued only. */
 MCLBM_API int mclbm_selftest_timeout(mclbm_ctx* ctx);
 
-/* Checkpoint of the current state: configuration, step count, parameters and the
- * stored populations, to a host file (written after synchronising the stream).
- * mclbm_load restores it into a context of the same N, M, precision and pattern.
- * Errors: IO (cannot open, truncated, not a checkpoint), SHAPE, CUDA. */
+/* Checkpoint of the current state to a host file (written after synchronising the stream):
+ * a magic word, the format version (2), the velocity count Q of the library, the
+ * configuration and its derived units, the step count, the parameters and the stored
+ * populations, and nothing after them.  mclbm_load restores it only into a context of the
+ * same lattice (Q), N, M, precision, pattern, options, viscosity, U_c and derived time step,
+ * U_lat and omega (anything else would resume the state under other dynamics).
+ * Errors: IO (cannot open, truncated, another format version, bytes after the lattice, not
+ * a checkpoint), SHAPE (another lattice or configuration), CUDA. */
 MCLBM_API int mclbm_save(const mclbm_ctx* ctx, const char* path);
 MCLBM_API int mclbm_load(mclbm_ctx* ctx, const char* path);
 

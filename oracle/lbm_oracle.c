@@ -213,7 +213,28 @@ void SYM(shear_part)(const real_t *fneq, real_t *ds)
  * found by bisection.  Dh = 0: gamma = 2 (the paper's BGK value). */
 static int exact_gamma_mode = 0;
 
-void RSYM(set_exact_gamma)(int on) { exact_gamma_mode = on; }
+/* How each exact-gamma node was decided since the mode was last switched on, so that a run can
+ * report how often the constraint binds: [0] Dh = 0 (gamma = 2), [1] empty positivity interval
+ * (closed form kept), [2] minimiser at the lower end, [3] at the upper end, [4] interior root. */
+static long long exact_gamma_counts[5];
+
+void RSYM(set_exact_gamma)(int on)
+{
+    exact_gamma_mode = on;
+    if (on)
+        for (int k = 0; k < 5; ++k) exact_gamma_counts[k] = 0;
+}
+
+void RSYM(exact_gamma_counts)(long long *out)
+{
+    for (int k = 0; k < 5; ++k) out[k] = exact_gamma_counts[k];
+}
+
+static void count_exact_gamma(int k)
+{
+#pragma omp atomic
+    exact_gamma_counts[k] += 1;
+}
 
 static double exact_gamma(const double *f, const double *ds, const double *dh, double omega, double g_closed)
 {
@@ -224,7 +245,10 @@ static double exact_gamma(const double *f, const double *ds, const double *dh, d
         if (B[i] > 0) { double r = A[i] / B[i]; if (r < hi) hi = r; }
         if (B[i] < 0) { double r = A[i] / B[i]; if (r > lo) lo = r; }
     }
-    if (!(lo < hi)) return g_closed;
+    if (!(lo < hi)) {
+        count_exact_gamma(1);
+        return g_closed;
+    }
     /* H is convex along the line: the minimiser over [lo, hi] is an end point where G does not
      * change sign inside, else the root */
     double G_lo = 0, G_hi = 0;
@@ -232,8 +256,15 @@ static double exact_gamma(const double *f, const double *ds, const double *dh, d
         G_lo += dh[i] * log((A[i] - lo * B[i]) / W[i]);
         G_hi += dh[i] * log((A[i] - hi * B[i]) / W[i]);
     }
-    if (!(G_lo > 0)) return lo;
-    if (!(G_hi < 0)) return hi;
+    if (!(G_lo > 0)) {
+        count_exact_gamma(2);
+        return lo;
+    }
+    if (!(G_hi < 0)) {
+        count_exact_gamma(3);
+        return hi;
+    }
+    count_exact_gamma(4);
     for (int it = 0; it < 400; ++it) {
         double mid = 0.5 * (lo + hi);
         if (!(mid > lo && mid < hi)) break;
@@ -266,7 +297,12 @@ void SYM(collide)(const real_t *f, double omega, real_t *fstar, real_t *gamma_ou
     else
         gamma = 2.0 / omega - (2.0 - 2.0 / omega) * sh / hh;
 #ifndef ORC_COMPLEX
-    if (exact_gamma_mode && hh != 0.0) gamma = exact_gamma(f, ds, dh, omega, gamma);
+    if (exact_gamma_mode) {
+        if (hh != 0.0)
+            gamma = exact_gamma(f, ds, dh, omega, gamma);
+        else
+            count_exact_gamma(0);
+    }
 #endif
     for (int i = 0; i < Q; ++i) fstar[i] = f[i] - omega * ds[i] - 0.5 * omega * gamma * dh[i];
     if (gamma_out) *gamma_out = gamma;

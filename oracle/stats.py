@@ -115,17 +115,18 @@ def structure_function_trace(u):
     return out
 
 
-def structure_function_axes(u, pmax=6):
+def structure_function_axes(u, pmax=6, lags=None):
     """Longitudinal structure functions along the lattice axes, Eq. (structuresLocal)
     restricted to n in {e_x, e_y, e_z} with the modulus of Eq. (structures):
     S_p,m(r) = 1/(3 N^3) sum_x sum_a |u_a(x + r e_a) - u_a(x)|^p, r = 1..N/2,
-    p = 2..pmax.  Returns [M][pmax-1][N/2] (index r-1)."""
+    p = 2..pmax.  Returns [M][pmax-1][N/2] (index r-1); with `lags` (a list of r), only those
+    entries are evaluated and the others stay zero (large lattices)."""
     u = np.asarray(u, dtype=np.float64)
     M, N = u.shape[0], u.shape[-1]
     out = np.zeros((M, pmax - 1, N // 2))
     axis_of = {0: -1, 1: -2, 2: -3}
     for m in range(M):
-        for r in range(1, N // 2 + 1):
+        for r in (range(1, N // 2 + 1) if lags is None else lags):
             incs = [np.abs(np.roll(u[m, a], -r, axis=axis_of[a]) - u[m, a]) for a in range(3)]
             for p in range(2, pmax + 1):
                 out[m, p - 2, r - 1] = sum(np.sum(d**p) for d in incs) / (3 * N**3)

@@ -81,6 +81,18 @@ class exact_gamma:
             _fn("set_exact_gamma", lattice=q)(0)
         return False
 
+    @staticmethod
+    def counts(lattice=19):
+        """How the nodes collided since the context was entered were decided: a dict of counts
+        'dh_zero' (gamma = 2), 'empty' (no g keeps every f* positive: closed form kept),
+        'lower_end', 'upper_end' (the constraint binds) and 'interior' (the unconstrained
+        root of Eq. (kbc_entropy) lies inside the interval and is taken)."""
+        out = (ctypes.c_longlong * 5)()
+        fn = _fn("exact_gamma_counts", lattice=lattice)
+        fn.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
+        fn(out)
+        return dict(zip(("dh_zero", "empty", "lower_end", "upper_end", "interior"), list(out)))
+
 
 def collide(f, omega, cplx=False):
     """One-node KBC collision: returns (f*, gamma, Ds, Dh)."""

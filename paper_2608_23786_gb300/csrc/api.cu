@@ -243,7 +243,7 @@ static size_t w1_region_bytes(int M)
 
 extern "C" {
 
-const char* mclbm_version(void) { return "mclbm 0.1.0 (" MCLBM_LATTICE_NAME " KBC, sm_103a)"; }
+const char* mclbm_version(void) { return "mclbm 0.2.0 (" MCLBM_LATTICE_NAME " KBC, sm_103a)"; }
 
 const char* mclbm_last_error(void) { return g_last_error.c_str(); }
 
@@ -549,10 +549,26 @@ int mclbm_selftest_timeout(mclbm_ctx* ctx)
     return MCLBM_OK;
 }
 
-// ---- checkpoint file: magic, version, config, units, steps, cur, params, lattice bytes
+// ---- checkpoint file: magic, format version, velocity count Q, config, units, steps, cur, params,
+// lattice bytes, and nothing after them
 namespace {
-constexpr uint64_t kMagic = 0x4d434c424d434b31ull;  // "MCLBMCK1"
+constexpr uint64_t kMagic = 0x4d434c424d434b32ull;  // "MCLBMCK2"
+constexpr int32_t kFormatVersion = 2;
+
+// The fields that fix the dynamics of a resumed state: a checkpoint restores only into a context
+// whose lattice, shape, storage, streaming pattern, units and options are the same.
+bool same_dynamics(const mclbm_config& a, const mclbm_units& ua, const mclbm_config& b, const mclbm_units& ub,
+                   std::string* why)
+{
+    if (a.N != b.N || a.M != b.M) { *why = "N or M"; return false; }
+    if (a.precision != b.precision) { *why = "storage precision"; return false; }
+    if (a.pattern != b.pattern) { *why = "streaming pattern"; return false; }
+    if (a.options != b.options) { *why = "options (exact gamma / Leray)"; return false; }
+    if (a.nu != b.nu || a.U_c != b.U_c) { *why = "viscosity or U_c"; return false; }
+    if (ua.dt != ub.dt || ua.U_lat != ub.U_lat || ua.omega != ub.omega) { *why = "time step, Ma or omega"; return false; }
+    return true;
 }
+}  // namespace
 
 int mclbm_save(const mclbm_ctx* ctx, const char* path)
 {
@@ -564,8 +580,10 @@ int mclbm_save(const mclbm_ctx* ctx, const char* path)
     FILE* fp = std::fopen(path, "wb");
     if (!fp) return set_error(MCLBM_ERR_IO, std::string("cannot open ") + path + " for writing");
     const uint64_t magic = kMagic, steps = (uint64_t)ctx->steps;
-    const int32_t cur = ctx->cur;
-    bool ok = std::fwrite(&magic, sizeof magic, 1, fp) == 1 && std::fwrite(&ctx->cfg, sizeof ctx->cfg, 1, fp) == 1 &&
+    const int32_t version = kFormatVersion, q = Q, cur = ctx->cur;
+    bool ok = std::fwrite(&magic, sizeof magic, 1, fp) == 1 && std::fwrite(&version, sizeof version, 1, fp) == 1 &&
+              std::fwrite(&q, sizeof q, 1, fp) == 1 && std::fwrite(&ctx->cfg, sizeof ctx->cfg, 1, fp) == 1 &&
+              std::fwrite(&ctx->units, sizeof ctx->units, 1, fp) == 1 &&
               std::fwrite(&steps, sizeof steps, 1, fp) == 1 && std::fwrite(&cur, sizeof cur, 1, fp) == 1 &&
               std::fwrite(ctx->params.data(), sizeof(double), ctx->params.size(), fp) == ctx->params.size() &&
               std::fwrite(host.data(), 1, bytes, fp) == bytes;
@@ -580,21 +598,41 @@ int mclbm_load(mclbm_ctx* ctx, const char* path)
     FILE* fp = std::fopen(path, "rb");
     if (!fp) return set_error(MCLBM_ERR_IO, std::string("cannot open ") + path);
     uint64_t magic = 0, steps = 0;
-    int32_t cur = 0;
+    int32_t version = 0, q = 0, cur = 0;
     mclbm_config cfg;
+    mclbm_units units;
+    bool ok = std::fread(&magic, sizeof magic, 1, fp) == 1 && magic == kMagic &&
+              std::fread(&version, sizeof version, 1, fp) == 1 && std::fread(&q, sizeof q, 1, fp) == 1 &&
+              std::fread(&cfg, sizeof cfg, 1, fp) == 1 && std::fread(&units, sizeof units, 1, fp) == 1;
+    if (!ok) {
+        std::fclose(fp);
+        return set_error(MCLBM_ERR_IO, std::string("reading ") + path + " failed (truncated or not a checkpoint)");
+    }
+    if (version != kFormatVersion) {
+        std::fclose(fp);
+        return set_error(MCLBM_ERR_IO, "checkpoint format version " + std::to_string(version) + " is not " +
+                                           std::to_string(kFormatVersion));
+    }
+    std::string why;
+    if (q != Q) {
+        std::fclose(fp);
+        return set_error(MCLBM_ERR_SHAPE, "checkpoint holds a D3Q" + std::to_string(q) + " lattice, the library is D3Q" +
+                                              std::to_string(Q));
+    }
+    if (!same_dynamics(cfg, units, ctx->cfg, ctx->units, &why)) {
+        std::fclose(fp);
+        return set_error(MCLBM_ERR_SHAPE, "checkpoint differs from the context in " + why);
+    }
     std::vector<double> params(ctx->params.size());
     const size_t bytes = ctx->elem_bytes * Q * (size_t)ctx->n * ctx->M;
     std::vector<char> host(bytes);
-    bool ok = std::fread(&magic, sizeof magic, 1, fp) == 1 && magic == kMagic &&
-              std::fread(&cfg, sizeof cfg, 1, fp) == 1 && std::fread(&steps, sizeof steps, 1, fp) == 1 &&
-              std::fread(&cur, sizeof cur, 1, fp) == 1 &&
-              std::fread(params.data(), sizeof(double), params.size(), fp) == params.size() &&
-              std::fread(host.data(), 1, bytes, fp) == bytes;
+    ok = std::fread(&steps, sizeof steps, 1, fp) == 1 && std::fread(&cur, sizeof cur, 1, fp) == 1 &&
+         std::fread(params.data(), sizeof(double), params.size(), fp) == params.size() &&
+         std::fread(host.data(), 1, bytes, fp) == bytes;
+    const bool at_end = ok && std::fgetc(fp) == EOF;
     std::fclose(fp);
-    if (!ok) return set_error(MCLBM_ERR_IO, std::string("reading ") + path + " failed (truncated or not a checkpoint)");
-    if (cfg.N != ctx->cfg.N || cfg.M != ctx->cfg.M || cfg.precision != ctx->cfg.precision ||
-        cfg.pattern != ctx->cfg.pattern)
-        return set_error(MCLBM_ERR_SHAPE, "checkpoint shape (N, M, precision, pattern) differs from the context");
+    if (!ok) return set_error(MCLBM_ERR_IO, std::string("reading ") + path + " failed (truncated)");
+    if (!at_end) return set_error(MCLBM_ERR_IO, std::string(path) + " has bytes after the lattice (not this layout)");
     if (cur != 0 && cur != 1) return set_error(MCLBM_ERR_IO, "corrupt checkpoint");
     ctx->cur = cur;
     ctx->steps = (int64_t)steps;

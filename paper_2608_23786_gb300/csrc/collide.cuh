@@ -486,9 +486,11 @@ __device__ __forceinline__ T exact_gamma_refine(const T (&am1)[Q], const T (&b)[
         else if (b[i] < T(0)) lo = fmax(lo, (T(1) + am1[i]) / b[i]);
     }
     if (!(lo < hi)) return g0;
-    // H is convex along the line, G = dH/dg (up to a positive factor) increases with g.  Near
-    // equilibrium the minimiser lies beyond the interval (reading of the constrained exact gamma),
-    // so the upper end is tested first; the lower end only when the root lies below the start.
+    // H is convex along the line.  G = sum w_i b_i ln r_i equals -dH/dg up to a positive factor
+    // (sum w_i b_i = 0: Dh carries no mass), so G decreases with g, and G(hi) >= 0 means that H
+    // still decreases at hi.  Near equilibrium the minimiser lies beyond the interval (reading of
+    // the constrained exact gamma), so the upper end is tested first; the lower end only when the
+    // root lies below the start (G < 0 there: H increases, and G(lo) <= 0 puts the minimum at lo).
     T G_hi = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) G_hi += weight<T>(i) * b[i] * log_ratio<T>(am1[i], hi, b[i]);

@@ -39,15 +39,15 @@ __global__ void k_set_pops(E* __restrict__ lat, Geom g, int pattern, int parity,
 }
 
 // Self-test of the bounded wait: one thread waits on an mbarrier that nothing arrives at,
-// gives up after `limit` polls and records MCLBM_ERR_TIMEOUT in the error word, exactly
-// as the staged stepper does when a wait runs out.  No copy is in flight.
-__global__ void k_wait_selftest(int* err, long limit)
+// gives up after `limit_ns` nanoseconds and records MCLBM_ERR_TIMEOUT in the error word,
+// exactly as the staged stepper does when a wait runs out.  No copy is in flight.
+__global__ void k_wait_selftest(int* err, uint64_t limit_ns)
 {
     __shared__ __align__(8) uint64_t bar;
     if (threadIdx.x != 0) return;
     mbar_init(smem_u32(&bar), 1);
     mbar_fence_init();
-    if (!mbar_wait_bounded(smem_u32(&bar), 0u, limit)) atomicExch(err, kTimeoutCode);
+    if (!mbar_wait_bounded(smem_u32(&bar), 0u, limit_ns)) atomicExch(err, kTimeoutCode);
 }
 
 
@@ -227,7 +227,7 @@ cudaError_t launch_step(mclbm_ctx* c) { return launch_step_with(c, c->launch, c-
 
 cudaError_t launch_wait_selftest(mclbm_ctx* c)
 {
-    k_wait_selftest<<<1, 32, 0, c->stream>>>((int*)(c->work + c->wl.flag) + 1, 1L << 12);
+    k_wait_selftest<<<1, 32, 0, c->stream>>>((int*)(c->work + c->wl.flag) + 1, 1000ull * 1000);  // 1 ms
     return cudaGetLastError();
 }
 

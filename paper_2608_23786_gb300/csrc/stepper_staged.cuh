@@ -18,9 +18,14 @@
 // block the memory system sees tens of kilobytes of outstanding reads per block
 // independent of the consumers' register use.
 //
-// Every wait is bounded (kSpinLimit polls with a suspend-time hint).  A wait that
-// gives up writes MCLBM_ERR_TIMEOUT into the error word and the block stops taking
-// tiles; before returning, the producer waits (again bounded) until every copy it
+// Every wait is bounded in time: it polls mbarrier.try_wait (each poll may suspend the
+// thread for at most kSuspendHintNs) until the barrier completes or kWaitLimitNs of
+// %globaltimer time have passed.  A wait that gives up writes MCLBM_ERR_TIMEOUT into the
+// error word and the block stops taking tiles.  Consumer waits also re-read the error word
+// every kErrPollEvery polls and leave as soon as it is set (by another block's timeout, or
+// left over from an earlier launch, in which case the producer issues nothing), so after a
+// timeout every later launch returns within about one poll interval instead of running out
+// the limit.  Before returning, the producer waits (again bounded) until every copy it
 // issued has landed, so no copy targets the shared memory of a finished block.
 #pragma once
 #include <cuda_fp16.h>
@@ -31,8 +36,10 @@ namespace mclbm {
 
 constexpr int kConsumerWarps = 8;
 constexpr int kStagedThreads = (kConsumerWarps + 1) * 32;
-constexpr long kSpinLimit = 1L << 26;  // polls (each may block for a system-defined time): seconds at most
-constexpr int kTimeoutCode = -6;       // MCLBM_ERR_TIMEOUT
+constexpr uint64_t kWaitLimitNs = 200ull * 1000 * 1000;  // 200 ms of %globaltimer time per wait
+constexpr uint32_t kSuspendHintNs = 2000;                 // longest suspension of one try_wait poll
+constexpr int kErrPollEvery = 256;                        // consumer polls between reads of the error word
+constexpr int kTimeoutCode = -6;                          // MCLBM_ERR_TIMEOUT
 
 template <class E>
 struct StagedArgs {
@@ -66,19 +73,34 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     asm volatile(
         "{\n"
         " .reg .pred p;\n"
-        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n"
         "}\n"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(kSuspendHintNs)
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long limit = kSpinLimit)
+__device__ __forceinline__ uint64_t global_ns()
 {
-    for (long it = 0; it < limit; ++it)
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for phase `parity` of barrier `bar` for at most limit_ns nanoseconds of %globaltimer
+// time.  With err != NULL the wait also gives up as soon as *err is nonzero (read every
+// kErrPollEvery polls).  Returns true when the phase completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns = kWaitLimitNs,
+                                                  const int* err = nullptr)
+{
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-    return false;
+        if ((it & (kErrPollEvery - 1)) == 0) {
+            if (err && *(volatile const int*)err != 0) return false;
+            if (global_ns() - t0 > limit_ns) return false;
+        }
+    }
 }
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
 {
@@ -215,8 +237,8 @@ __global__ void __launch_bounds__(kStagedThreads) k_step_staged(const StagedArgs
             const uint32_t ph = (uint32_t)((k / S) & 1);
             int ok = 1;
             if (lane == 0) {
-                ok = mbar_wait_bounded(smem_u32(&bars[S + s]), ph ^ 1u) ? 1 : 0;
-                if (!ok) atomicExch(a.err, kTimeoutCode);
+                ok = mbar_wait_bounded(smem_u32(&bars[S + s]), ph ^ 1u, kWaitLimitNs, a.err) ? 1 : 0;
+                if (!ok && *(volatile int*)a.err == 0) atomicExch(a.err, kTimeoutCode);
                 if (*(volatile int*)a.err != 0) ok = 0;
             }
             ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -239,8 +261,8 @@ __global__ void __launch_bounds__(kStagedThreads) k_step_staged(const StagedArgs
     for (int64_t t = blockIdx.x; t < total; t += gridDim.x, ++k) {
         const int s = (int)(k % S);
         const uint32_t ph = (uint32_t)((k / S) & 1);
-        if (!mbar_wait_bounded(smem_u32(&bars[s]), ph)) {
-            atomicExch(a.err, kTimeoutCode);
+        if (!mbar_wait_bounded(smem_u32(&bars[s]), ph, kWaitLimitNs, a.err)) {
+            if (*(volatile int*)a.err == 0) atomicExch(a.err, kTimeoutCode);
             break;
         }
         consume_tile<E, PATTERN, VEC>(a, tile_coord(a, t), stage0 + (int64_t)s * a.stage_elems, ctid);

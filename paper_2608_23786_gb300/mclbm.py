@@ -88,6 +88,7 @@ _SIGNATURES = {
     "mclbm_w1_2pt": (_c.c_int, [_vp, _c.c_int32, _vp, _c.c_int32, _c.c_int32, _c.c_int32, _vp, _c.c_size_t, _vp, _dp,
                                 _vp]),
     "mclbm_check_finite": (_c.c_int, [_ctx_p]),
+    "mclbm_alu_rate": (_c.c_int, [_c.c_int32, _c.c_int32, _vp, _vp, _dp, _dp]),
     "mclbm_w1_restricted_noalloc": (_c.c_int, [_vp, _c.c_int32, _vp, _c.c_int32, _c.c_int32, _vp, _dp, _dp]),
     "mclbm_set_launch": (_c.c_int, [_ctx_p, _c.c_int32, _c.c_int32, _c.c_int32]),
     "mclbm_get_launch": (_c.c_int, [_ctx_p, _i32p, _i32p, _i32p]),
@@ -182,6 +183,18 @@ def _darr(a):
     return a.ctypes.data_as(_dp)
 
 
+def _stream(stream):
+    """cudaStream_t handle for the C calls: an explicit handle (an int, 0 = the legacy default
+    stream) is passed as given; None takes torch's current stream on the current device, so
+    that work torch queued there (filling the inputs) is ordered before the call."""
+    if stream is not None:
+        return stream or None
+    import torch
+    if not torch.cuda.is_available():
+        return None
+    return torch.cuda.current_stream().cuda_stream or None
+
+
 # ---- same-named wrappers ------------------------------------------------------
 
 def mclbm_version(lattice=19):
@@ -215,10 +228,10 @@ def mclbm_required_bytes(cfg, lattice=19):
     return pop.value, work.value
 
 
-def mclbm_create(cfg, d_pop, pop_bytes, d_work, work_bytes, stream=0, lattice=19):
+def mclbm_create(cfg, d_pop, pop_bytes, d_work, work_bytes, stream=None, lattice=19):
     ctx = _ctx_p()
     _check(load(lattice=lattice).mclbm_create(ctypes.byref(cfg), d_pop, pop_bytes, d_work, work_bytes,
-                                              stream or None, ctypes.byref(ctx)))
+                                              _stream(stream), ctypes.byref(ctx)))
     _owner[ctx.value] = lattice
     return ctx
 
@@ -321,9 +334,9 @@ def mclbm_w1_work_bytes(MA, MB, G):
     return load().mclbm_w1_work_bytes(int(MA), int(MB), int(G))
 
 
-def mclbm_w1_restricted(d_a, MA, d_b, MB, G, d_work, work_bytes, stream=0, per_point=None):
+def mclbm_w1_restricted(d_a, MA, d_b, MB, G, d_work, work_bytes, stream=None, per_point=None):
     W = ctypes.c_double()
-    _check(load().mclbm_w1_restricted(d_a, int(MA), d_b, int(MB), int(G), d_work, work_bytes, stream or None,
+    _check(load().mclbm_w1_restricted(d_a, int(MA), d_b, int(MB), int(G), d_work, work_bytes, _stream(stream),
                                       ctypes.byref(W), _darr(per_point)))
     return W.value
 
@@ -332,10 +345,10 @@ def mclbm_w1_2pt_work_bytes(G, vector):
     return load().mclbm_w1_2pt_work_bytes(int(G), int(vector))
 
 
-def mclbm_w1_2pt(d_a, MA, d_b, MB, G, vector, d_work, work_bytes, stream=0, d_per_pair=None):
+def mclbm_w1_2pt(d_a, MA, d_b, MB, G, vector, d_work, work_bytes, stream=None, d_per_pair=None):
     """Two-point W1 (vector or component-wise) on restricted device fields; returns W."""
     W = ctypes.c_double()
-    _check(load().mclbm_w1_2pt(d_a, int(MA), d_b, int(MB), int(G), int(vector), d_work, work_bytes, stream or None,
+    _check(load().mclbm_w1_2pt(d_a, int(MA), d_b, int(MB), int(G), int(vector), d_work, work_bytes, _stream(stream),
                                ctypes.byref(W), d_per_pair or None))
     return W.value
 
@@ -344,21 +357,33 @@ def mclbm_sample_error_work_bytes(M):
     return load().mclbm_sample_error_work_bytes(int(M))
 
 
-def mclbm_sample_error(d_u, d_ref, M, G, d_work, work_bytes, stream=0):
+def mclbm_sample_error(d_u, d_ref, M, G, d_work, work_bytes, stream=None):
     """Eq. (sample_error) on restricted device fields; returns [4] (x, y, z, vector)."""
     import numpy as np
     out = np.zeros(4)
-    _check(load().mclbm_sample_error(d_u, d_ref, int(M), int(G), d_work, work_bytes, stream or None, _darr(out)))
+    _check(load().mclbm_sample_error(d_u, d_ref, int(M), int(G), d_work, work_bytes, _stream(stream), _darr(out)))
     return out
 
 
-def mclbm_w1_restricted_noalloc(d_a, MA, d_b, MB, G, stream=0, per_point=None):
+def mclbm_w1_restricted_noalloc(d_a, MA, d_b, MB, G, stream=None, per_point=None):
     """W_{1,1} on device restricted fields without any device allocation (scratch is a fixed
     array inside the library, G <= 4096 points)."""
     W = ctypes.c_double()
-    _check(load().mclbm_w1_restricted_noalloc(d_a, int(MA), d_b, int(MB), int(G), stream or None, ctypes.byref(W),
+    _check(load().mclbm_w1_restricted_noalloc(d_a, int(MA), d_b, int(MB), int(G), _stream(stream), ctypes.byref(W),
                                               _darr(per_point)))
     return W.value
+
+
+ALU_KINDS = {"fp64_fma": 0, "fp32_fma": 1, "fp32x2_fma": 2, "half2_fma": 3, "fp32_rcp": 4}
+
+
+def mclbm_alu_rate(kind, iters, d_sink, stream=None):
+    """(results per second, ms) of the arithmetic-throughput kernel of `kind` (a name of
+    ALU_KINDS or its number) on the current device."""
+    k = ALU_KINDS.get(kind, kind)
+    r, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().mclbm_alu_rate(int(k), int(iters), d_sink, _stream(stream), ctypes.byref(r), ctypes.byref(ms)))
+    return r.value, ms.value
 
 
 def mclbm_check_finite(ctx):

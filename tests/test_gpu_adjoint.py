@@ -149,6 +149,33 @@ def test_autograd_function():
     np.testing.assert_allclose(p.grad.numpy(), G * weights.numpy()[:, None], rtol=1e-13, atol=0)
 
 
+def test_autograd_forward_without_backward_runs_no_adjoint(monkeypatch):
+    """The forward pass is a plain run: it never enters mclbm_grad (the only caller of the
+    adjoint kernels), and no k_adjoint kernel appears among the kernels it launches.  J equals
+    the adjoint's J to the bit, and backward still gives the adjoint's gradient."""
+    N, M, Re, Ma, T = 16, 2, 200.0, 0.1, 6
+    X = gen.draw_params(13, M)
+    J_ref, G_ref = _gpu_grad(N, M, X, Re, Ma, T, 4, 0, "fp32")
+    calls = []
+    real_grad = mclbm.mclbm_grad
+    monkeypatch.setattr(mclbm, "mclbm_grad", lambda *a, **k: calls.append(1) or real_grad(*a, **k))
+    p = torch.tensor(X, requires_grad=True)
+    from torch.profiler import ProfilerActivity, profile
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        J = ensemble_objective(p, N=N, Ma=Ma, Re=Re, nsteps=T, precision="fp32", ckpt_every=4)
+        torch.cuda.synchronize()
+    assert calls == []
+    names = [e.name for e in prof.events() if e.device_type == torch.autograd.DeviceType.CUDA]
+    assert not any("k_adjoint" in n for n in names)
+    np.testing.assert_array_equal(J.detach().numpy(), J_ref)
+    J.sum().backward()
+    assert calls == [1]
+    np.testing.assert_array_equal(p.grad.numpy(), G_ref)
+    with torch.no_grad():
+        J2 = ensemble_objective(p, N=N, Ma=Ma, Re=Re, nsteps=T, precision="fp32", objective="enstrophy")
+    assert calls == [1] and np.all(np.isfinite(J2.numpy()))
+
+
 def test_full_size_adjoint_fp32_vs_fp64():
     """The adjoint workload: 64^3 x 16 samples, 500 steps, checkpoint every 50, E(T).  J of the
     FP32 run agrees with FP64 to 2e-5.  The FP32 gradient agrees with the FP64 gradient (which is

@@ -65,3 +65,43 @@ def test_checkpoint_resume_is_bitwise(tmp_path, pattern):
     with pytest.raises(mclbm.MclbmError) as e:
         mclbm.mclbm_load(b.ctx, os.path.join(tmp_path, "missing.mclbm"))
     assert e.value.status == "IO"
+
+
+def test_checkpoint_rejects_other_dynamics_and_trailing_bytes(tmp_path):
+    """A checkpoint restores only into a context with the same lattice, units and options: one
+    taken at another Reynolds number, with the exact-gamma option, or by the D3Q27 library is
+    rejected (SHAPE), and a file with bytes after the lattice is not taken for a checkpoint (IO)."""
+    a = Ensemble(16, 2, Re=300.0, Ma=0.1, precision="fp32").init().step(3)
+    path = os.path.join(tmp_path, "a.mclbm")
+    mclbm.mclbm_save(a.ctx, path)
+    for other in (Ensemble(16, 2, Re=600.0, Ma=0.1, precision="fp32").init(),
+                  Ensemble(16, 2, Re=300.0, Ma=0.05, precision="fp32").init(),
+                  Ensemble(16, 2, Re=300.0, Ma=0.1, precision="fp32", exact_gamma=True).init()):
+        with pytest.raises(mclbm.MclbmError) as e:
+            mclbm.mclbm_load(other.ctx, path)
+        assert e.value.status == "SHAPE"
+    padded = os.path.join(tmp_path, "padded.mclbm")
+    with open(path, "rb") as f, open(padded, "wb") as g:
+        g.write(f.read() + b"\0" * 8)
+    with pytest.raises(mclbm.MclbmError) as e:
+        mclbm.mclbm_load(a.ctx, padded)
+    assert e.value.status == "IO"
+    truncated = os.path.join(tmp_path, "truncated.mclbm")
+    with open(path, "rb") as f, open(truncated, "wb") as g:
+        g.write(f.read()[:-4])
+    with pytest.raises(mclbm.MclbmError) as e:
+        mclbm.mclbm_load(a.ctx, truncated)
+    assert e.value.status == "IO"
+    # the D3Q27 library's checkpoint (same N, M, units) does not load into the D3Q19 library
+    mclbm.load(lattice=27, build_if_missing=True)
+    b27 = Ensemble(16, 2, Re=300.0, Ma=0.1, precision="fp32", lattice=27).init().step(3)
+    p27 = os.path.join(tmp_path, "b27.mclbm")
+    mclbm.mclbm_save(b27.ctx, p27)
+    with pytest.raises(mclbm.MclbmError) as e:
+        mclbm.mclbm_load(a.ctx, p27)
+    assert e.value.status == "SHAPE"
+    with pytest.raises(mclbm.MclbmError) as e:
+        mclbm.mclbm_load(b27.ctx, path)
+    assert e.value.status == "SHAPE"
+    mclbm.mclbm_load(a.ctx, path)  # its own file still loads
+    assert a.steps_taken == 3

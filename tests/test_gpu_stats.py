@@ -110,6 +110,33 @@ def test_sf_axes(N, pmax):
     assert _rel(got, ref) <= 1e-10
 
 
+@pytest.mark.parametrize("N", [64, 128])
+def test_reductions_at_large_kernel_shapes(N):
+    """FP64 parity of the spectrum, trace S2 and axis S_p where the kernels take the shapes of
+    the large lattices: the S_p kernel stages 256 / (N/2) lines per block (8 at N = 64, 4 at
+    N = 128, against 16 at N = 32), and the shell kernel spreads 16 blocks over the rows of
+    disks of up to N/2 rows.  Same bounds as at small N: 1e-10 relative on bins holding at
+    least 1e-12 of the total."""
+    ens, u = _pair(N=N, M=2, steps=10)
+    _bins_close(ens.spectrum(), stats.energy_spectrum(u), 1e-10, 1e-12)
+    _bins_close(ens.sf_trace(), stats.structure_function_trace(u), 1e-10, 1e-12)
+    assert _rel(ens.sf_axes(6), stats.structure_function_axes(u, 6)) <= 1e-10
+
+
+def test_reductions_at_256():
+    """N = 256 (two lines per block in the S_p kernel, shells of up to 128 disk rows), one FP64
+    sample on the library's own velocity field (its moments are checked against the oracle at
+    the smaller sizes): spectrum and trace S2 on every bin, S_p at the lags 1, 37, 128."""
+    ens = Ensemble(256, 1, Re=1600.0, Ma=0.05, precision="fp64", seed=23).init().step(4)
+    u = _gpu_field(ens)
+    _bins_close(ens.spectrum(), stats.energy_spectrum(u), 1e-10, 1e-12)
+    _bins_close(ens.sf_trace(), stats.structure_function_trace(u), 1e-10, 1e-12)
+    lags = [1, 37, 128]
+    got = ens.sf_axes(6)[:, :, [r - 1 for r in lags]]
+    ref = stats.structure_function_axes(u, 6, lags=lags)[:, :, [r - 1 for r in lags]]
+    assert _rel(got, ref) <= 1e-10
+
+
 def _gpu_field(ens):
     """The library's own physical velocity of every sample, [M][3][N][N][N] (for FP32/FP16
     storage formed in FP32 from the stored deviations, like the stepper's moments)."""

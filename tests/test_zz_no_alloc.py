@@ -49,3 +49,21 @@ def test_noalloc_w1_rejects_more_points_than_its_scratch_holds():
     with pytest.raises(mclbm.MclbmError) as e:
         mclbm.mclbm_w1_restricted_noalloc(a.data_ptr(), 2, a.data_ptr(), 2, 4097)
     assert e.value.status == "SHAPE" and "4096" in str(e.value)
+
+
+def test_noalloc_w1_default_stream_is_torch_current_stream():
+    """Without an explicit stream the wrapper passes torch's current stream, so inputs filled on a
+    torch side stream (created non-blocking) are ordered before the call."""
+    MA, MB, G = 40, 24, 512
+    a0 = torch.as_tensor(gen.normal(72, (MA, G, 3)), device="cuda")
+    b0 = torch.as_tensor(gen.normal(172, (MB, G, 3)) + 0.1, device="cuda")
+    W_ref, _ = _with_work_buffer(a0, MA, b0, MB, G)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        a = torch.empty_like(a0)
+        b = torch.empty_like(b0)
+        a.copy_(a0)
+        b.copy_(b0)
+        W = mclbm.mclbm_w1_restricted_noalloc(a.data_ptr(), MA, b.data_ptr(), MB, G)
+    assert abs(W - W_ref) <= 1e-12 * abs(W_ref)
