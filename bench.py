@@ -262,6 +262,40 @@ def run_peaks(args):
                       "how": "8 blocks x 256 threads per SM, 8 independent chains per thread, CUDA events"}))
 
 
+def run_stats(args):
+    """The ensemble statistics on one ensemble (N = 128, M = 4 unless --N / --M; storage
+    --precision, FP32 by default) after 10 steps, each timed once with CUDA events after one
+    untimed call: E_m and the mean/variance fields in one pass, the shell spectrum, trace S_2,
+    S_p along the axes (p = 2..6), the restriction to 8^3 points, the one-point W1 and the
+    vector and component-wise two-point W1 against a second ensemble of the same shape."""
+    import torch
+    from paper_2608_23786_gb300 import Ensemble, mclbm
+    import ensemble_inputs as gen
+    mclbm.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    N, M, prec = args.N or 128, args.M or 4, args.precision or "fp32"
+    A = Ensemble(N, M, Re=1600.0, Ma=1.6 / N, precision=prec, seed=7, device=dev, stream=stream).init(
+        gen.draw_params(7, M)).step(10)
+    B = Ensemble(N, M, Re=1600.0, Ma=1.6 / N, precision=prec, seed=8, device=dev, stream=stream).init(
+        gen.draw_params(8, M)).step(10)
+    calls = {"energy_mean_var": lambda: A.energy_mean_var(), "spectrum": lambda: A.spectrum(),
+             "sf_trace": lambda: A.sf_trace(), "sf_axes_p2_6": lambda: A.sf_axes(6), "restrict_8": lambda: A.restrict(8),
+             "w1_1pt": lambda: A.w1(B), "w1_2pt_vector": lambda: A.w1_2pt(B, Q=8, vector=True),
+             "w1_2pt_componentwise": lambda: A.w1_2pt(B, Q=8, vector=False)}
+    out = {}
+    for name, fn in calls.items():
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        out[name] = (time.perf_counter() - t0) * 1e3
+    print(json.dumps({"metric": "statistics_ms", "unit": "ms per call (host wall clock around a synchronising call)",
+                      "config": {"workload": f"rtgv_{N}cube_x{M}_{prec}_stats", "N": N, "M": M}, "ms": out}))
+
+
 def run_reference(args, wl):
     """Reference arm: the FP64 oracle timed on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -605,7 +639,7 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="let the library's autotuner pick the launch shape")
     ap.add_argument("--workload", default="ensemble64",
                     choices=["ensemble64", "levels_fp32", "levels_fp16", "large", "adjoint", "oracle_report",
-                             "peaks"],
+                             "peaks", "stats"],
                     help="ensemble64 (default): 64^3 x 64 FP32; levels_*: 3-level batch; large: 512^3 x 4 FP16 AA; "
                          "adjoint: gradient of E(T), 64^3 x 16, 500 steps; oracle_report: the oracle on cfg1/cfg2 "
                          "(all cores and one core), its statistics per snapshot, and the GPU on cfg1")
@@ -626,6 +660,8 @@ def main():
         return run_oracle_report(args)
     if args.workload == "peaks":
         return run_peaks(args)
+    if args.workload == "stats":
+        return run_stats(args)
     wl = dict(WORKLOAD)
     if args.N or args.M:
         wl["N"] = args.N or wl["N"]
@@ -755,6 +791,7 @@ def main():
     if not args.no_e2e:
         plain = Ensemble(wl["N"], 1, Re=wl["Re"], Ma=wl["Ma"], precision="fp64", pattern="pull", device=dev,
                          stream=stream, lattice=wl["lattice"]).init(X[:1])
+        plain_launch = mclbm.mclbm_autotune(plain.ctx, 5)  # its fastest shape (restores the initial state)
         plain.step(5)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -807,7 +844,9 @@ def main():
             # the plain FP64 stepper's bandwidth against the copy bandwidth (its arithmetic
             # ceiling is the measured FP64 fma rate in alu_measured)
             plain_gbs = plain_glups * BYTES_PER_LU["fp64"] * wl["lattice"] // 19
-            plain_ratio = {"achieved_gbs": plain_gbs, "frac_of_hbm": plain_gbs / peaks["hbm_gbs"]}
+            plain_ratio = {"achieved_gbs": plain_gbs, "frac_of_hbm": plain_gbs / peaks["hbm_gbs"],
+                           "launch": dict(launch_desc(plain_launch), chosen_by="autotuner"),
+                           "l2": "80 MB of populations: L2-resident"}
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()

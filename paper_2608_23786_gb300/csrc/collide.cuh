@@ -26,7 +26,9 @@ namespace mclbm {
         else if ((sgn) < 0) acc -= (v); \
     } while (0)
 
-// Plain KBC on raw populations (in place).  Returns gamma.
+// Plain KBC on raw populations (in place).  Returns gamma.  Divisions are the costly FP64
+// operations here: 1/rho and the 1/f^eq_i of the inner products are each formed once (one
+// correctly rounded reciprocal each) and multiplied in, 20 divisions per node instead of 41.
 template <class T>
 __host__ __device__ __forceinline__ T kbc_raw(T (&f)[Q], T omega)
 {
@@ -38,7 +40,8 @@ __host__ __device__ __forceinline__ T kbc_raw(T (&f)[Q], T omega)
         MCLBM_SIGNED_ADD(jy, cy(i), f[i]);
         MCLBM_SIGNED_ADD(jz, cz(i), f[i]);
     }
-    const T ux = jx / rho, uy = jy / rho, uz = jz / rho;
+    const T rinv = T(1) / rho;
+    const T ux = jx * rinv, uy = jy * rinv, uz = jz * rinv;
     const T uu = ux * ux + uy * uy + uz * uz;
     T feq[Q], fneq[Q];
 #pragma unroll
@@ -78,8 +81,9 @@ __host__ __device__ __forceinline__ T kbc_raw(T (&f)[Q], T omega)
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const T dh = fneq[i] - ds[i];
-        sh += ds[i] * dh / feq[i];
-        hh += dh * dh / feq[i];
+        const T dhw = dh * (T(1) / feq[i]);
+        sh += ds[i] * dhw;
+        hh += dh * dhw;
     }
     const T gamma = (hh == T(0)) ? T(2) : T(2) / omega - (T(2) - T(2) / omega) * sh / hh;
     const T bo = T(0.5) * omega * gamma;
