@@ -296,6 +296,162 @@ def run_stats(args):
                       "config": {"workload": f"rtgv_{N}cube_x{M}_{prec}_stats", "N": N, "M": M}, "ms": out}))
 
 
+def run_w1_2pt(args):
+    """Two-point W1 (vector W_{1,2}^v and component-wise W_{1,2}) between two RTGV ensembles of
+    M samples (100 unless --M, the paper's smaller EOWC ensembles; N = 32 unless --N, 10 steps)
+    on the Q^3 restriction grid (Q = 8 unless --Q: 131328 point pairs), each timed once with
+    CUDA events on the stream after one untimed call."""
+    import torch
+    from paper_2608_23786_gb300 import Ensemble, mclbm
+    import ensemble_inputs as gen
+    mclbm.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    N, M, Q = args.N or 32, args.M or 100, args.Q
+    A = Ensemble(N, M, Re=1600.0, Ma=1.6 / N, precision="fp32", seed=11, device=dev, stream=stream).init(
+        gen.draw_params(11, M)).step(10)
+    B = Ensemble(N, M, Re=1600.0, Ma=1.6 / N, precision="fp32", seed=12, device=dev, stream=stream).init(
+        gen.draw_params(12, M)).step(10)
+    G = Q**3
+    out = {}
+    for vector, key in ((True, "vector"), (False, "componentwise")):
+        A.w1_2pt(B, Q=Q, vector=vector)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        W = A.w1_2pt(B, Q=Q, vector=vector)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        nprob = G * (G + 1) // 2 * (1 if vector else 3)
+        out[key] = {"W": W, "ms": ms, "problems": nprob, "us_per_problem": ms * 1e3 / nprob}
+    print(json.dumps({"metric": "w1_2pt_ms", "unit": "ms per call (CUDA events)",
+                      "config": {"workload": f"w1_2pt_rtgv_{N}cube_x{M}_Q{Q}", "N": N, "M": M, "Q": Q,
+                                 "pairs": G * (G + 1) // 2}, "w1_2pt": out}))
+
+
+def _observables(ens, pmax=6, fields=True):
+    """Per-sample statistics of one ensemble (host arrays)."""
+    out = {"ke": ens.energy(), "spectrum": ens.spectrum(), "s2": ens.sf_trace(), "sp": ens.sf_axes(pmax)}
+    if fields:
+        E, mean, var = ens.energy_mean_var()
+        out["mean"], out["var"] = mean.cpu().numpy(), var.cpu().numpy()
+        out["u"] = [ens.moments(m)[1].cpu().numpy() for m in range(ens.M)]
+    return out
+
+
+def _precision_errors(red, ref):
+    """Relative errors of one reduced-precision run's observables against the FP64 run's."""
+    def rel(a, b):
+        return float(np.max(np.abs(a - b) / np.abs(b)))
+    e = {"ke": rel(red["ke"], ref["ke"])}
+    S, So = red["spectrum"], ref["spectrum"]
+    tot = So.sum(axis=1, keepdims=True)
+    for floor in (1e-2, 1e-4, 1e-6):
+        big = So >= floor * tot
+        e[f"spectrum_bins_ge_{floor:g}_of_total"] = float(np.max(np.abs(S - So)[big] / So[big]))
+    e["spectrum_abs_over_total"] = float(np.max(np.abs(S - So) / tot))
+    e["s2"] = rel(red["s2"][:, 1:], ref["s2"][:, 1:])
+    e["sp"] = rel(red["sp"], ref["sp"])
+    if "u" in red:
+        e["u_l2"] = float(max(np.linalg.norm(a - b) / np.linalg.norm(b) for a, b in zip(red["u"], ref["u"])))
+        e["mean_l2"] = float(np.linalg.norm(red["mean"] - ref["mean"]) / np.linalg.norm(ref["mean"]))
+        e["var_l2"] = float(np.linalg.norm(red["var"] - ref["var"]) / np.linalg.norm(ref["var"]))
+    return e
+
+
+def run_precision(args):
+    """FP32 and FP16 shifted storage against the plain FP64 GPU stepper (whose parity with the
+    oracle the tests establish), per observable, after a fixed horizon:
+      - 128^3 x 32 RTGV samples at Re 1600, Ma 0.0125, 500 steps: FP32 and FP16, pull and AA;
+        kinetic energy, velocity field (relative L2), E(kappa) (on bins holding >= 1e-2, 1e-4,
+        1e-6 of the total, and the largest absolute error over the total), trace S_2, S_p along
+        the axes (p = 2..6), mean and variance fields, and the one-point W1 between the reduced-
+        precision law and the FP64 law of the same samples as a fraction of the W1 between two
+        independent FP64 ensembles (the sampling distance);
+      - the three-level batch (64^3 x 64, 128^3 x 32, 256^3 x 8 at Re 400 / 1600 / 3200, 1 : 4 : 16
+        sub-steps), FP16 AA and FP32 pull batches against per-level FP64 runs after 10 macro
+        steps: per level the same statistics (S_p for p = 2, 3), and the one-point W1 between
+        consecutive levels."""
+    import torch
+    from paper_2608_23786_gb300 import Ensemble, mclbm
+    import ensemble_inputs as gen
+    mclbm.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    res = {"metric": "precision_errors", "unit": "relative error against the FP64 GPU run"}
+    # ---- 128^3 x 32
+    N, M, Re, Ma, T = 128, args.M or 32, 1600.0, 0.0125, args.T
+    XA, XB = gen.draw_params(21, M), gen.draw_params(22, M)
+
+    def run(prec, pat, X, seed):
+        return Ensemble(N, M, Re=Re, Ma=Ma, precision=prec, pattern=pat, seed=seed, device=dev,
+                        stream=stream).init(X).step(T)
+
+    t0 = time.perf_counter()
+    A64 = run("fp64", "pull", XA, 21)
+    ref = _observables(A64)
+    rA = A64.restrict(8).cpu().numpy()
+    del A64
+    B64 = run("fp64", "pull", XB, 22)
+    rB = B64.restrict(8).cpu().numpy()
+    del B64
+    torch.cuda.empty_cache()
+    from paper_2608_23786_gb300 import mclbm as _m
+
+    def w1_restricted(a, b):
+        da, db = torch.as_tensor(a, device=dev), torch.as_tensor(b, device=dev)
+        nb = _m.mclbm_w1_work_bytes(a.shape[0], b.shape[0], a.shape[1])
+        work = torch.empty(nb, dtype=torch.uint8, device=dev)
+        return _m.mclbm_w1_restricted(da.data_ptr(), a.shape[0], db.data_ptr(), b.shape[0], a.shape[1],
+                                      work.data_ptr(), nb, stream.cuda_stream)
+
+    w_sampling = w1_restricted(rA, rB)
+    table = {}
+    for prec, pat in (("fp32", "pull"), ("fp32", "aa"), ("fp16", "pull"), ("fp16", "aa")):
+        e = run(prec, pat, XA, 21)
+        err = _precision_errors(_observables(e), ref)
+        err["w1_to_fp64_law_over_sampling_w1"] = w1_restricted(e.restrict(8).cpu().numpy(), rA) / w_sampling
+        table[f"{prec}_{pat}"] = err
+        del e
+        torch.cuda.empty_cache()
+    res["rtgv_128cube_x%d_%dsteps" % (M, T)] = {"errors": table, "sampling_w1": w_sampling,
+                                                 "seconds": time.perf_counter() - t0}
+    # ---- three-level batch
+    t0 = time.perf_counter()
+    MACRO = 10
+    refs, rrefs = [], []
+    for (Nl, Ml, Rel, Mal, sub, seed) in LEVELS:
+        e = Ensemble(Nl, Ml, Re=Rel, Ma=Mal, precision="fp64", pattern="pull", seed=seed, device=dev,
+                     stream=stream).init(gen.draw_params(seed, Ml)).step(sub * MACRO)
+        refs.append(_observables(e, pmax=3, fields=False))
+        rrefs.append(e.restrict(8).cpu().numpy())
+        del e
+        torch.cuda.empty_cache()
+    w_ref = [w1_restricted(rrefs[k], rrefs[k + 1]) for k in range(2)]
+    batch = {}
+    for prec, pat in (("fp32", "pull"), ("fp16", "aa")):
+        levels = [Ensemble(Nl, Ml, Re=Rel, Ma=Mal, precision=prec, pattern=pat, seed=seed, device=dev,
+                           stream=stream).init(gen.draw_params(seed, Ml)) for Nl, Ml, Rel, Mal, _, seed in LEVELS]
+        b = mclbm.mclbm_batch_create([x.ctx for x in levels], [lv[4] for lv in LEVELS])
+        mclbm.mclbm_batch_step(b, MACRO)
+        mclbm.mclbm_batch_destroy(b)
+        per = {}
+        for k, x in enumerate(levels):
+            per[f"{LEVELS[k][0]}cube_x{LEVELS[k][1]}"] = _precision_errors(_observables(x, pmax=3, fields=False),
+                                                                           refs[k])
+        rr = [x.restrict(8).cpu().numpy() for x in levels]
+        per["w1_consecutive_levels"] = [abs(w1_restricted(rr[k], rr[k + 1]) - w_ref[k]) / w_ref[k] for k in range(2)]
+        batch[f"{prec}_{pat}"] = per
+        del levels
+        torch.cuda.empty_cache()
+    res[f"levels_64x64_128x32_256x8_{MACRO}macro"] = {"errors": batch, "w1_consecutive_levels_fp64": w_ref,
+                                                     "seconds": time.perf_counter() - t0}
+    print(json.dumps(res))
+
+
 def run_reference(args, wl):
     """Reference arm: the FP64 oracle timed on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -639,11 +795,12 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="let the library's autotuner pick the launch shape")
     ap.add_argument("--workload", default="ensemble64",
                     choices=["ensemble64", "levels_fp32", "levels_fp16", "large", "adjoint", "oracle_report",
-                             "peaks", "stats"],
+                             "peaks", "stats", "w1_2pt", "precision"],
                     help="ensemble64 (default): 64^3 x 64 FP32; levels_*: 3-level batch; large: 512^3 x 4 FP16 AA; "
                          "adjoint: gradient of E(T), 64^3 x 16, 500 steps; oracle_report: the oracle on cfg1/cfg2 "
                          "(all cores and one core), its statistics per snapshot, and the GPU on cfg1")
     ap.add_argument("--T", type=int, default=500, help="adjoint horizon (steps) of --workload adjoint")
+    ap.add_argument("--Q", type=int, default=8, help="restriction grid Q^3 of --workload w1_2pt")
     ap.add_argument("--oracle-child", default=None, choices=["all", "one"], help=argparse.SUPPRESS)
     ap.add_argument("--exact-gamma", action="store_true",
                     help="ensemble workload with the exact entropic gamma (Newton per node) instead of the closed form")
@@ -662,6 +819,10 @@ def main():
         return run_peaks(args)
     if args.workload == "stats":
         return run_stats(args)
+    if args.workload == "w1_2pt":
+        return run_w1_2pt(args)
+    if args.workload == "precision":
+        return run_precision(args)
     wl = dict(WORKLOAD)
     if args.N or args.M:
         wl["N"] = args.N or wl["N"]

@@ -245,16 +245,20 @@ MCLBM_API int mclbm_w1_restricted(const double* d_a, int32_t MA, const double* d
  * (u(x_i), u(x_j)) in R^6; vector = 0: W_{1,2} of Algorithm "WassersteinDistance2", the W1
  * of (u_c(x_i), u_c(x_j)) in R^2 for each component c, summed over c.  Euclidean ground
  * metric, every point pair i <= j, off-diagonal pairs counted twice, divided by G^2.  Each
- * pair is an exact transport problem between uniform empirical measures, solved as an
- * assignment of L = lcm(MA, MB) <= 64 atoms per side (atoms repeated L/MA, L/MB times) with
- * fixed-point integer costs from FP32 atoms taken relative to their mean; the matched costs
- * are summed in FP64 (each pair's value is within about 1e-7 of the spread of its atoms of
- * the exact optimum).  W: host scalar.  d_per_pair: device
- * FP64 [G (G + 1) / 2][vector ? 1 : 3] in row-major upper-triangle order (pair (i, j) at
- * i G - i (i - 1) / 2 + j - i), or NULL.  d_work: >= mclbm_w1_2pt_work_bytes(G, vector)
- * bytes.  Runs on cuda_stream and synchronises it.  Errors: INVALID_ARG, SHAPE (lcm > 64),
- * OOM (work buffer too small). */
-MCLBM_API size_t mclbm_w1_2pt_work_bytes(int32_t G, int32_t vector);
+ * pair is an exact transport problem between uniform empirical measures (1 <= MA, MB <= 1024):
+ * for L = lcm(MA, MB) <= 64 an assignment of L atoms per side (atoms repeated L/MA, L/MB
+ * times), one warp per problem; otherwise the transportation problem with integer supply MB/g
+ * per atom of A and demand MA/g per atom of B (g = gcd(MA, MB)) by successive shortest paths,
+ * one block per problem.  Costs are fixed-point integers from FP32 atoms taken relative to
+ * their mean; the plan is optimal for those costs and its cost is summed in FP64 (each pair's
+ * value is within about 1e-7 of the spread of its atoms of the exact optimum).  W: host
+ * scalar.  d_per_pair: device FP64 [G (G + 1) / 2][vector ? 1 : 3] in row-major upper-triangle
+ * order (pair (i, j) at i G - i (i - 1) / 2 + j - i), or NULL.  d_work: >=
+ * mclbm_w1_2pt_work_bytes(MA, MB, G, vector) bytes, 256-byte aligned (it includes, for unequal
+ * MA and MB with lcm > 64, one 2 MA MB-byte flow matrix for each of 256 problems in flight).
+ * Runs on cuda_stream and synchronises it.  Errors: INVALID_ARG, SHAPE (MA or MB > 1024),
+ * OOM (work buffer too small), NONFINITE (a search failed, e.g. on non-finite atoms). */
+MCLBM_API size_t mclbm_w1_2pt_work_bytes(int32_t MA, int32_t MB, int32_t G, int32_t vector);
 MCLBM_API int mclbm_w1_2pt(const double* d_a, int32_t MA, const double* d_b, int32_t MB, int32_t G, int32_t vector,
                            void* d_work, size_t work_bytes, void* cuda_stream, double* W, double* d_per_pair);
 

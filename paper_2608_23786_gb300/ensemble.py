@@ -183,7 +183,7 @@ class Ensemble:
         this ensemble and `other` on the common Q^3 restriction grid (mclbm_w1_2pt)."""
         ua, ub = self.restrict(Q), other.restrict(Q)
         G = Q**3
-        nb = _m.mclbm_w1_2pt_work_bytes(G, int(vector))
+        nb = _m.mclbm_w1_2pt_work_bytes(self.M, other.M, G, int(vector))
         work = torch.empty(nb, dtype=torch.uint8, device=self.device)
         self._enter(work, ua, ub)
         W = _m.mclbm_w1_2pt(ua.data_ptr(), self.M, ub.data_ptr(), other.M, G, int(vector), work.data_ptr(), nb,

@@ -81,7 +81,7 @@ _SIGNATURES = {
     "mclbm_w1_1pt": (_c.c_int, [_ctx_p, _ctx_p, _c.c_int32, _dp, _dp]),
     "mclbm_w1_work_bytes": (_c.c_size_t, [_c.c_int32, _c.c_int32, _c.c_int32]),
     "mclbm_w1_restricted": (_c.c_int, [_vp, _c.c_int32, _vp, _c.c_int32, _c.c_int32, _vp, _c.c_size_t, _vp, _dp, _dp]),
-    "mclbm_w1_2pt_work_bytes": (_c.c_size_t, [_c.c_int32, _c.c_int32]),
+    "mclbm_w1_2pt_work_bytes": (_c.c_size_t, [_c.c_int32, _c.c_int32, _c.c_int32, _c.c_int32]),
     "mclbm_sample_error_work_bytes": (_c.c_size_t, [_c.c_int32]),
     "mclbm_leray_params": (_c.c_int, [_dp, _c.c_int32, _c.c_int32, _dp]),
     "mclbm_sample_error": (_c.c_int, [_vp, _vp, _c.c_int32, _c.c_int32, _vp, _c.c_size_t, _vp, _dp]),
@@ -341,8 +341,8 @@ def mclbm_w1_restricted(d_a, MA, d_b, MB, G, d_work, work_bytes, stream=None, pe
     return W.value
 
 
-def mclbm_w1_2pt_work_bytes(G, vector):
-    return load().mclbm_w1_2pt_work_bytes(int(G), int(vector))
+def mclbm_w1_2pt_work_bytes(MA, MB, G, vector):
+    return load().mclbm_w1_2pt_work_bytes(int(MA), int(MB), int(G), int(vector))
 
 
 def mclbm_w1_2pt(d_a, MA, d_b, MB, G, vector, d_work, work_bytes, stream=None, d_per_pair=None):

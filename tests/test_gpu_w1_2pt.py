@@ -26,7 +26,7 @@ def _gpu(ua, ub, vector):
     G = ua.shape[1]
     da = torch.as_tensor(ua, device="cuda").contiguous()
     db = torch.as_tensor(ub, device="cuda").contiguous()
-    nb = mclbm.mclbm_w1_2pt_work_bytes(G, vector)
+    nb = mclbm.mclbm_w1_2pt_work_bytes(ua.shape[0], ub.shape[0], G, vector)
     work = torch.empty(nb, dtype=torch.uint8, device="cuda")
     per = torch.empty(G * (G + 1) // 2 * (1 if vector else 3), dtype=torch.float64, device="cuda")
     W = mclbm.mclbm_w1_2pt(da.data_ptr(), ua.shape[0], db.data_ptr(), ub.shape[0], G, vector, work.data_ptr(), nb,
@@ -96,13 +96,70 @@ def test_identical_laws_and_shape_errors():
     for vector in (1, 0):
         W, per = _gpu(ua, ua, vector)
         assert W == 0.0 and np.all(per == 0.0)
-    da = torch.zeros((64, 8, 3), dtype=torch.float64, device="cuda")
-    db = torch.zeros((48, 8, 3), dtype=torch.float64, device="cuda")
-    nb = mclbm.mclbm_w1_2pt_work_bytes(8, 1)
+    da = torch.zeros((1025, 8, 3), dtype=torch.float64, device="cuda")
+    nb = mclbm.mclbm_w1_2pt_work_bytes(64, 64, 8, 1)
     work = torch.empty(nb, dtype=torch.uint8, device="cuda")
-    with pytest.raises(mclbm.MclbmError) as e:  # lcm(64, 48) = 192 > 64
-        mclbm.mclbm_w1_2pt(da.data_ptr(), 64, db.data_ptr(), 48, 8, 1, work.data_ptr(), nb)
+    assert mclbm.mclbm_w1_2pt_work_bytes(1025, 64, 8, 1) == 0
+    with pytest.raises(mclbm.MclbmError) as e:  # more than 1024 samples on one side
+        mclbm.mclbm_w1_2pt(da.data_ptr(), 1025, da.data_ptr(), 64, 8, 1, work.data_ptr(), nb)
     assert e.value.status == "SHAPE"
     with pytest.raises(mclbm.MclbmError) as e:
         mclbm.mclbm_w1_2pt(da.data_ptr(), 64, da.data_ptr(), 64, 8, 1, work.data_ptr(), nb - 8)
     assert e.value.status == "OOM"
+
+
+@pytest.mark.parametrize("vector", [1, 0])
+def test_paper_sample_count_100_every_pair(vector):
+    """M = 100 on both sides (the paper's smaller EOWC ensembles; one block per transport
+    problem), G = 27 points: every one of the 378 pairs against the oracle's assignment, and the
+    aggregate; a second call gives the same bits (fixed tie-breaking and reduction order)."""
+    M, G = 100, 27
+    ua = gen.normal(300, (M, G, 3), 0.3)
+    ub = gen.normal(301, (M, G, 3), 0.3) + 0.02
+    W, per = _gpu(ua, ub, vector)
+    Wref, Dref = stats.w1_two_point(ua, ub, vector=bool(vector), per_pair=True)
+    _check(W, per, Wref, Dref)
+    W2, per2 = _gpu(ua, ub, vector)
+    assert W2 == W and np.array_equal(per2, per)
+
+
+@pytest.mark.parametrize("vector", [1, 0])
+def test_paper_sample_count_1000_sampled_pairs(vector):
+    """M = 1000 on both sides (the paper's larger EOWC ensembles): G = 2 points, all three pairs
+    against the oracle's assignment."""
+    M, G = 1000, 2
+    ua = gen.normal(310, (M, G, 3), 0.3)
+    ub = gen.normal(311, (M, G, 3), 0.3) + 0.01
+    W, per = _gpu(ua, ub, vector)
+    Wref, Dref = stats.w1_two_point(ua, ub, vector=bool(vector), per_pair=True)
+    _check(W, per, Wref, Dref)
+
+
+@pytest.mark.parametrize("MA,MB,G", [(120, 90, 4), (250, 240, 2), (100, 50, 4), (64, 48, 4), (7, 100, 4)])
+@pytest.mark.parametrize("vector", [1, 0])
+def test_unequal_sample_counts_transportation(MA, MB, G, vector):
+    """Unequal sample counts beyond the replicated assignment (lcm > 64): the transportation
+    problem with supply MB/g and demand MA/g per atom (g = gcd), flows in the work buffer,
+    against the oracle's transport linear program on every pair."""
+    ua = gen.normal(320 + MA, (MA, G, 3), 0.3)
+    ub = gen.normal(321 + MB, (MB, G, 3), 0.3) + 0.03
+    W, per = _gpu(ua, ub, vector)
+    Wref, Dref = stats.w1_two_point(ua, ub, vector=bool(vector), per_pair=True)
+    _check(W, per, Wref, Dref)
+
+
+def test_coprime_sample_counts_1000_999():
+    """1000 against 999 samples (coprime: lcm 999000, no replicated assignment exists): one point
+    pair of the vector problem against the oracle's transport linear program."""
+    ua = gen.normal(330, (1000, 1, 3), 0.3)
+    ub = gen.normal(331, (999, 1, 3), 0.3) + 0.01
+    W, per = _gpu(ua, ub, 1)
+    Wref, Dref = stats.w1_two_point(ua, ub, vector=True, per_pair=True)
+    _check(W, per, Wref, Dref)
+
+
+def test_identical_laws_at_100_samples():
+    ua = gen.normal(340, (100, 8, 3), 0.3)
+    for vector in (1, 0):
+        W, per = _gpu(ua, ua, vector)
+        assert W == 0.0 and np.all(per == 0.0)
