@@ -45,8 +45,11 @@ def _errors(precision, pattern, oracle_fields):
     Eo = stats.kinetic_energy(ua)
     err["ke"] = np.max(np.abs(a.energy() - Eo) / Eo)
     Sp, So = a.spectrum(), stats.energy_spectrum(ua)
-    big = So >= 1e-6 * So.sum(axis=1, keepdims=True)
-    err["spectrum"] = np.max(np.abs(Sp - So)[big] / So[big])
+    tot = So.sum(axis=1, keepdims=True)
+    for key, floor in (("spectrum", 1e-6), ("spectrum_1e-4", 1e-4), ("spectrum_1e-2", 1e-2)):
+        big = So >= floor * tot
+        err[key] = np.max(np.abs(Sp - So)[big] / So[big])
+    err["spectrum_abs"] = np.max(np.abs(Sp - So) / tot)
     T, To = a.sf_trace(), stats.structure_function_trace(ua)
     err["s2"] = np.max(np.abs(T - To)[:, 1:] / To[:, 1:])
     P, Po = a.sf_axes(6), stats.structure_function_axes(ua, 6)
@@ -66,9 +69,14 @@ def test_fp32_statistics_against_the_fp64_oracle_run(pattern, oracle_fields):
 
 
 def test_fp16_statistics_against_the_fp64_oracle_run(oracle_fields):
-    """Measured: KE 2.5e-5, E(kappa) 3.6e-2 (on its smallest retained bins), S2 2.6e-5, S_p 1.5e-4,
-    W1 4.6e-3."""
+    """Measured: KE 2.5e-5; E(kappa) 2.5e-5 on bins holding >= 1e-2 of the energy, 1.9e-4 on bins
+    >= 1e-4, and at most 2.5e-5 of the total energy on any bin; S2 2.6e-5, S_p 1.5e-4, W1 4.6e-3.
+    On the bins near 1e-6 of the total the relative error reaches 3.6e-2: there the FP16
+    rounding of the stored deviations (2^-11 of |h|, about 1e-5 of the velocity scale, spread
+    over all wavenumbers) is comparable to the bin itself, so those bins are held to the
+    absolute bound instead."""
     err = _errors("fp16", "aa", oracle_fields)
-    bounds = {"ke": 1e-4, "spectrum": 1e-1, "s2": 1e-4, "sp": 1e-3, "w1": 2e-2}
+    bounds = {"ke": 1e-4, "spectrum_1e-2": 1e-4, "spectrum_1e-4": 1e-3, "spectrum_abs": 1e-4, "s2": 1e-4,
+              "sp": 1e-3, "w1": 2e-2}
     for k, tol in bounds.items():
         assert err[k] <= tol, (k, err[k])
