@@ -294,7 +294,7 @@ MCLBM_API int mclbm_leray_params(const double* X, int32_t M, int32_t transpose, 
  * kind 3: kind 2 with the FP32 collision of two nodes at a time in the packed FP32
  * instructions of sm_100 and later (FP32 and FP16 storage, even vec).
  * kinds 4 and 5: kind 3 with the runs ahead copied by cp.async into a shared-memory ring, one
- * or two runs deep (FP32 and FP16 storage, block 128; not in the D3Q27 library).
+ * or two runs deep (FP32 and FP16 storage, block 128).
  * kind 6: the direct kernel with the exact entropic gamma (contexts with
  * MCLBM_OPT_EXACT_GAMMA, and only they; vec = the first of the type's list, block 128).
  * Results do not depend on the shape (same arithmetic per node, every operation

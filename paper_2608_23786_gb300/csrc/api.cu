@@ -157,11 +157,12 @@ LaunchConfig default_launch(int precision, int pattern, int options)
 {
     if (options & MCLBM_OPT_EXACT_GAMMA) return LaunchConfig{exact_vec(precision), 128, 6};
 #ifdef MCLBM_D3Q27
-    // D3Q27 (measured): FP32 prefetching kernel in blocks of 256; FP16 pull the direct kernel,
-    // AA even steps the packed prefetching one in blocks of 256
+    // D3Q27 (measured at 128^3 x 32): FP32 prefetching kernel in blocks of 256; FP16 pull the
+    // shared-memory ring (76% against 67% for the direct kernel), AA even steps the packed
+    // prefetching one in blocks of 256
     if (precision == MCLBM_FP64) return LaunchConfig{1, 128, 0};
     if (precision == MCLBM_FP32) return LaunchConfig{2, 256, 2};
-    return pattern == MCLBM_PULL ? LaunchConfig{4, 128, 0} : LaunchConfig{4, 256, 3};
+    return pattern == MCLBM_PULL ? LaunchConfig{4, 128, 4} : LaunchConfig{4, 256, 3};
 #else
     if (precision == MCLBM_FP64) return LaunchConfig{2, 128, 0};
     if (precision == MCLBM_FP32) return LaunchConfig{2, 128, 3};
@@ -171,14 +172,14 @@ LaunchConfig default_launch(int precision, int pattern, int options)
 
 // AA odd steps read and write shifted rows and favour other shapes (measured per parity at
 // 128^3 x 32 and 64^3 x 64): D3Q19 FP32 the two-stage cp.async ring with 4 nodes per thread,
-// FP16 the packed prefetching kernel with 4; D3Q27 FP32 the packed prefetching kernel, FP16 the
-// one-node prefetching kernel, both in blocks of 128.
+// FP16 the packed prefetching kernel with 4; D3Q27 FP32 the packed prefetching kernel in blocks
+// of 256, FP16 the one-stage cp.async ring (63% against 52% for the one-node prefetching kernel).
 LaunchConfig default_launch_odd(int precision, int pattern, int options)
 {
     const LaunchConfig even = default_launch(precision, pattern, options);
     if (pattern != MCLBM_AA || even.kind == 6 || precision == MCLBM_FP64) return even;
 #ifdef MCLBM_D3Q27
-    return precision == MCLBM_FP32 ? LaunchConfig{2, 128, 3} : LaunchConfig{4, 128, 2};
+    return precision == MCLBM_FP32 ? LaunchConfig{2, 256, 3} : LaunchConfig{4, 128, 4};
 #else
     return precision == MCLBM_FP32 ? LaunchConfig{4, 128, 5} : LaunchConfig{4, 128, 3};
 #endif

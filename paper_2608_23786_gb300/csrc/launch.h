@@ -22,7 +22,7 @@ struct LaunchConfig {
 
 // Variants compiled per element type (nodes per thread; VEC * sizeof(E) <= 16 bytes).  The
 // D3Q27 build compiles a reduced set (its collision is heavier to compile): one VEC per
-// type and no shared-memory ring kinds.
+// type.
 #ifdef MCLBM_D3Q27
 #define MCLBM_VECS_F64 1
 #define MCLBM_VECS_F32 2
@@ -30,7 +30,7 @@ struct LaunchConfig {
 constexpr int kVecF64[] = {1};
 constexpr int kVecF32[] = {2};
 constexpr int kVecF16[] = {4};
-constexpr bool kAsyncKinds = false;  // kinds 4 and 5
+constexpr bool kAsyncKinds = true;  // kinds 4 and 5
 #else
 #define MCLBM_VECS_F64 1, 2
 #define MCLBM_VECS_F32 1, 2, 4

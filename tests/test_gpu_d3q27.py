@@ -70,6 +70,7 @@ def test_every_launch_shape_and_aa_equal_pull(precision):
     shapes = [(k, v, b) for k in (0, 2) for v in vecs for b in (128, 256)]
     if precision != "fp64":
         shapes += [(3, v, b) for v in vecs for b in (128, 256)]
+        shapes += [(k, v, 128) for k in (4, 5) for v in vecs]  # shared-memory prefetch rings
     shapes += [(1, 1, 0)]
     ref = None
     for pattern in ("pull", "aa"):
