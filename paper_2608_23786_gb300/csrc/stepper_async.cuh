@@ -63,7 +63,8 @@ __device__ __forceinline__ const void* edge_word(const E* row, int e)
         return row + e;
 }
 
-template <class E, int VEC, int BLOCK, int STAGES, int FIX, int I = 0>
+// WRAP: every row lies within one warp and its lanes rotate (row_lane), so no edge word is copied.
+template <class E, int VEC, int BLOCK, int STAGES, int FIX, bool WRAP = false, int I = 0>
 __device__ __forceinline__ void async_issue_all(const E* base, const Geom& g, const RunLoc& p, int lane,
                                                 const AsyncRing<E, VEC, BLOCK, STAGES>& ring, int stage)
 {
@@ -75,14 +76,15 @@ __device__ __forceinline__ void async_issue_all(const E* base, const Geom& g, co
         const int rz = shift ? g.wrap(p.z - Dir<I>::z) : p.z;
         const E* row = base + (int64_t)slot * g.n + g.node(0, ry, rz);
         cp_async<AsyncRing<E, VEC, BLOCK, STAGES>::kVB>(ring.vec_slot(stage, I), row + p.x0);
-        if constexpr (Dir<I>::x > 0) {
+        if constexpr (WRAP) {
+        } else if constexpr (Dir<I>::x > 0) {
             if (shift && (lane == 0 || p.x0 == 0))
                 cp_async<4>(ring.edge_slot(stage, I), edge_word(row, (p.x0 - 1) & (g.N - 1)));
         } else if constexpr (Dir<I>::x < 0) {
             if (shift && (lane == 31 || p.x0 + VEC == g.N))
                 cp_async<4>(ring.edge_slot(stage, I), edge_word(row, (p.x0 + VEC) & (g.N - 1)));
         }
-        async_issue_all<E, VEC, BLOCK, STAGES, FIX, I + 1>(base, g, p, lane, ring, stage);
+        async_issue_all<E, VEC, BLOCK, STAGES, FIX, WRAP, I + 1>(base, g, p, lane, ring, stage);
     }
 }
 
@@ -109,27 +111,27 @@ __device__ __forceinline__ RawRun<E, VEC> ring_read(const unsigned char* smem, i
     return r;
 }
 
-template <class E, int VEC, int BLOCK, int STAGES, int FIX, int I = 0>
+template <class E, int VEC, int BLOCK, int STAGES, int FIX, bool WRAP = false, int I = 0>
 __device__ __forceinline__ void async_finish_all(const unsigned char* smem, int stage, int tid, const Geom& g,
                                                  const RunLoc& p, int lane, typename Storage<E>::compute (&v)[Q][VEC])
 {
     if constexpr (I < Q) {
         const int mode = FIX >= 0 ? FIX : p.mode;
         if (mode != 1) {
-            const RawRun<E, VEC> r = ring_read<E, VEC, BLOCK, STAGES, Dir<I>::x>(smem, stage, I, tid);
-            finish_row<E, VEC, Dir<I>::x>(r, p.x0, g.N, lane, v[I]);
+            const RawRun<E, VEC> r = ring_read<E, VEC, BLOCK, STAGES, WRAP ? 0 : Dir<I>::x>(smem, stage, I, tid);
+            finish_row<E, VEC, Dir<I>::x, WRAP>(r, p.x0, g.N, lane, v[I]);
         } else {
             const RawRun<E, VEC> r = ring_read<E, VEC, BLOCK, STAGES, 0>(smem, stage, I, tid);
             finish_row<E, VEC, 0>(r, p.x0, g.N, lane, v[I]);
         }
-        async_finish_all<E, VEC, BLOCK, STAGES, FIX, I + 1>(smem, stage, tid, g, p, lane, v);
+        async_finish_all<E, VEC, BLOCK, STAGES, FIX, WRAP, I + 1>(smem, stage, tid, g, p, lane, v);
     }
 }
 
 // FIX as in k_step_prefetch.  STAGES - 1 runs ahead are in flight; a thread's k-th run is
 // read from stage k mod STAGES.  Every thread commits one copy group per run slot (empty
 // past its last run), so wait_group STAGES - 1 always means "the current run has landed".
-template <class E, int VEC, int PATTERN, int BLOCK, int FIX, int STAGES>
+template <class E, int VEC, int PATTERN, int BLOCK, int FIX, int STAGES, bool WRAP = false>
 __global__ void __launch_bounds__(BLOCK) k_step_async(const BatchArgs<E> args)
 {
     static_assert(Storage<E>::shifted, "the shared-memory prefetch variant serves the FP32 and FP16 storage");
@@ -153,8 +155,8 @@ __global__ void __launch_bounds__(BLOCK) k_step_async(const BatchArgs<E> args)
         if (ts < total) {
             loc[s] = locate<E, VEC>(args, ts, PATTERN);
             const LevelArgs<E>& L = args.lev[loc[s].l];
-            async_issue_all<E, VEC, BLOCK, STAGES, FIX>(L.src + (int64_t)loc[s].m * Q * L.g.n, L.g, loc[s], lane, ring,
-                                                       s);
+            async_issue_all<E, VEC, BLOCK, STAGES, FIX, WRAP>(L.src + (int64_t)loc[s].m * Q * L.g.n, L.g, loc[s], lane,
+                                                             ring, s);
         }
         cp_async_commit();
     }
@@ -168,15 +170,15 @@ __global__ void __launch_bounds__(BLOCK) k_step_async(const BatchArgs<E> args)
             const LevelArgs<E>& La = args.lev[ahead.l];
             int sa = stage + STAGES - 1;
             if (sa >= STAGES) sa -= STAGES;
-            async_issue_all<E, VEC, BLOCK, STAGES, FIX>(La.src + (int64_t)ahead.m * Q * La.g.n, La.g, ahead, lane, ring,
-                                                       sa);
+            async_issue_all<E, VEC, BLOCK, STAGES, FIX, WRAP>(La.src + (int64_t)ahead.m * Q * La.g.n, La.g, ahead, lane,
+                                                             ring, sa);
         }
         cp_async_commit();
         cp_async_wait<STAGES - 1>();
         const LevelArgs<E>& L = args.lev[cur.l];
         const Geom g = L.g;
         C v[Q][VEC];
-        async_finish_all<E, VEC, BLOCK, STAGES, FIX>(smem, stage, threadIdx.x, g, cur, lane, v);
+        async_finish_all<E, VEC, BLOCK, STAGES, FIX, WRAP>(smem, stage, threadIdx.x, g, cur, lane, v);
         collide_run<E, VEC, (VEC % 2 == 0)>(v, L);
         E* base = L.dst + (int64_t)cur.m * Q * g.n;
         const int mode = FIX >= 0 ? FIX : cur.mode;
@@ -185,7 +187,7 @@ __global__ void __launch_bounds__(BLOCK) k_step_async(const BatchArgs<E> args)
         else if (mode == 1)
             store_own_opp<E, VEC>(base, g, cur.node, v);
         else
-            scatter_all<E, VEC, 1>(base, g, cur.x0, cur.y, cur.z, lane, v);
+            scatter_all<E, VEC, 1, WRAP>(base, g, cur.x0, cur.y, cur.z, lane, v);
         t += stride;
         if (t >= total) break;
 #pragma unroll

@@ -169,6 +169,13 @@ __device__ __forceinline__ P run_direct(P base, const Geom& g, int slot, int x0,
     return base + (int64_t)slot * g.n + g.node(0, g.wrap(y + dy), g.wrap(z + dz)) + x0;
 }
 
+// Row rotation (the WRAP variants, for launches whose every level has N <= 32 VEC): a whole
+// x-row is then R = N / VEC consecutive lanes of one warp (R divides 32), and the periodic
+// neighbour of a row's end run is the row's other end, one shuffle among the row's lanes away,
+// so every lane loads and stores full aligned runs with no separate end elements.  The launch
+// picks the variant (a compile-time choice: no per-population branch).
+__device__ __forceinline__ int row_lane(int lane, int R, int d) { return (lane & ~(R - 1)) | ((lane + d) & (R - 1)); }
+
 // Offsets from a run's first element (x0) to the element before it and after it in its
 // periodic row.
 __device__ __forceinline__ int before_run(int x0, int N) { return x0 == 0 ? N - 1 : -1; }
@@ -202,7 +209,7 @@ __device__ __forceinline__ void gather_row(const E* run, int x0, int N, int lane
 
 // Scatter the VEC values of nodes x0..x0+VEC-1 to positions shifted by CXI in x; run points
 // at element x0 of the destination row.
-template <class E, int VEC, int CXI>
+template <class E, int VEC, int CXI, bool WRAP = false>
 __device__ __forceinline__ void scatter_row(E* run, int x0, int N, int lane, const typename Storage<E>::compute (&v)[VEC])
 {
     E w[VEC];
@@ -210,6 +217,18 @@ __device__ __forceinline__ void scatter_row(E* run, int x0, int N, int lane, con
     for (int k = 0; k < VEC; ++k) w[k] = from_c<E>(v[k]);
     if constexpr (CXI == 0) {
         vstore<E, VEC>(run, w);
+    } else if constexpr (WRAP) {  // the row's lanes rotate: every lane stores a full run
+        E o[VEC];
+        if constexpr (CXI > 0) {  // node x goes to x + 1
+            o[0] = __shfl_sync(0xffffffffu, w[VEC - 1], row_lane(lane, N / VEC, -1));
+#pragma unroll
+            for (int k = 1; k < VEC; ++k) o[k] = w[k - 1];
+        } else {  // node x goes to x - 1
+#pragma unroll
+            for (int k = 0; k < VEC - 1; ++k) o[k] = w[k + 1];
+            o[VEC - 1] = __shfl_sync(0xffffffffu, w[0], row_lane(lane, N / VEC, 1));
+        }
+        vstore<E, VEC>(run, o);
     } else if constexpr (CXI > 0) {  // node x goes to x + 1
         const E prev = __shfl_up_sync(0xffffffffu, w[VEC - 1], 1);
         const bool can_receive = lane != 0 && x0 != 0;
@@ -326,14 +345,14 @@ __device__ __forceinline__ void gather_all(const E* base, const Geom& g, int x0,
 }
 
 // Store all Q post-collision populations: slot I of the row shifted by SIGN * c_i.
-template <class E, int VEC, int SIGN, int I = 0>
+template <class E, int VEC, int SIGN, bool WRAP = false, int I = 0>
 __device__ __forceinline__ void scatter_rows(E* base, const Geom& g, const RowOffsets& r, int x0, int lane,
                                              const typename Storage<E>::compute (&v)[Q][VEC])
 {
     if constexpr (I < Q) {
-        scatter_row<E, VEC, SIGN * Dir<I>::x>(run_at(base, g, I, r, SIGN * Dir<I>::y, SIGN * Dir<I>::z), x0, g.N,
-                                               lane, v[I]);
-        scatter_rows<E, VEC, SIGN, I + 1>(base, g, r, x0, lane, v);
+        scatter_row<E, VEC, SIGN * Dir<I>::x, WRAP>(run_at(base, g, I, r, SIGN * Dir<I>::y, SIGN * Dir<I>::z), x0,
+                                                     g.N, lane, v[I]);
+        scatter_rows<E, VEC, SIGN, WRAP, I + 1>(base, g, r, x0, lane, v);
     }
 }
 template <class E, int VEC, int I = 0>
@@ -346,12 +365,12 @@ __device__ __forceinline__ void scatter_direct(E* base, const Geom& g, int x0, i
     }
 }
 // SIGN 1: the AA odd step (row offsets); 0: pull, own rows (direct addresses).
-template <class E, int VEC, int SIGN>
+template <class E, int VEC, int SIGN, bool WRAP = false>
 __device__ __forceinline__ void scatter_all(E* base, const Geom& g, int x0, int y, int z, int lane,
                                             const typename Storage<E>::compute (&v)[Q][VEC])
 {
     if constexpr (SIGN != 0)
-        scatter_rows<E, VEC, SIGN>(base, g, row_offsets(g, x0, y, z), x0, lane, v);
+        scatter_rows<E, VEC, SIGN, WRAP>(base, g, row_offsets(g, x0, y, z), x0, lane, v);
     else
         scatter_direct<E, VEC>(base, g, x0, y, z, lane, v);
 }
@@ -445,24 +464,37 @@ struct RunLoc {
     int64_t node;
 };
 
-template <class E, int VEC, int CXI>
+template <class E, int VEC, int CXI, bool WRAP = false>
 __device__ __forceinline__ void issue_row(const E* run, int x0, int N, int lane, RawRun<E, VEC>& r)
 {
     vload<E, VEC>(run, r.w);
-    if constexpr (CXI > 0) {
+    if constexpr (WRAP) {  // the row's lanes rotate: no end element to load
+    } else if constexpr (CXI > 0) {
         if (lane == 0 || x0 == 0) r.edge = sload<E>(run + before_run(x0, N));
     } else if constexpr (CXI < 0) {
         if (lane == 31 || x0 + VEC == N) r.edge = sload<E>(run + after_run<VEC>(x0, N));
     }
 }
 
-template <class E, int VEC, int CXI>
+template <class E, int VEC, int CXI, bool WRAP = false>
 __device__ __forceinline__ void finish_row(const RawRun<E, VEC>& r, int x0, int N, int lane,
                                            typename Storage<E>::compute (&v)[VEC])
 {
     if constexpr (CXI == 0) {
 #pragma unroll
         for (int k = 0; k < VEC; ++k) v[k] = to_c<E>(r.w[k]);
+    } else if constexpr (WRAP) {  // the row's lanes rotate
+        if constexpr (CXI > 0) {
+            const E prev = __shfl_sync(0xffffffffu, r.w[VEC - 1], row_lane(lane, N / VEC, -1));
+            v[0] = to_c<E>(prev);
+#pragma unroll
+            for (int k = 1; k < VEC; ++k) v[k] = to_c<E>(r.w[k - 1]);
+        } else {
+            const E next = __shfl_sync(0xffffffffu, r.w[0], row_lane(lane, N / VEC, 1));
+#pragma unroll
+            for (int k = 0; k < VEC - 1; ++k) v[k] = to_c<E>(r.w[k + 1]);
+            v[VEC - 1] = to_c<E>(next);
+        }
     } else if constexpr (CXI > 0) {
         E prev = __shfl_up_sync(0xffffffffu, r.w[VEC - 1], 1);
         if (lane == 0 || x0 == 0) prev = r.edge;
@@ -478,7 +510,7 @@ __device__ __forceinline__ void finish_row(const RawRun<E, VEC>& r, int x0, int 
     }
 }
 
-template <class E, int VEC, int FIX, int I = 0>
+template <class E, int VEC, int FIX, bool WRAP = false, int I = 0>
 __device__ __forceinline__ void issue_rows(const E* base, const Geom& g, const RowOffsets& r, const RunLoc& p,
                                            int lane, RawRun<E, VEC> (&raw)[Q])
 {
@@ -488,13 +520,13 @@ __device__ __forceinline__ void issue_rows(const E* base, const Geom& g, const R
         const int slot = mode == 2 ? Dir<I>::o : I;
         const E* run = run_at(base, g, slot, r, shift ? -Dir<I>::y : 0, shift ? -Dir<I>::z : 0);
         if (shift)
-            issue_row<E, VEC, Dir<I>::x>(run, p.x0, g.N, lane, raw[I]);
+            issue_row<E, VEC, Dir<I>::x, WRAP>(run, p.x0, g.N, lane, raw[I]);
         else
             issue_row<E, VEC, 0>(run, p.x0, g.N, lane, raw[I]);
-        issue_rows<E, VEC, FIX, I + 1>(base, g, r, p, lane, raw);
+        issue_rows<E, VEC, FIX, WRAP, I + 1>(base, g, r, p, lane, raw);
     }
 }
-template <class E, int VEC, int FIX, int I = 0>
+template <class E, int VEC, int FIX, bool WRAP = false, int I = 0>
 __device__ __forceinline__ void issue_direct(const E* base, const Geom& g, const RunLoc& p, int lane,
                                              RawRun<E, VEC> (&raw)[Q])
 {
@@ -504,34 +536,34 @@ __device__ __forceinline__ void issue_direct(const E* base, const Geom& g, const
         const int slot = mode == 2 ? Dir<I>::o : I;
         const E* run = run_direct(base, g, slot, p.x0, p.y, p.z, shift ? -Dir<I>::y : 0, shift ? -Dir<I>::z : 0);
         if (shift)
-            issue_row<E, VEC, Dir<I>::x>(run, p.x0, g.N, lane, raw[I]);
+            issue_row<E, VEC, Dir<I>::x, WRAP>(run, p.x0, g.N, lane, raw[I]);
         else
             issue_row<E, VEC, 0>(run, p.x0, g.N, lane, raw[I]);
-        issue_direct<E, VEC, FIX, I + 1>(base, g, p, lane, raw);
+        issue_direct<E, VEC, FIX, WRAP, I + 1>(base, g, p, lane, raw);
     }
 }
 // FIX 2 (AA odd): row offsets; pull, AA even and mixed launches: direct addresses.
-template <class E, int VEC, int FIX>
+template <class E, int VEC, int FIX, bool WRAP = false>
 __device__ __forceinline__ void issue_all(const E* base, const Geom& g, const RunLoc& p, int lane,
                                           RawRun<E, VEC> (&raw)[Q])
 {
     if constexpr (FIX == 2)
-        issue_rows<E, VEC, FIX>(base, g, row_offsets(g, p.x0, p.y, p.z), p, lane, raw);
+        issue_rows<E, VEC, FIX, WRAP>(base, g, row_offsets(g, p.x0, p.y, p.z), p, lane, raw);
     else
-        issue_direct<E, VEC, FIX>(base, g, p, lane, raw);
+        issue_direct<E, VEC, FIX, WRAP>(base, g, p, lane, raw);
 }
 
-template <class E, int VEC, int FIX, int I = 0>
+template <class E, int VEC, int FIX, bool WRAP = false, int I = 0>
 __device__ __forceinline__ void finish_all(const Geom& g, const RunLoc& p, int lane, const RawRun<E, VEC> (&raw)[Q],
                                            typename Storage<E>::compute (&v)[Q][VEC])
 {
     if constexpr (I < Q) {
         const int mode = FIX >= 0 ? FIX : p.mode;
         if (mode != 1)
-            finish_row<E, VEC, Dir<I>::x>(raw[I], p.x0, g.N, lane, v[I]);
+            finish_row<E, VEC, Dir<I>::x, WRAP>(raw[I], p.x0, g.N, lane, v[I]);
         else
             finish_row<E, VEC, 0>(raw[I], p.x0, g.N, lane, v[I]);
-        finish_all<E, VEC, FIX, I + 1>(g, p, lane, raw, v);
+        finish_all<E, VEC, FIX, WRAP, I + 1>(g, p, lane, raw, v);
     }
 }
 
@@ -557,7 +589,7 @@ __device__ __forceinline__ RunLoc locate(const BatchArgs<E>& args, int64_t t, in
 // FIX: -1 takes each level's mode at run time; 0 (pull), 1 (AA even) or 2 (AA odd) when every
 // level of the launch has that mode, which drops the other branches.  PACK: packed FP32
 // collision of node pairs.
-template <class E, int VEC, int PATTERN, int BLOCK, int FIX, bool PACK>
+template <class E, int VEC, int PATTERN, int BLOCK, int FIX, bool PACK, bool WRAP = false>
 __global__ void __launch_bounds__(BLOCK) k_step_prefetch(const BatchArgs<E> args)
 {
     using C = typename Storage<E>::compute;
@@ -570,20 +602,20 @@ __global__ void __launch_bounds__(BLOCK) k_step_prefetch(const BatchArgs<E> args
     RawRun<E, VEC> raw[Q];
     {
         const LevelArgs<E>& L = args.lev[cur.l];
-        issue_all<E, VEC, FIX>(L.src + (int64_t)cur.m * Q * L.g.n, L.g, cur, lane, raw);
+        issue_all<E, VEC, FIX, WRAP>(L.src + (int64_t)cur.m * Q * L.g.n, L.g, cur, lane, raw);
     }
     while (true) {
         const LevelArgs<E>& L = args.lev[cur.l];
         const Geom g = L.g;
         C v[Q][VEC];
-        finish_all<E, VEC, FIX>(g, cur, lane, raw, v);
+        finish_all<E, VEC, FIX, WRAP>(g, cur, lane, raw, v);
         const int64_t tn = t + stride;
         const bool more = tn < total;
         RunLoc nxt = cur;
         if (more) {
             nxt = locate<E, VEC>(args, tn, PATTERN);
             const LevelArgs<E>& Ln = args.lev[nxt.l];
-            issue_all<E, VEC, FIX>(Ln.src + (int64_t)nxt.m * Q * Ln.g.n, Ln.g, nxt, lane, raw);
+            issue_all<E, VEC, FIX, WRAP>(Ln.src + (int64_t)nxt.m * Q * Ln.g.n, Ln.g, nxt, lane, raw);
         }
         collide_run<E, VEC, PACK>(v, L);
         E* base = L.dst + (int64_t)cur.m * Q * g.n;
@@ -593,7 +625,7 @@ __global__ void __launch_bounds__(BLOCK) k_step_prefetch(const BatchArgs<E> args
         else if (mode == 1)
             store_own_opp<E, VEC>(base, g, cur.node, v);
         else
-            scatter_all<E, VEC, 1>(base, g, cur.x0, cur.y, cur.z, lane, v);
+            scatter_all<E, VEC, 1, WRAP>(base, g, cur.x0, cur.y, cur.z, lane, v);
         if (!more) break;
         t = tn;
         cur = nxt;

@@ -30,10 +30,10 @@ cudaError_t launch_variant(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, 
     return cudaGetLastError();
 }
 
-template <class E, int VEC, int PATTERN, int BLOCK, int FIX, bool PACK>
+template <class E, int VEC, int PATTERN, int BLOCK, int FIX, bool PACK, bool WRAP = false>
 cudaError_t launch_prefetch_fixed(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, int* occupancy_out)
 {
-    auto kern = k_step_prefetch<E, VEC, PATTERN, BLOCK, FIX, PACK>;
+    auto kern = k_step_prefetch<E, VEC, PATTERN, BLOCK, FIX, PACK, WRAP>;
     static int occ = -1;
     if (occ < 0) {
         int o = 0;
@@ -51,6 +51,16 @@ cudaError_t launch_prefetch_fixed(const BatchArgs<E>& a, int grid_cap, cudaStrea
     return cudaGetLastError();
 }
 
+// Whether every level's x-row lies within one warp (N <= 32 VEC): the launch then takes the
+// kernels' row-rotation variant (WRAP) for its shifted rows.
+template <class E>
+bool rows_in_warp(const BatchArgs<E>& a, int vec)
+{
+    for (int l = 0; l < a.nlev; ++l)
+        if (a.lev[l].g.N > 32 * vec) return false;
+    return true;
+}
+
 // Parity of an AA launch: the host launches AA levels of different parity separately
 // (launch_levels), so every launch here has one parity; -1 if not (not launched).
 template <class E>
@@ -66,19 +76,29 @@ template <class E, int VEC, int PATTERN, int BLOCK, bool PACK>
 cudaError_t launch_prefetch_variant(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, int* occ)
 {
     if constexpr (PATTERN == 0) {
+        // pull: FP16 storage takes the row rotation where rows lie within one warp (measured: FP16
+        // pull with 4 nodes per thread 75.6% -> 82.3%); FP32, at the memory bound, keeps the end
+        // elements (no gain measured)
+        if constexpr (std::is_same<E, __half>::value)
+            if (rows_in_warp(a, VEC)) return launch_prefetch_fixed<E, VEC, 0, BLOCK, 0, PACK, true>(a, grid_cap, s, occ);
         return launch_prefetch_fixed<E, VEC, 0, BLOCK, 0, PACK>(a, grid_cap, s, occ);
     } else {
         const int par = launch_parity(a);
         if (par == 0) return launch_prefetch_fixed<E, VEC, 1, BLOCK, 1, PACK>(a, grid_cap, s, occ);
-        if (par == 1) return launch_prefetch_fixed<E, VEC, 1, BLOCK, 2, PACK>(a, grid_cap, s, occ);
+        if (par == 1) {
+            // odd steps shift loads and stores: where every level's x-row lies within one warp the
+            // row's lanes rotate (no separate end elements)
+            if (rows_in_warp(a, VEC)) return launch_prefetch_fixed<E, VEC, 1, BLOCK, 2, PACK, true>(a, grid_cap, s, occ);
+            return launch_prefetch_fixed<E, VEC, 1, BLOCK, 2, PACK>(a, grid_cap, s, occ);
+        }
         return cudaErrorInvalidValue;
     }
 }
 
-template <class E, int VEC, int PATTERN, int BLOCK, int FIX, int STAGES>
+template <class E, int VEC, int PATTERN, int BLOCK, int FIX, int STAGES, bool WRAP = false>
 cudaError_t launch_async_fixed(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, int* occupancy_out)
 {
-    auto kern = k_step_async<E, VEC, PATTERN, BLOCK, FIX, STAGES>;
+    auto kern = k_step_async<E, VEC, PATTERN, BLOCK, FIX, STAGES, WRAP>;
     constexpr int smem = AsyncRing<E, VEC, BLOCK, STAGES>::kBytes;
     static int occ = -1;
     if (occ < 0) {
@@ -103,12 +123,24 @@ cudaError_t launch_async_fixed(const BatchArgs<E>& a, int grid_cap, cudaStream_t
 template <class E, int VEC, int PATTERN, int BLOCK, int STAGES>
 cudaError_t launch_async_variant(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, int* occ)
 {
+    // steps with shifted rows (pull, AA odd) of FP16 storage take the row rotation where every
+    // level's row lies within one warp (measured at 128^3 x 32: FP16 pull 81.6% -> 88.6% of the
+    // copy bandwidth, AA odd 65% -> 77%; FP32, already at the memory bound, loses with it:
+    // AA odd 100% -> 89%, so FP32 ring launches keep the end elements)
+    constexpr bool kWrapKind = std::is_same<E, __half>::value;
+    const bool wrap = kWrapKind && rows_in_warp(a, VEC);
     if constexpr (PATTERN == 0) {
+        if constexpr (kWrapKind)
+            if (wrap) return launch_async_fixed<E, VEC, 0, BLOCK, 0, STAGES, true>(a, grid_cap, s, occ);
         return launch_async_fixed<E, VEC, 0, BLOCK, 0, STAGES>(a, grid_cap, s, occ);
     } else {
         const int par = launch_parity(a);
         if (par == 0) return launch_async_fixed<E, VEC, 1, BLOCK, 1, STAGES>(a, grid_cap, s, occ);
-        if (par == 1) return launch_async_fixed<E, VEC, 1, BLOCK, 2, STAGES>(a, grid_cap, s, occ);
+        if (par == 1) {
+            if constexpr (kWrapKind)
+                if (wrap) return launch_async_fixed<E, VEC, 1, BLOCK, 2, STAGES, true>(a, grid_cap, s, occ);
+            return launch_async_fixed<E, VEC, 1, BLOCK, 2, STAGES>(a, grid_cap, s, occ);
+        }
         return cudaErrorInvalidValue;
     }
 }
