@@ -39,9 +39,9 @@ STEPPER_SOURCES = ["paper_2608_23786_gb300/csrc/stepper.cu", "paper_2608_23786_g
                    "paper_2608_23786_gb300/csrc/stepper_f32_pull.cu"]
 # DRAM bytes (read + write) per launch of the stepper on this workload, from one ncu capture of the
 # kernel built from sources with this digest and launched with this shape (kind, vec, block); the
-# capture ran 16 of the 64 samples (318.8 MB read + 267.6 MB written) and is scaled by 64/16.
+# capture ran 16 of the 64 samples (318.9 MB read + 267.7 MB written) and is scaled by 64/16.
 # Reported as null when the sources or the launch shape differ.
-NCU_TRAFFIC = {"sha256": "c18dfcc40eb1ed25", "launch": (3, 2, 128), "bytes_per_launch": 4 * (318.807040e6 + 267.649792e6)}
+NCU_TRAFFIC = {"sha256": "854b4c35242ed047", "launch": (3, 2, 128), "bytes_per_launch": 4 * (318.864384e6 + 267.672832e6)}
 
 
 def stepper_digest():
@@ -265,7 +265,7 @@ def run_peaks(args):
 def run_stats(args):
     """The ensemble statistics on one ensemble (N = 128, M = 4 unless --N / --M; storage
     --precision, FP32 by default) after 10 steps, each timed once with CUDA events after one
-    untimed call: E_m and the mean/variance fields in one pass, the shell spectrum, trace S_2,
+    untimed call: E_m and Z_m, E_m and the mean/variance fields in one pass, the shell spectrum, trace S_2,
     S_p along the axes (p = 2..6), the restriction to 8^3 points, the one-point W1 and the
     vector and component-wise two-point W1 against a second ensemble of the same shape."""
     import torch
@@ -280,7 +280,8 @@ def run_stats(args):
         gen.draw_params(7, M)).step(10)
     B = Ensemble(N, M, Re=1600.0, Ma=1.6 / N, precision=prec, seed=8, device=dev, stream=stream).init(
         gen.draw_params(8, M)).step(10)
-    calls = {"energy_mean_var": lambda: A.energy_mean_var(), "spectrum": lambda: A.spectrum(),
+    calls = {"energy_enstrophy": lambda: A.energy(enstrophy=True), "energy_mean_var": lambda: A.energy_mean_var(),
+             "spectrum": lambda: A.spectrum(),
              "sf_trace": lambda: A.sf_trace(), "sf_axes_p2_6": lambda: A.sf_axes(6), "restrict_8": lambda: A.restrict(8),
              "w1_1pt": lambda: A.w1(B), "w1_2pt_vector": lambda: A.w1_2pt(B, Q=8, vector=True),
              "w1_2pt_componentwise": lambda: A.w1_2pt(B, Q=8, vector=False)}

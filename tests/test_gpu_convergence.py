@@ -38,3 +38,4 @@ def test_sample_error_work_buffer_check():
     with pytest.raises(mclbm.MclbmError) as e:
         mclbm.mclbm_sample_error(u.data_ptr(), u.data_ptr(), 4, 8, work.data_ptr(), nb - 8)
     assert e.value.status == "OOM"
+
