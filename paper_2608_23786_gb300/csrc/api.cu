@@ -158,8 +158,8 @@ LaunchConfig default_launch(int precision, int pattern, int options)
     if (options & MCLBM_OPT_EXACT_GAMMA) return LaunchConfig{exact_vec(precision), 128, 6};
 #ifdef MCLBM_D3Q27
     // D3Q27 (measured at 128^3 x 32): FP32 prefetching kernel in blocks of 256; FP16 pull the
-    // shared-memory ring (76% against 67% for the direct kernel), AA even steps the packed
-    // prefetching one in blocks of 256
+    // shared-memory ring (81% with the row rotation, against 67% for the direct kernel), AA even
+    // steps the packed prefetching one in blocks of 256
     if (precision == MCLBM_FP64) return LaunchConfig{1, 128, 0};
     if (precision == MCLBM_FP32) return LaunchConfig{2, 256, 2};
     return pattern == MCLBM_PULL ? LaunchConfig{4, 128, 4} : LaunchConfig{4, 256, 3};
@@ -172,14 +172,15 @@ LaunchConfig default_launch(int precision, int pattern, int options)
 
 // AA odd steps read and write shifted rows and favour other shapes (measured per parity at
 // 128^3 x 32 and 64^3 x 64): D3Q19 FP32 the two-stage cp.async ring with 4 nodes per thread,
-// FP16 the packed prefetching kernel with 4; D3Q27 FP32 the packed prefetching kernel in blocks
-// of 256, FP16 the one-stage cp.async ring (63% against 52% for the one-node prefetching kernel).
+// FP16 the packed prefetching kernel with 4; D3Q27 FP32 and FP16 the packed prefetching kernel in
+// blocks of 256 (D3Q27 FP16 with the row rotation at 128^3: 81.7% of the copy bandwidth, against
+// 52% for the one-node prefetching kernel without it).
 LaunchConfig default_launch_odd(int precision, int pattern, int options)
 {
     const LaunchConfig even = default_launch(precision, pattern, options);
     if (pattern != MCLBM_AA || even.kind == 6 || precision == MCLBM_FP64) return even;
 #ifdef MCLBM_D3Q27
-    return precision == MCLBM_FP32 ? LaunchConfig{2, 256, 3} : LaunchConfig{4, 128, 4};
+    return precision == MCLBM_FP32 ? LaunchConfig{2, 256, 3} : LaunchConfig{4, 256, 3};
 #else
     return precision == MCLBM_FP32 ? LaunchConfig{4, 128, 5} : LaunchConfig{4, 128, 3};
 #endif
