@@ -149,6 +149,9 @@ TARGETS = [("rtgv_128cube_x32_fp32_pull", 128, 32, 1600.0, 0.0125, "fp32", "pull
            ("rtgv_128cube_x32_fp16_pull", 128, 32, 1600.0, 0.0125, "fp16", "pull"),
            ("rtgv_128cube_x32_fp16_aa", 128, 32, 1600.0, 0.0125, "fp16", "aa"),
            ("rtgv_512cube_x4_fp16_aa", 512, 4, 6400.0, 0.003125, "fp16", "aa")]
+# the D3Q27 library at the target shape (FP16 storage: the configuration furthest from the roofline)
+TARGETS_D3Q27 = [("rtgv_128cube_x32_fp16_pull_d3q27", 128, 32, 1600.0, 0.0125, "fp16", "pull"),
+                 ("rtgv_128cube_x32_fp16_aa_d3q27", 128, 32, 1600.0, 0.0125, "fp16", "aa")]
 LEVELS = [(64, 64, 400.0, 0.025, 1, 1), (128, 32, 1600.0, 0.0125, 4, 2), (256, 8, 3200.0, 0.00625, 16, 3)]
 ALU_KINDS = [("fp64_fma", 2.0), ("fp32_fma", 2.0), ("fp32x2_fma", 2.0), ("half2_fma", 2.0), ("fp32_rcp", 1.0)]
 
@@ -179,9 +182,11 @@ def measure_targets(dev, stream, peaks, peak_kind, lattice=19):
     from paper_2608_23786_gb300 import Ensemble, mclbm
     import ensemble_inputs as gen
     out = {}
-    for name, N, M, Re, Ma, prec, pat in TARGETS:
+    runs = [t + (lattice,) for t in TARGETS] + ([t + (27,) for t in TARGETS_D3Q27] if lattice == 19 else [])
+    for name, N, M, Re, Ma, prec, pat, q in runs:
+        mclbm.load(lattice=q)
         ens = Ensemble(N, M, Re=Re, Ma=Ma, precision=prec, pattern=pat, seed=2, device=dev, stream=stream,
-                       lattice=lattice).init(gen.draw_params(2, M))
+                       lattice=q).init(gen.draw_params(2, M))
         step = lambda n: ens.step(n)  # noqa: E731
         step(4)
         est = _event_time(stream, step, 4) / 4
@@ -191,7 +196,7 @@ def measure_targets(dev, stream, peaks, peak_kind, lattice=19):
             sec = _event_time(stream, step, n)
         mclbm.mclbm_device_status(ens.ctx)
         lu = M * N**3 * n
-        bpl = BYTES_PER_LU[prec] * lattice // 19
+        bpl = BYTES_PER_LU[prec] * q // 19
         ach = bpl * lu / sec / 1e9
         launch = launch_desc(mclbm.mclbm_get_launch_parity(ens.ctx, 0),
                              mclbm.mclbm_get_launch_parity(ens.ctx, 1) if pat == "aa" else None)

@@ -339,7 +339,8 @@ typedef struct mclbm_batch mclbm_batch;
 MCLBM_API int mclbm_batch_create(mclbm_ctx* const* levels, int32_t nlev, const int32_t* substeps, mclbm_batch** out);
 MCLBM_API void mclbm_batch_destroy(mclbm_batch* b);
 MCLBM_API int mclbm_batch_set_graph(mclbm_batch* b, int32_t enable);
-/* The batch's launch shape (initially that of levels[0]): mclbm_batch_set_launch for every
+/* The batch's launch shape (initially that of levels[0]; an AA odd-step shape still at its
+ * default becomes the default for the batch's largest level): mclbm_batch_set_launch for every
  * step, the _parity forms per parity of AA batches, with the rules of
  * mclbm_set_launch_parity; every level must accept the shape. */
 MCLBM_API int mclbm_batch_set_launch(mclbm_batch* b, int32_t kind, int32_t vec, int32_t block);

@@ -317,6 +317,20 @@ int mclbm_batch_create(mclbm_ctx* const* levels, int32_t nlev, const int32_t* su
     b->stream = levels[0]->stream;
     b->launch = levels[0]->launch;
     b->launch_odd = levels[0]->launch_odd;
+    {
+        // levels[0] on its default odd-step shape: the batch takes the default for its largest level
+        const mclbm_config& c0 = levels[0]->cfg;
+        int Nmax = 0;
+        for (int l = 0; l < nlev; ++l) Nmax = levels[l]->N > Nmax ? levels[l]->N : Nmax;
+        const LaunchConfig d0 = default_launch_odd(c0.precision, c0.pattern, c0.options, levels[0]->N);
+        const LaunchConfig& cur = levels[0]->launch_odd;
+        if (cur.kind == d0.kind && cur.vec == d0.vec && cur.block == d0.block) {
+            const LaunchConfig dm = default_launch_odd(c0.precision, c0.pattern, c0.options, Nmax);
+            bool ok = true;
+            for (int l = 0; l < nlev; ++l) ok = ok && launch_supported(c0.precision, dm) && levels[l]->N % dm.vec == 0;
+            if (ok) b->launch_odd = dm;
+        }
+    }
     b->use_graph = b->stream != nullptr;
     b->warmed = false;
     b->macro_steps = 0;

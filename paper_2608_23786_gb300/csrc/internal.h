@@ -83,7 +83,7 @@ cudaError_t launch_levels(mclbm_ctx* const* levels, int nlev, const LaunchConfig
 bool vec_supported(int precision, int vec);
 bool launch_supported(int precision, const LaunchConfig& c);
 LaunchConfig default_launch(int precision, int pattern, int options);
-LaunchConfig default_launch_odd(int precision, int pattern, int options);  // AA odd steps
+LaunchConfig default_launch_odd(int precision, int pattern, int options, int Nmax);  // AA odd steps
 int exact_vec(int precision);  // the one VEC of the exact-gamma kernel (kind 6)
 void leray_map(const double* X, int M, bool transpose, double* Y);  // api.cu
 cudaError_t launch_get_populations(const mclbm_ctx* c, int sample, double* d_out);

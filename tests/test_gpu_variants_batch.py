@@ -203,3 +203,30 @@ def test_batch_autotune_and_validation():
     other = Ensemble(16, 1, Re=100.0, Ma=0.1, precision="fp16", stream=stream).init()
     with pytest.raises(mclbm.MclbmError):
         mclbm.mclbm_batch_create([lv[0].ctx, other.ctx], (1, 4))  # mixed precision
+
+
+def test_batch_odd_step_default_follows_the_largest_level():
+    """An FP16 AA batch whose odd-step shape is still the default takes the default of its largest
+    level: 8 nodes per thread in the two-stage ring where the largest rows have 129..256 nodes (rows
+    within one warp rotate), 4 in the packed prefetching kernel otherwise; the stepped states equal
+    those of per-level stepping to the bit."""
+    stream = torch.cuda.Stream()
+    small = [Ensemble(N, 1, Re=400.0, Ma=0.05, precision="fp16", pattern="aa", seed=N, stream=stream).init()
+             for N in (32, 64)]
+    b = mclbm.mclbm_batch_create([e.ctx for e in small], [1, 2])
+    assert mclbm.mclbm_batch_get_launch_parity(b, 1) == (3, 4, 128)
+    mclbm.mclbm_batch_destroy(b)
+    spec = [(64, 2, 1), (256, 1, 2)]
+    lv = [Ensemble(N, M, Re=400.0, Ma=0.05, precision="fp16", pattern="aa", seed=N, stream=stream).init()
+          for N, M, _ in spec]
+    b = mclbm.mclbm_batch_create([e.ctx for e in lv], [s for _, _, s in spec])
+    assert mclbm.mclbm_batch_get_launch_parity(b, 1) == (4, 8, 128)
+    mclbm.mclbm_batch_step(b, 3)
+    stream.synchronize()
+    mclbm.mclbm_batch_destroy(b)
+    for (N, M, s), e in zip(spec, lv):
+        ref = Ensemble(N, M, Re=400.0, Ma=0.05, precision="fp16", pattern="aa", seed=N, stream=stream).init()
+        ref.step(3 * s)
+        assert e.steps_taken == 3 * s
+        for m in range(M):
+            assert torch.equal(e.populations(m), ref.populations(m))
