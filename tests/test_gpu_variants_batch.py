@@ -230,3 +230,18 @@ def test_batch_odd_step_default_follows_the_largest_level():
         assert e.steps_taken == 3 * s
         for m in range(M):
             assert torch.equal(e.populations(m), ref.populations(m))
+
+
+@pytest.mark.parametrize("precision,shapes", [("fp16", [(3, 4, 128), (3, 4, 256), (2, 4, 128)]),
+                                              ("fp32", [(3, 2, 128), (2, 1, 128), (3, 4, 128)])])
+def test_aa_odd_steps_with_rows_across_warps_equal_pull(precision, shapes):
+    """N = 256 with 1 to 4 nodes per thread: a row spans 2 to 8 warps, so the odd step's end
+    elements cross warp boundaries (loaded and stored apart); AA reaches pull's state to the bit."""
+    X = gen.draw_params(33, 1)
+    pull = Ensemble(256, 1, Re=800.0, Ma=0.05, precision=precision, pattern="pull").init(X).step(3)
+    for kind, vec, block in shapes:
+        ens = Ensemble(256, 1, Re=800.0, Ma=0.05, precision=precision, pattern="aa").init(X)
+        mclbm.mclbm_set_launch_parity(ens.ctx, 1, vec, block, kind)
+        ens.step(3)
+        mclbm.mclbm_device_status(ens.ctx)
+        assert torch.equal(ens.populations(0), pull.populations(0)), (kind, vec, block)
