@@ -176,9 +176,10 @@ LaunchConfig default_launch(int precision, int pattern, int options)
 // blocks of 256 (D3Q27 FP16 with the row rotation at 128^3: 81.7% of the copy bandwidth, against
 // 52% for the one-node prefetching kernel without it).
 // Nmax: the largest lattice the shape serves (a context's N, a batch's largest level): D3Q19 FP16
-// odd steps with 128 < Nmax <= 256 take the two-stage ring with 8 nodes per thread, whose rows of up
-// to 256 nodes lie within one warp and rotate (the three-level batch 64^3 x 64 + 128^3 x 32 + 256^3
-// x 8: 77.7% -> 81.8% of the copy bandwidth per macro step).
+// odd steps with Nmax <= 256 take the two-stage ring with 8 nodes per thread, whose rows of up to
+// 256 nodes lie within one warp and rotate (128^3 x 32: 81.4% of the copy bandwidth against 80.7%
+// for the packed prefetching kernel with 4; the three-level batch 64^3 x 64 + 128^3 x 32 + 256^3 x 8:
+// 84.2% per macro step against 77.7% with rows of 256 nodes spanning warps).
 LaunchConfig default_launch_odd(int precision, int pattern, int options, int Nmax)
 {
     const LaunchConfig even = default_launch(precision, pattern, options);
@@ -188,7 +189,7 @@ LaunchConfig default_launch_odd(int precision, int pattern, int options, int Nma
     return precision == MCLBM_FP32 ? LaunchConfig{2, 256, 3} : LaunchConfig{4, 256, 3};
 #else
     if (precision == MCLBM_FP32) return LaunchConfig{4, 128, 5};
-    if (Nmax > 32 * 4 && Nmax <= 32 * 8) return LaunchConfig{8, 128, 4};
+    if (Nmax <= 32 * 8) return LaunchConfig{8, 128, 4};
     return LaunchConfig{4, 128, 3};
 #endif
 }

@@ -119,7 +119,7 @@ __device__ __forceinline__ void async_finish_all(const unsigned char* smem, int 
         const int mode = FIX >= 0 ? FIX : p.mode;
         if (mode != 1) {
             const RawRun<E, VEC> r = ring_read<E, VEC, BLOCK, STAGES, WRAP ? 0 : Dir<I>::x>(smem, stage, I, tid);
-            finish_row<E, VEC, Dir<I>::x, WRAP>(r, p.x0, g.N, lane, v[I]);
+            finish_row<E, VEC, Dir<I>::x, WRAP, FIX == 0>(r, p.x0, g.N, lane, v[I]);
         } else {
             const RawRun<E, VEC> r = ring_read<E, VEC, BLOCK, STAGES, 0>(smem, stage, I, tid);
             finish_row<E, VEC, 0>(r, p.x0, g.N, lane, v[I]);

@@ -218,16 +218,22 @@ __device__ __forceinline__ void scatter_row(E* run, int x0, int N, int lane, con
     if constexpr (CXI == 0) {
         vstore<E, VEC>(run, w);
     } else if constexpr (WRAP) {  // the row's lanes rotate: every lane stores a full run
-        E o[VEC];
+        // the shift moves compute-type values (whole registers), then the shifted run is converted
+        // (for FP16, pairs of nodes pack into one word with no half-word rearranging)
+        using C = typename Storage<E>::compute;
+        C of[VEC];
         if constexpr (CXI > 0) {  // node x goes to x + 1
-            o[0] = __shfl_sync(0xffffffffu, w[VEC - 1], row_lane(lane, N / VEC, -1));
+            of[0] = __shfl_sync(0xffffffffu, v[VEC - 1], row_lane(lane, N / VEC, -1));
 #pragma unroll
-            for (int k = 1; k < VEC; ++k) o[k] = w[k - 1];
+            for (int k = 1; k < VEC; ++k) of[k] = v[k - 1];
         } else {  // node x goes to x - 1
 #pragma unroll
-            for (int k = 0; k < VEC - 1; ++k) o[k] = w[k + 1];
-            o[VEC - 1] = __shfl_sync(0xffffffffu, w[0], row_lane(lane, N / VEC, 1));
+            for (int k = 0; k < VEC - 1; ++k) of[k] = v[k + 1];
+            of[VEC - 1] = __shfl_sync(0xffffffffu, v[0], row_lane(lane, N / VEC, 1));
         }
+        E o[VEC];
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) o[k] = from_c<E>(of[k]);
         vstore<E, VEC>(run, o);
     } else if constexpr (CXI > 0) {  // node x goes to x + 1
         const E prev = __shfl_up_sync(0xffffffffu, w[VEC - 1], 1);
@@ -476,14 +482,17 @@ __device__ __forceinline__ void issue_row(const E* run, int x0, int N, int lane,
     }
 }
 
-template <class E, int VEC, int CXI, bool WRAP = false>
+// CF (pull steps): with the row rotation, the end element is converted before it moves, so the
+// shuffle moves a whole register (FP16 pull 88.7% -> 90.3% of the copy bandwidth at 128^3; the AA
+// odd step, at its register limit, loses with it and moves the stored element instead).
+template <class E, int VEC, int CXI, bool WRAP = false, bool CF = false>
 __device__ __forceinline__ void finish_row(const RawRun<E, VEC>& r, int x0, int N, int lane,
                                            typename Storage<E>::compute (&v)[VEC])
 {
     if constexpr (CXI == 0) {
 #pragma unroll
         for (int k = 0; k < VEC; ++k) v[k] = to_c<E>(r.w[k]);
-    } else if constexpr (WRAP) {  // the row's lanes rotate
+    } else if constexpr (WRAP && !CF) {  // the row's lanes rotate
         if constexpr (CXI > 0) {
             const E prev = __shfl_sync(0xffffffffu, r.w[VEC - 1], row_lane(lane, N / VEC, -1));
             v[0] = to_c<E>(prev);
@@ -494,6 +503,19 @@ __device__ __forceinline__ void finish_row(const RawRun<E, VEC>& r, int x0, int 
 #pragma unroll
             for (int k = 0; k < VEC - 1; ++k) v[k] = to_c<E>(r.w[k + 1]);
             v[VEC - 1] = to_c<E>(next);
+        }
+    } else if constexpr (WRAP) {  // the row's lanes rotate (converted values move: whole registers)
+        using C = typename Storage<E>::compute;
+        if constexpr (CXI > 0) {
+            const C last = to_c<E>(r.w[VEC - 1]);
+            v[0] = __shfl_sync(0xffffffffu, last, row_lane(lane, N / VEC, -1));
+#pragma unroll
+            for (int k = 1; k < VEC; ++k) v[k] = to_c<E>(r.w[k - 1]);
+        } else {
+            const C first = to_c<E>(r.w[0]);
+#pragma unroll
+            for (int k = 0; k < VEC - 1; ++k) v[k] = to_c<E>(r.w[k + 1]);
+            v[VEC - 1] = __shfl_sync(0xffffffffu, first, row_lane(lane, N / VEC, 1));
         }
     } else if constexpr (CXI > 0) {
         E prev = __shfl_up_sync(0xffffffffu, r.w[VEC - 1], 1);
@@ -560,7 +582,7 @@ __device__ __forceinline__ void finish_all(const Geom& g, const RunLoc& p, int l
     if constexpr (I < Q) {
         const int mode = FIX >= 0 ? FIX : p.mode;
         if (mode != 1)
-            finish_row<E, VEC, Dir<I>::x, WRAP>(raw[I], p.x0, g.N, lane, v[I]);
+            finish_row<E, VEC, Dir<I>::x, WRAP, FIX == 0>(raw[I], p.x0, g.N, lane, v[I]);
         else
             finish_row<E, VEC, 0>(raw[I], p.x0, g.N, lane, v[I]);
         finish_all<E, VEC, FIX, WRAP, I + 1>(g, p, lane, raw, v);

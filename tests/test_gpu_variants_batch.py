@@ -207,15 +207,18 @@ def test_batch_autotune_and_validation():
 
 def test_batch_odd_step_default_follows_the_largest_level():
     """An FP16 AA batch whose odd-step shape is still the default takes the default of its largest
-    level: 8 nodes per thread in the two-stage ring where the largest rows have 129..256 nodes (rows
-    within one warp rotate), 4 in the packed prefetching kernel otherwise; the stepped states equal
-    those of per-level stepping to the bit."""
+    level: 8 nodes per thread in the two-stage ring where the largest rows have up to 256 nodes
+    (rows within one warp rotate), 4 in the packed prefetching kernel beyond; the stepped states
+    equal those of per-level stepping to the bit."""
     stream = torch.cuda.Stream()
     small = [Ensemble(N, 1, Re=400.0, Ma=0.05, precision="fp16", pattern="aa", seed=N, stream=stream).init()
              for N in (32, 64)]
     b = mclbm.mclbm_batch_create([e.ctx for e in small], [1, 2])
-    assert mclbm.mclbm_batch_get_launch_parity(b, 1) == (3, 4, 128)
+    assert mclbm.mclbm_batch_get_launch_parity(b, 1) == (4, 8, 128)
     mclbm.mclbm_batch_destroy(b)
+    big = Ensemble(512, 1, Re=400.0, Ma=0.05, precision="fp16", pattern="aa", seed=5, stream=stream)
+    assert mclbm.mclbm_get_launch_parity(big.ctx, 1) == (3, 4, 128)
+    del big
     spec = [(64, 2, 1), (256, 1, 2)]
     lv = [Ensemble(N, M, Re=400.0, Ma=0.05, precision="fp16", pattern="aa", seed=N, stream=stream).init()
           for N, M, _ in spec]
