@@ -41,14 +41,20 @@ STEPPER_SOURCES = ["paper_2608_23786_gb300/csrc/stepper.cu", "paper_2608_23786_g
 # kernel built from sources with this digest and launched with this shape (kind, vec, block); the
 # capture ran 16 of the 64 samples (318.8 MB read + 267.6 MB written) and is scaled by 64/16.
 # Reported as null when the sources or the launch shape differ.
-NCU_TRAFFIC = {"sha256": "15f0e68ecfd72091", "launch": (3, 2, 128), "bytes_per_launch": 4 * (318.808832e6 + 267.566848e6)}
+NCU_TRAFFIC = {"sha256": "720e93a766ec8369", "launch": (3, 2, 128), "bytes_per_launch": 4 * (318.808832e6 + 267.566848e6)}
 
 
 def stepper_digest():
+    """Digest of the stepper's code: the sources with their line comments, trailing blanks and
+    empty lines removed, so that a change of wording in a comment keeps the traffic record (the
+    sources hold no string literal with a double slash)."""
     h = hashlib.sha256()
     for p in STEPPER_SOURCES:
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, p), encoding="utf-8") as f:
+            for line in f:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

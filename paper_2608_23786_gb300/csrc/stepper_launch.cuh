@@ -77,8 +77,8 @@ cudaError_t launch_prefetch_variant(const BatchArgs<E>& a, int grid_cap, cudaStr
 {
     if constexpr (PATTERN == 0) {
         // pull: FP16 storage takes the row rotation where rows lie within one warp (measured: FP16
-        // pull with 4 nodes per thread 75.6% -> 82.3%); FP32, at the memory bound, keeps the end
-        // elements (no gain measured)
+        // pull with 4 nodes per thread 75.6% -> 82.3% of the copy bandwidth at 128^3); FP32, at the
+        // memory bound, keeps the end elements (no gain measured)
         if constexpr (std::is_same<E, __half>::value)
             if (rows_in_warp(a, VEC)) return launch_prefetch_fixed<E, VEC, 0, BLOCK, 0, PACK, true>(a, grid_cap, s, occ);
         return launch_prefetch_fixed<E, VEC, 0, BLOCK, 0, PACK>(a, grid_cap, s, occ);
@@ -124,9 +124,9 @@ template <class E, int VEC, int PATTERN, int BLOCK, int STAGES>
 cudaError_t launch_async_variant(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, int* occ)
 {
     // steps with shifted rows (pull, AA odd) of FP16 storage take the row rotation where every
-    // level's row lies within one warp (measured at 128^3 x 32: FP16 pull 81.6% -> 88.6% of the
-    // copy bandwidth, AA odd 65% -> 77%; FP32, already at the memory bound, loses with it:
-    // AA odd 100% -> 89%, so FP32 ring launches keep the end elements)
+    // level's row lies within one warp (measured at 128^3 x 32 with 8 nodes per thread: FP16 pull
+    // 81.6% -> 90.6% of the copy bandwidth, AA odd steps 65% -> 81.4%; FP32, already at the memory
+    // bound, loses with it: AA odd 100% -> 89%, so FP32 ring launches keep the end elements)
     constexpr bool kWrapKind = std::is_same<E, __half>::value;
     const bool wrap = kWrapKind && rows_in_warp(a, VEC);
     if constexpr (PATTERN == 0) {
