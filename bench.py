@@ -1064,7 +1064,7 @@ def main():
         "alu_measured": alu,
         "adjoint": adjoint,
         "clocks": clk.summary(),
-        "stepper_sources_sha256": digest,
+        "stepper_code_digest": digest,
     }
     print(json.dumps(out))
     if world > 1:
