@@ -219,10 +219,11 @@ WorkLayout work_layout(int N, int M)
     size_t part = (size_t)M * 2 * 1024 * sizeof(double);
     wl.partial = take(part > kPartialBytes ? part : kPartialBytes);
     wl.flag = take(16 * sizeof(int));
-    wl.field = take(3 * n * sizeof(double));
+    wl.field = take(4 * n * sizeof(double));
     wl.cplx = take(n * 2 * sizeof(double));
     const size_t sfb = sf_axes_partial_bytes(N);
     wl.real = take(n * sizeof(double) > sfb ? n * sizeof(double) : sfb);
+    wl.real2 = take(n * sizeof(double));
     wl.twiddle = take((size_t)(N / 2) * 2 * sizeof(double));
     wl.trig = take((size_t)N * 4 * sizeof(double));
     size_t per = 2 * (size_t)(N / 2 + 1);

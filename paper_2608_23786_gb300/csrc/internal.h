@@ -17,9 +17,11 @@ struct WorkLayout {
     size_t params;    // [M][24] double
     size_t partial;   // reduction partials, kPartialBytes
     size_t flag;      // int status words (16 ints)
-    size_t field;     // velocity field of one sample [3][n] double
+    size_t field;     // velocity fields [4][n] double: one sample's [3][n], or during the paired
+                      // spectra the second sample's [3][n] below the first one's u_z
     size_t cplx;      // complex FFT buffer [n] double2
     size_t real;      // power spectrum / autocorrelation [n] double
+    size_t real2;     // power spectrum of the second sample of a pair [n] double
     size_t twiddle;   // [N/2] double2
     size_t trig;      // [N][4] double: sin, cos of x_n and 2 x_n
     size_t bins;      // shell sums [2][N/2+1] double x M

@@ -7,8 +7,13 @@
 // global access is a coalesced run of T complex values), applies the
 // bit-reversal permutation on load and log2 N butterfly stages in place, and
 // writes the tile back.  Twiddles exp(-2 pi i k / N) come from a table made
-// once per context.  The spectrum of a real field pair (u_x, u_y) comes from one
-// transform of u_x + i u_y.
+// once per context.  Real fields share complex transforms two at a time: samples
+// are taken in pairs (a, b), u_x + i u_y of each sample is one transform (only the
+// sum of the two powers is needed), and u_z of a with u_z of b is a third, whose two
+// powers are separated through Z_k and Z_-k: 1.5 forward transforms per sample.  The
+// autocorrelations of a pair come from one inverse transform of psi_a + i psi_b
+// (each psi is real and even, so each inverse is real).  An odd last sample takes
+// two forward and one inverse transform of its own.
 //
 // Shell sums: the blocks of shell kappa (or lag radius r) enumerate its integer
 // points {k in K_N : round(|k|) = kappa}, K_N = {-N/2+1..N/2}^3, with an exact
@@ -142,6 +147,25 @@ __global__ void k_accum_power_pair(const double2* __restrict__ in, double* __res
     }
 }
 
+// Powers of the two real fields packed as Z = a + i b, each on its own: 2 A_k = Z_k + conj(Z_-k)
+// and 2 i B_k = Z_k - conj(Z_-k), so |A_k|^2 and |B_k|^2 are a quarter of the squared moduli;
+// added to psi_a and psi_b.
+__global__ void k_accum_power_split(const double2* __restrict__ in, double* __restrict__ psi_a,
+                                    double* __restrict__ psi_b, int N, int logN)
+{
+    const int64_t n = (int64_t)N << (2 * logN);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(k & (N - 1)), iy = (int)((k >> logN) & (N - 1)), iz = (int)(k >> (2 * logN));
+        const int64_t km = ((int64_t)((N - iz) & (N - 1)) << (2 * logN)) | ((int64_t)((N - iy) & (N - 1)) << logN) |
+                           (int64_t)((N - ix) & (N - 1));
+        const double2 v = in[k], w = in[km];
+        const double ar = v.x + w.x, ai = v.y - w.y;  // 2 A_k
+        const double br = v.x - w.x, bi = v.y + w.y;  // 2 i B_k
+        psi_a[k] += 0.25 * (ar * ar + ai * ai);
+        psi_b[k] += 0.25 * (br * br + bi * bi);
+    }
+}
+
 __global__ void k_accum_power(const double2* __restrict__ in, double* __restrict__ psi, int64_t n, int first)
 {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
@@ -166,15 +190,27 @@ __device__ __forceinline__ double block_sum(double v, double* sh)
 }
 
 // Shell sums.  mode 0 (spectrum): out[kappa] = 4 pi / |S| sum |k|^2 psi / 2 * scale.
-// mode 1 (structure function): out[r] = 1/|C| sum 2 (R_0 - R_h), R_h = re(cbuf[h]) * scale.
+// mode 1 (structure function): out[r] = 1/|C| sum 2 (R_0 - R_h), R_h = cbuf[h] * scale, taking
+// the real (comp 0) or imaginary (comp 1) part of the complex buffer.
 // Block (kappa, s) takes every kShellSplit-th thread stride of the rows (k_z, k_y) with
 // |k_z|, |k_y| <= kappa (no other row meets the shell) and, per row, the k_x >= 0 with
 // 4|k|^2 in [(2 kappa - 1)^2, (2 kappa + 1)^2), found in integers; partial[kappa][s] = (sum,
-// count), summed over s in order by k_shell_finish.
+// count), summed over s in order by k_shell_finish.  One FP64 fma per point (the factors 1/2
+// and 2 are applied once per shell) and an integer count keep the work off the FP64 pipe.
 constexpr int kShellSplit = 16;
 
-__global__ void k_shells(const double* __restrict__ psi, const double2* __restrict__ cbuf, int N, int mode, double scale,
-                         double* __restrict__ partial)
+// Largest x >= 0 with 4 x^2 < v (v > 0): a single-precision guess (v < 2^24 here), corrected
+// in integers.
+__device__ __forceinline__ int isqrt_below(int64_t v)
+{
+    int x = (int)sqrtf(0.25f * (float)v);
+    while (x >= 0 && 4 * (int64_t)x * x >= v) --x;
+    while (4 * (int64_t)(x + 1) * (x + 1) < v) ++x;
+    return x;
+}
+
+__global__ void k_shells(const double* __restrict__ psi, const double2* __restrict__ cbuf, int comp, int N, int mode,
+                         double scale, double* __restrict__ partial)
 {
     __shared__ double sh[32];
     const int kap = blockIdx.x, s = blockIdx.y;
@@ -185,23 +221,22 @@ __global__ void k_shells(const double* __restrict__ psi, const double2* __restri
     const int lo = -R > -half + 1 ? -R : -half + 1;  // K_N: -N/2+1..N/2
     const int side = R - lo + 1;
     const int64_t rows = (int64_t)side * side;
-    const double R0 = mode == 1 ? cbuf[0].x * scale : 0.0;
-    double acc = 0.0, cnt = 0.0;
+    const double* cpart = reinterpret_cast<const double*>(cbuf) + comp;  // element h at cpart[2 h]
+    const double R0 = mode == 1 ? cpart[0] * scale : 0.0;
+    double acc = 0.0;
+    int cnt = 0;
     for (int64_t p = (int64_t)s * blockDim.x + threadIdx.x; p < rows; p += (int64_t)gridDim.y * blockDim.x) {
         const int kz = lo + (int)(p / side), ky = lo + (int)(p % side);
         const int64_t kzy = (int64_t)kz * kz + (int64_t)ky * ky;
         const int64_t need = lo4 - 4 * kzy, below = hi4 - 4 * kzy;  // 4 kx^2 >= need, 4 kx^2 < below
         if (below <= 0) continue;
-        int kx0 = need <= 0 ? 0 : (int)sqrt((double)need / 4.0);
-        while (kx0 > 0 && 4 * (int64_t)(kx0 - 1) * (kx0 - 1) >= need) --kx0;
-        while (4 * (int64_t)kx0 * kx0 < need) ++kx0;
-        int kx1 = (int)sqrt((double)below / 4.0);
-        while (kx1 >= 0 && 4 * (int64_t)kx1 * kx1 >= below) --kx1;
-        while (4 * (int64_t)(kx1 + 1) * (kx1 + 1) < below) ++kx1;
+        const int kx0 = need <= 0 ? 0 : isqrt_below(need) + 1;
+        int kx1 = isqrt_below(below);
         if (kx1 > half) kx1 = half;
         const int iz = kz < 0 ? kz + N : kz, iy = ky < 0 ? ky + N : ky;
+        const int64_t row = ((int64_t)iz * N + iy) * N;
         for (int kx = kx0; kx <= kx1; ++kx) {
-            const int64_t k4 = 4 * (kzy + (int64_t)kx * kx);
+            const double k2 = (double)(kzy + (int64_t)kx * kx);
             for (int sgn = 0; sgn < 2; ++sgn) {
                 int sx;
                 if (sgn == 0) sx = kx;
@@ -209,21 +244,20 @@ __global__ void k_shells(const double* __restrict__ psi, const double2* __restri
                     if (kx == 0 || kx == half) continue;  // -0 is +0; -N/2 is not in K_N
                     sx = -kx;
                 }
-                const int ix = sx < 0 ? sx + N : sx;
-                const int64_t idx = ((int64_t)iz * N + iy) * N + ix;
+                const int64_t idx = row + (sx < 0 ? sx + N : sx);
                 if (mode == 0)
-                    acc += 0.5 * (double)(k4 / 4) * psi[idx];
+                    acc = fma(k2, psi[idx], acc);
                 else
-                    acc += 2.0 * (R0 - cbuf[idx].x * scale);
-                cnt += 1.0;
+                    acc += fma(-cpart[2 * idx], scale, R0);
+                ++cnt;
             }
         }
     }
     acc = block_sum(acc, sh);
-    cnt = block_sum(cnt, sh);
+    const double count = block_sum((double)cnt, sh);
     if (threadIdx.x == 0) {
         partial[((int64_t)kap * gridDim.y + s) * 2] = acc;
-        partial[((int64_t)kap * gridDim.y + s) * 2 + 1] = cnt;
+        partial[((int64_t)kap * gridDim.y + s) * 2 + 1] = count;
     }
 }
 
@@ -237,17 +271,18 @@ __global__ void k_shell_finish(const double* __restrict__ partial, int nb, int s
             cnt += partial[((int64_t)kap * split + s) * 2 + 1];
         }
         if (mode == 0)
-            out[kap] = cnt > 0 ? 4.0 * 3.14159265358979323846 / cnt * acc * scale : 0.0;
+            out[kap] = cnt > 0 ? 4.0 * 3.14159265358979323846 / cnt * (0.5 * acc) * scale : 0.0;
         else
-            out[kap] = cnt > 0 ? acc / cnt : 0.0;
+            out[kap] = cnt > 0 ? 2.0 * acc / cnt : 0.0;
     }
 }
 
-cudaError_t shells(const mclbm_ctx* c, const double* psi, const double2* cbuf, int mode, double scale, double* out)
+cudaError_t shells(const mclbm_ctx* c, const double* psi, const double2* cbuf, int comp, int mode, double scale,
+                   double* out)
 {
     const int nb = c->N / 2 + 1;
     double* partial = (double*)(c->work + c->wl.partial);
-    k_shells<<<dim3(nb, kShellSplit), 256, 0, c->stream>>>(psi, cbuf, c->N, mode, scale, partial);
+    k_shells<<<dim3(nb, kShellSplit), 256, 0, c->stream>>>(psi, cbuf, comp, c->N, mode, scale, partial);
     k_shell_finish<<<(nb + 255) / 256, 256, 0, c->stream>>>(partial, nb, kShellSplit, mode, mode == 0 ? scale : 1.0, out);
     return cudaGetLastError();
 }
@@ -289,39 +324,67 @@ cudaError_t launch_spectral(mclbm_ctx* c, double* h_E, double* h_S2)
 {
     const int64_t n = c->n;
     const int nb = c->N / 2 + 1;
-    double* field = (double*)(c->work + c->wl.field);
+    double* field = (double*)(c->work + c->wl.field);  // [4][n]
     double2* cb = (double2*)(c->work + c->wl.cplx);
-    double* psi = (double*)(c->work + c->wl.real);
+    double* psi_a = (double*)(c->work + c->wl.real);
+    double* psi_b = (double*)(c->work + c->wl.real2);
     const double2* tw = (const double2*)(c->work + c->wl.twiddle);
     double* bins = (double*)(c->work + c->wl.bins);  // [2][M][nb]
     const double N3 = (double)n;
+    const double s6 = 1.0 / (N3 * N3);  // Phi = |u~|^2 with u~ = F(u) / N^3, so Phi = psi / N^6
+    const int gn = grid_for(n);
+    cudaStream_t st = c->stream;
     cudaError_t e;
-    for (int m = 0; m < c->M; ++m) {
-        if ((e = launch_field(c, m, field)) != cudaSuccess) return e;
-        // psi = sum_a |F(u_a)|^2: u_x and u_y share one complex transform, u_z takes one
-        k_pack_complex<<<grid_for(n), 256, 0, c->stream>>>(field, field + n, cb, n);
+    int m = 0;
+    for (; m + 1 < c->M; m += 2) {
+        // sample m at field + n (its u_z at field + 3n), then sample m + 1 at field (u_z at field + 2n)
+        if ((e = launch_field(c, m, field + n)) != cudaSuccess) return e;
+        k_pack_complex<<<gn, 256, 0, st>>>(field + n, field + 2 * n, cb, n);
         if ((e = fft3d(c, cb, tw, 0)) != cudaSuccess) return e;
-        k_accum_power_pair<<<grid_for(n), 256, 0, c->stream>>>(cb, psi, c->N, c->logN, 1);
-        k_real_to_complex<<<grid_for(n), 256, 0, c->stream>>>(field + 2 * n, cb, n);
+        k_accum_power_pair<<<gn, 256, 0, st>>>(cb, psi_a, c->N, c->logN, 1);
+        if ((e = launch_field(c, m + 1, field)) != cudaSuccess) return e;
+        k_pack_complex<<<gn, 256, 0, st>>>(field, field + n, cb, n);
         if ((e = fft3d(c, cb, tw, 0)) != cudaSuccess) return e;
-        k_accum_power<<<grid_for(n), 256, 0, c->stream>>>(cb, psi, n, 0);
-        // Phi = |u~|^2 with u~ = F(u) / N^3, so Phi = psi / N^6
-        if (h_E && (e = shells(c, psi, nullptr, 0, 1.0 / (N3 * N3), bins + (int64_t)m * nb)) != cudaSuccess) return e;
+        k_accum_power_pair<<<gn, 256, 0, st>>>(cb, psi_b, c->N, c->logN, 1);
+        k_pack_complex<<<gn, 256, 0, st>>>(field + 3 * n, field + 2 * n, cb, n);
+        if ((e = fft3d(c, cb, tw, 0)) != cudaSuccess) return e;
+        k_accum_power_split<<<gn, 256, 0, st>>>(cb, psi_a, psi_b, c->N, c->logN);
+        if (h_E) {
+            if ((e = shells(c, psi_a, nullptr, 0, 0, s6, bins + (int64_t)m * nb)) != cudaSuccess) return e;
+            if ((e = shells(c, psi_b, nullptr, 0, 0, s6, bins + (int64_t)(m + 1) * nb)) != cudaSuccess) return e;
+        }
         if (h_S2) {
-            // R = N^-3 F^-1(psi), F^-1 with the factor N^-3: R_h = re(sum_k psi_k e^{+2 pi i k.h/N}) / N^6
-            k_real_to_complex<<<grid_for(n), 256, 0, c->stream>>>(psi, cb, n);
+            // R = N^-3 F^-1(psi), F^-1 with the factor N^-3: R_h = re(sum_k psi_k e^{+2 pi i k.h/N}) / N^6;
+            // the pair's two autocorrelations are the real and imaginary parts of one inverse
+            k_pack_complex<<<gn, 256, 0, st>>>(psi_a, psi_b, cb, n);
             if ((e = fft3d(c, cb, tw, 1)) != cudaSuccess) return e;
-            if ((e = shells(c, nullptr, cb, 1, 1.0 / (N3 * N3), bins + (int64_t)(c->M + m) * nb)) != cudaSuccess)
-                return e;
+            if ((e = shells(c, nullptr, cb, 0, 1, s6, bins + (int64_t)(c->M + m) * nb)) != cudaSuccess) return e;
+            if ((e = shells(c, nullptr, cb, 1, 1, s6, bins + (int64_t)(c->M + m + 1) * nb)) != cudaSuccess) return e;
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (h_E && (e = cudaMemcpyAsync(h_E, bins, sizeof(double) * c->M * nb, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+    if (m < c->M) {  // the odd last sample: u_x + i u_y, then u_z alone
+        if ((e = launch_field(c, m, field)) != cudaSuccess) return e;
+        k_pack_complex<<<gn, 256, 0, st>>>(field, field + n, cb, n);
+        if ((e = fft3d(c, cb, tw, 0)) != cudaSuccess) return e;
+        k_accum_power_pair<<<gn, 256, 0, st>>>(cb, psi_a, c->N, c->logN, 1);
+        k_real_to_complex<<<gn, 256, 0, st>>>(field + 2 * n, cb, n);
+        if ((e = fft3d(c, cb, tw, 0)) != cudaSuccess) return e;
+        k_accum_power<<<gn, 256, 0, st>>>(cb, psi_a, n, 0);
+        if (h_E && (e = shells(c, psi_a, nullptr, 0, 0, s6, bins + (int64_t)m * nb)) != cudaSuccess) return e;
+        if (h_S2) {
+            k_real_to_complex<<<gn, 256, 0, st>>>(psi_a, cb, n);
+            if ((e = fft3d(c, cb, tw, 1)) != cudaSuccess) return e;
+            if ((e = shells(c, nullptr, cb, 0, 1, s6, bins + (int64_t)(c->M + m) * nb)) != cudaSuccess) return e;
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (h_E && (e = cudaMemcpyAsync(h_E, bins, sizeof(double) * c->M * nb, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return e;
     if (h_S2 && (e = cudaMemcpyAsync(h_S2, bins + (int64_t)c->M * nb, sizeof(double) * c->M * nb, cudaMemcpyDeviceToHost,
-                                     c->stream)) != cudaSuccess)
+                                     st)) != cudaSuccess)
         return e;
-    return cudaStreamSynchronize(c->stream);
+    return cudaStreamSynchronize(st);
 }
 
 }  // namespace mclbm

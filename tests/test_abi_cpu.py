@@ -88,8 +88,9 @@ def test_validation_errors(lib):
 def test_required_bytes(lib, prec, b, pattern, k):
     pop, work = mclbm.mclbm_required_bytes(_cfg(N=64, M=64, precision=prec, pattern=pattern))
     assert pop == k * 19 * b * 64**3 * 64
-    # statistics of one sample at a time: velocity field + complex FFT buffer + power spectrum
-    assert work >= 64**3 * (24 + 16 + 8)
+    # statistics of two samples at a time: two velocity fields (one sample's u_z kept beside the
+    # other's field) + complex FFT buffer + two power spectra
+    assert work >= 64**3 * (32 + 16 + 16)
     # 512^3 x 4 FP16 AA: 38 bytes per node
     pop, _ = mclbm.mclbm_required_bytes(_cfg(N=512, M=4, Re=6400, Ma=0.003125, precision=mclbm.FP16,
                                              pattern=mclbm.AA))
