@@ -216,8 +216,8 @@ MCLBM_API int mclbm_sf_trace(mclbm_ctx* ctx, double* S2);
  * with n in {e_x, e_y, e_z}, modulus as in Eq. (structures)):
  * S [M][pmax - 1][N/2] host FP64, p = 2..pmax (2 <= pmax <= 8), r = 1..N/2.  FP64 contexts
  * (and pmax > 6) form the differences and powers in FP64; FP32 and FP16 storage contexts, whose
- * velocity carries FP32 precision at most, form them in FP32, sum 32 points in FP32 and
- * accumulate those sums in FP64.  Synchronises. */
+ * velocity carries FP32 precision at most, form them in FP32, sum each line (32-point chunks,
+ * then the chunks) in FP32 and accumulate the line sums in FP64.  Synchronises. */
 MCLBM_API int mclbm_sf_axes(mclbm_ctx* ctx, int32_t pmax, double* S);
 
 /* Exact restriction of the physical velocity to the common Q^3 grid (node n = j N / Q,

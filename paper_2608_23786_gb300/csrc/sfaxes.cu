@@ -5,8 +5,9 @@
 // A line is the component u_a along axis a for fixed other coordinates (3 N^2
 // lines).  Each block stages L lines in shared memory; thread t owns the lag
 // r = t % (N/2) + 1 of line t / (N/2) and accumulates the p-th powers in FP64
-// over the whole line (contexts with FP32 or FP16 storage: FP32 differences and powers,
-// FP64 accumulation every 32 points), keeping its sums in registers across all batches of
+// over the whole line (contexts with FP32 or FP16 storage: FP32 differences and powers, FP32
+// sums of 32 points added up in FP32 over the line, and the line's sums accumulated in FP64),
+// keeping its sums in registers across all batches of
 // lines the block handles.  Threads with the same lag are then summed in a fixed
 // order, and a second kernel sums the blocks in a fixed order: deterministic.
 #include "internal.h"
@@ -105,9 +106,11 @@ __global__ void __launch_bounds__(kThreads) k_sf_axes(const double* __restrict__
 
 // The same sums for contexts with FP32 or FP16 storage, whose velocity field carries FP32
 // precision at most: the lines are staged in FP32, each difference and its powers (p = 2..6) are
-// formed in FP32, summed in FP32 over 32 consecutive points, and those partial sums are
-// accumulated in FP64 (the FP32 sums of 32 positive terms are within 2e-6 relative).  GB300 runs
-// FP32 at many times its FP64 rate, and this kernel is otherwise bound by the FP64 units.
+// formed in FP32 and summed in FP32 over 32 consecutive points, the chunk sums of a line are
+// added in FP32 (at most N / 32 = 16 of them), and each line's sums are accumulated in FP64.  All
+// terms are positive, so a line's FP32 sum is within (32 + 16) 2^-24 < 3e-6 relative, and the
+// FP64 units (GB300 runs FP32 at many times their rate) see 10 operations per line instead of 10
+// per 32 points.
 __global__ void __launch_bounds__(kThreads) k_sf_axes_f32(const double* __restrict__ u, int N, int logN,
                                                           double* __restrict__ partial)
 {
@@ -146,6 +149,7 @@ __global__ void __launch_bounds__(kThreads) k_sf_axes_f32(const double* __restri
         __syncthreads();
         if (active && b * L + lsub < nlines) {
             const float* Lp = line + lsub * N;
+            float l0 = 0.f, l1 = 0.f, l2 = 0.f, l3 = 0.f, l4 = 0.f;  // the line's sums
             for (int x0 = 0; x0 < N; x0 += chunk) {
                 float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
                 for (int x = x0; x < x0 + chunk; ++x) {
@@ -159,12 +163,17 @@ __global__ void __launch_bounds__(kThreads) k_sf_axes_f32(const double* __restri
                     s3 = fmaf(d4, ad, s3);
                     s4 = fmaf(d4, d2, s4);
                 }
-                acc[0] += (double)s0;
-                acc[1] += (double)s1;
-                acc[2] += (double)s2;
-                acc[3] += (double)s3;
-                acc[4] += (double)s4;
+                l0 += s0;
+                l1 += s1;
+                l2 += s2;
+                l3 += s3;
+                l4 += s4;
             }
+            acc[0] += (double)l0;
+            acc[1] += (double)l1;
+            acc[2] += (double)l2;
+            acc[3] += (double)l3;
+            acc[4] += (double)l4;
         }
     }
     __syncthreads();

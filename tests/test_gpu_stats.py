@@ -82,24 +82,43 @@ def _bins_close(got, ref, rel, floor):
     assert np.max(np.abs(got - ref)) <= rel * tot.max()
 
 
-@pytest.mark.parametrize("N", [8, 16, 32])
-def test_spectrum(N):
-    ens, u = _pair(N=N, M=2)
+# M = 3: one pair of samples sharing transforms (u_z of both in one transform, both
+# autocorrelations from one inverse) and an odd last sample with transforms of its own
+@pytest.mark.parametrize("N,M", [(8, 2), (16, 3), (32, 2)])
+def test_spectrum(N, M):
+    ens, u = _pair(N=N, M=M)
     _bins_close(ens.spectrum(), stats.energy_spectrum(u), 1e-10, 1e-12)
 
 
-def test_spectrum_tgv_closed_form():
-    """Deterministic TGV at t = 0: E(2) = 3 pi U^2 / 124 (U = U_c = 1), zero elsewhere."""
-    ens = Ensemble(16, 1, Re=100.0, Ma=0.05, precision="fp64").init_tgv()
-    E = ens.spectrum()[0]
-    assert abs(E[2] - 3 * np.pi / 124) <= 1e-12
-    assert np.all(np.abs(np.delete(E, 2)) <= 1e-14)
+@pytest.mark.parametrize("M", [1, 2])
+def test_spectrum_tgv_closed_form(M):
+    """Deterministic TGV at t = 0: E(2) = 3 pi U^2 / 124 (U = U_c = 1), zero elsewhere; with
+    M = 2 both samples come out of the paired transforms."""
+    ens = Ensemble(16, M, Re=100.0, Ma=0.05, precision="fp64").init_tgv()
+    for E in ens.spectrum():
+        assert abs(E[2] - 3 * np.pi / 124) <= 1e-12
+        assert np.all(np.abs(np.delete(E, 2)) <= 1e-14)
 
 
-@pytest.mark.parametrize("N", [8, 16, 32])
-def test_sf_trace(N):
-    ens, u = _pair(N=N, M=2)
+@pytest.mark.parametrize("N,M", [(8, 2), (16, 3), (32, 2)])
+def test_sf_trace(N, M):
+    ens, u = _pair(N=N, M=M)
     _bins_close(ens.sf_trace(), stats.structure_function_trace(u), 1e-10, 1e-12)
+
+
+def test_paired_spectra_match_single_sample_contexts():
+    """A sample's spectrum and trace S2 do not depend on the sample it is paired with: the
+    samples of a 3-sample ensemble (a pair and a single) against three one-sample contexts
+    holding the same parameters: within 1e-12 relative on bins holding at least 1e-6 of the
+    total, and 1e-12 of the total on every bin (the transforms' rounding differs between the
+    two)."""
+    X = gen.draw_params(29, 3)
+    ens = Ensemble(16, 3, Re=300.0, Ma=0.1, precision="fp64").init(X).step(12)
+    E, S = ens.spectrum(), ens.sf_trace()
+    for m in range(3):
+        one = Ensemble(16, 1, Re=300.0, Ma=0.1, precision="fp64").init(X[m:m + 1]).step(12)
+        _bins_close(E[m:m + 1], one.spectrum(), 1e-12, 1e-6)
+        _bins_close(S[m:m + 1], one.sf_trace(), 1e-12, 1e-6)
 
 
 @pytest.mark.parametrize("N,pmax", [(8, 6), (16, 6), (32, 3), (8, 8)])
@@ -143,13 +162,25 @@ def _gpu_field(ens):
     return np.stack([ens.moments(m)[1].cpu().numpy() for m in range(ens.M)])
 
 
+def test_sf_axes_fp32_line_sums_at_256():
+    """FP32 storage at N = 256 (eight 32-point chunks per line summed in FP32 before the FP64
+    accumulation): S_p, p = 2..6, at the lags 1, 37 and 128 against the oracle's FP64 evaluation
+    of the library's own velocity field, within 1e-5 relative."""
+    ens = Ensemble(256, 1, Re=1600.0, Ma=0.05, precision="fp32", seed=23).init().step(4)
+    u = _gpu_field(ens)
+    lags = [1, 37, 128]
+    got = ens.sf_axes(6)[:, :, [r - 1 for r in lags]]
+    ref = stats.structure_function_axes(u, 6, lags=lags)[:, :, [r - 1 for r in lags]]
+    assert _rel(got, ref) <= 1e-5
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
 def test_sf_axes_reduced_precision_storage(precision):
-    """FP32/FP16 storage: differences and powers in FP32, FP64 accumulation of 32-point FP32
-    sums, against the oracle's FP64 evaluation on the library's own velocity field (N = 64
-    spans two 32-point chunks per line; p = 2..6 within 1e-5 relative); pmax = 8 takes the FP64
-    path (1e-10).  The field itself matches the oracle's FP64 moments of the same populations to
-    FP32 rounding."""
+    """FP32/FP16 storage: differences and powers in FP32, FP32 line sums (of 32-point chunks)
+    accumulated in FP64, against the oracle's FP64 evaluation on the library's own velocity
+    field (N = 64 spans two 32-point chunks per line; p = 2..6 within 1e-5 relative); pmax = 8
+    takes the FP64 path (1e-10).  The field itself matches the oracle's FP64 moments of the same
+    populations to FP32 rounding."""
     ens, u = _pair(N=64, M=2, steps=20, precision=precision)
     ug = _gpu_field(ens)
     assert np.max(np.abs(ug - u)) <= 1e-6 * np.max(np.abs(u))
