@@ -14,6 +14,8 @@
 // moments.  gamma = 2/omega - (2 - 2/omega) <Ds|Dh>/<Dh|Dh> with
 // <X|Y> = sum X_i Y_i / f^eq_i; gamma = 2 (BGK) where <Dh|Dh> vanishes.
 #pragma once
+#include <type_traits>
+
 #include "lattice.cuh"
 
 namespace mclbm {
@@ -180,6 +182,33 @@ template <class F>
 __device__ __forceinline__ float map(float a, float b, F f) { return f(a, b); }
 template <class F>
 __device__ __forceinline__ float2 map(float2 a, float2 b, F f) { return make_float2(f(a.x, b.x), f(a.y, b.y)); }
+
+// The arithmetic of a collision as a policy: Asm, the PTX forms above; Native, the
+// round-to-nearest intrinsics (__fadd_rn, __fmul_rn, __fmaf_rn and the packed __fadd2_rn,
+// __fmul2_rn, __ffma2_rn of sm_100+), which round the same way and are never contracted either,
+// so both give the same bits.  They differ only in what the compiler sees (opaque assembly or the
+// operations themselves), hence in its register allocation and instruction schedule; the stepper
+// takes the one measured faster for each kernel.
+struct Asm {
+    template <class V>
+    static __device__ __forceinline__ V add(V x, V y) { return lanes::add(x, y); }
+    template <class V>
+    static __device__ __forceinline__ V mul(V x, V y) { return lanes::mul(x, y); }
+    template <class V>
+    static __device__ __forceinline__ V fma(V x, V y, V z) { return lanes::fma(x, y, z); }
+    template <class V>
+    static __device__ __forceinline__ V sub(V x, V y) { return lanes::sub(x, y); }
+};
+struct Native {
+    static __device__ __forceinline__ float add(float x, float y) { return __fadd_rn(x, y); }
+    static __device__ __forceinline__ float mul(float x, float y) { return __fmul_rn(x, y); }
+    static __device__ __forceinline__ float fma(float x, float y, float z) { return __fmaf_rn(x, y, z); }
+    static __device__ __forceinline__ float sub(float x, float y) { return __fmaf_rn(y, -1.f, x); }
+    static __device__ __forceinline__ float2 add(float2 x, float2 y) { return __fadd2_rn(x, y); }
+    static __device__ __forceinline__ float2 mul(float2 x, float2 y) { return __fmul2_rn(x, y); }
+    static __device__ __forceinline__ float2 fma(float2 x, float2 y, float2 z) { return __ffma2_rn(x, y, z); }
+    static __device__ __forceinline__ float2 sub(float2 x, float2 y) { return __ffma2_rn(y, make_float2(-1.f, -1.f), x); }
+};
 }  // namespace lanes
 
 // The shifted collision hard-codes the library velocity order: odd i and i + 1 are
@@ -199,10 +228,11 @@ constexpr bool shifted_order_holds()
 static_assert(shifted_order_holds(), "kbc_shifted assumes the library velocity order");
 
 // c_i . j for odd i (compile-time constant after unrolling)
-template <class V>
+template <class V, class Ar = lanes::Asm>
 __device__ __forceinline__ V c_dot(int i, V jx, V jy, V jz)
 {
-    using namespace lanes;
+    const auto add = [](V x, V y) { return Ar::add(x, y); };
+    const auto sub = [](V x, V y) { return Ar::sub(x, y); };
     if (cx(i) != 0 && cy(i) != 0 && cz(i) != 0) {  // corner (D3Q27)
         const V t = cy(i) > 0 ? add(jx, jy) : sub(jx, jy);
         return cz(i) > 0 ? add(t, jz) : sub(t, jz);
@@ -218,11 +248,18 @@ __device__ __forceinline__ V c_dot(int i, V jx, V jy, V jz)
 // KBC on normalised deviations h_i = f_i / w_i - 1 (in place), FP32, one node (V = float)
 // or two (V = float2).  a = 2/omega and b = 2 - 2/omega are passed in (computed once on the
 // host); the reciprocals 1/rho, 1/(1 + heq_i) and 1/hh are the hardware approximation (one
-// ulp, below the FP32 rounding already present in the sums).
-template <class V>
+// ulp, below the FP32 rounding already present in the sums).  Ar: the arithmetic policy
+// (lanes::Asm or lanes::Native, the same bits).
+template <class V, class Ar = lanes::Asm>
 __device__ __forceinline__ V kbc_shifted(V (&h)[Q], float omega, float a, float b)
 {
-    using namespace lanes;
+    using lanes::bc;
+    using lanes::map;
+    using lanes::rcp_approx;
+    const auto add = [](auto x, auto y) { return Ar::add(x, y); };
+    const auto mul = [](auto x, auto y) { return Ar::mul(x, y); };
+    const auto fma = [](auto x, auto y, auto z) { return Ar::fma(x, y, z); };
+    const auto sub = [](auto x, auto y) { return Ar::sub(x, y); };
     const V one = bc<V>(1.f), W0 = bc<V>(1.0f / 3.0f), W1 = bc<V>(1.0f / 18.0f), W2 = bc<V>(1.0f / 36.0f);
     const auto frcp = [](float x) { return rcp_approx(x); };
     // density deviation and momentum: sum w h, sum w c h (d_p: difference of pair p)
@@ -248,7 +285,7 @@ __device__ __forceinline__ V kbc_shifted(V (&h)[Q], float omega, float a, float 
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
         const int i = 2 * p + 1;
-        const V cj = c_dot(i, jx, jy, jz);
+        const V cj = c_dot<V, Ar>(i, jx, jy, jz);
         const V q = fma(rinv, fma(bc<V>(4.5f), mul(cj, cj), jj15), drho);
         heq[i] = fma(bc<V>(3.f), cj, q);
         heq[i + 1] = fma(bc<V>(-3.f), cj, q);
@@ -303,7 +340,7 @@ __device__ __forceinline__ V kbc_shifted(V (&h)[Q], float omega, float a, float 
     const V se = fma(D[3], sub(A[3], A[4]), fma(D[4], sub(A[5], A[6]), mul(D[5], sub(A[7], A[8]))));
     const V sh = fma(bc<V>(0.5f), sf, mul(bc<V>(1.0f / 144.0f), se));
     const V hh = fma(W0, mul(kr0, k[0]), fma(W1, hf, mul(W2, he)));
-    const V gamma = map(hh, sh, [a, b](float hs, float ss) {
+    const V gamma = map(hh, sh, [a, b, fma, mul](float hs, float ss) {
         return hs <= kHHGuard ? 2.0f : fma(-b, mul(ss, rcp_approx(hs)), a);
     });
     // f* = f - omega Ds - (omega gamma / 2) Dh, written as f^eq + (1 - omega) Ds + (1 - beta) Dh so
@@ -336,9 +373,11 @@ constexpr bool d3q27_order_holds()
 }
 static_assert(d3q27_order_holds(), "kbc_shifted assumes the library's D3Q27 corner order");
 
-template <class V>
+// (Ar: accepted for a uniform call; this form is written in the Asm arithmetic.)
+template <class V, class Ar = lanes::Asm>
 __device__ __forceinline__ V kbc_shifted(V (&h)[Q], float omega, float a, float b)
 {
+    static_assert(std::is_same<Ar, lanes::Asm>::value, "the D3Q27 collision takes the Asm arithmetic");
     using namespace lanes;
     const V one = bc<V>(1.f);
     const V W0 = bc<V>(8.0f / 27.0f), W1 = bc<V>(2.0f / 27.0f), W2 = bc<V>(1.0f / 54.0f), W3 = bc<V>(1.0f / 216.0f);

@@ -138,6 +138,11 @@ __global__ void __launch_bounds__(BLOCK) k_step_async(const BatchArgs<E> args)
     static_assert(sizeof(E) == 4 || VEC % 2 == 0, "FP16 runs must be whole 4-byte words");
     using C = typename Storage<E>::compute;
     using Ring = AsyncRing<E, VEC, BLOCK, STAGES>;
+    // the D3Q19 FP16 AA even step collides with the intrinsic arithmetic (the same bits; its
+    // schedule measured 86.7% -> 89.9% of the copy bandwidth at 128^3 x 32, while the other
+    // kernels keep the assembly form, which measured faster for them: FP16 AA odd 81.2% against
+    // 78.1%, FP32 pull 99.5% against 99.1%)
+    using Arith = std::conditional_t<Q == 19 && std::is_same<E, __half>::value && FIX == 1, lanes::Native, lanes::Asm>;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int64_t total = args.prefix[args.nlev];
@@ -179,7 +184,7 @@ __global__ void __launch_bounds__(BLOCK) k_step_async(const BatchArgs<E> args)
         const Geom g = L.g;
         C v[Q][VEC];
         async_finish_all<E, VEC, BLOCK, STAGES, FIX, WRAP>(smem, stage, threadIdx.x, g, cur, lane, v);
-        collide_run<E, VEC, (VEC % 2 == 0)>(v, L);
+        collide_run<E, VEC, (VEC % 2 == 0), false, Arith>(v, L);
         E* base = L.dst + (int64_t)cur.m * Q * g.n;
         const int mode = FIX >= 0 ? FIX : cur.mode;
         if (mode == 0)

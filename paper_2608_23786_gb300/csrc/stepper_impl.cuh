@@ -268,8 +268,8 @@ __device__ __forceinline__ void scatter_row(E* run, int x0, int N, int lane, con
 
 // Collide the VEC nodes of a run.  PACK (shifted storage, VEC even) runs the FP32
 // collision on node pairs in the packed FP32 pipe; the results are bit-identical to the
-// one-node form.
-template <class E, int VEC, bool PACK = false, bool EXACT = false>
+// one-node form.  Ar: the arithmetic policy of the shifted collision (same bits either way).
+template <class E, int VEC, bool PACK = false, bool EXACT = false, class Ar = lanes::Asm>
 __device__ __forceinline__ void collide_run(typename Storage<E>::compute (&v)[Q][VEC], const LevelArgs<E>& L)
 {
     const typename Storage<E>::compute omega = omega_of<E>(L);
@@ -291,7 +291,7 @@ __device__ __forceinline__ void collide_run(typename Storage<E>::compute (&v)[Q]
             float2 t[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) t[i] = make_float2(v[i][k], v[i][k + 1]);
-            kbc_shifted<float2>(t, omega, L.a32, L.b32);
+            kbc_shifted<float2, Ar>(t, omega, L.a32, L.b32);
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 v[i][k] = t[i].x;
@@ -305,7 +305,7 @@ __device__ __forceinline__ void collide_run(typename Storage<E>::compute (&v)[Q]
 #pragma unroll
             for (int i = 0; i < Q; ++i) t[i] = v[i][k];
             if constexpr (Storage<E>::shifted)
-                kbc_shifted<float>(t, omega, L.a32, L.b32);
+                kbc_shifted<float, Ar>(t, omega, L.a32, L.b32);
             else
                 kbc_raw(t, omega);
 #pragma unroll
