@@ -225,6 +225,11 @@ __global__ void __launch_bounds__(kRunBlock) k_adjoint_async(const E* __restrict
                                                              float omega, float a, float b)
 {
     static_assert(VEC == 2, "node pairs");
+    // the D3Q27 FP32 transposed collision takes the intrinsic arithmetic (the same bits; its
+    // schedule measured 89.5% -> 92.6% of the copy bandwidth for the reverse sweep at 64^3 x 16);
+    // the D3Q19 one and the FP16-state kernels keep the assembly form (FP16 state: 85.2% against
+    // 82.1% for D3Q19, 89.6% against 82.0% for D3Q27)
+    using Arith = std::conditional_t<Q == 27 && std::is_same<E, float>::value, lanes::Native, lanes::Asm>;
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
     const int lane = threadIdx.x & 31;
@@ -264,7 +269,7 @@ __global__ void __launch_bounds__(kRunBlock) k_adjoint_async(const E* __restrict
             h2[i] = make_float2(hv[i][0], hv[i][1]);
             m2[i] = make_float2(mv[i][0], mv[i][1]);
         }
-        kbc_vjp_shifted<float2>(h2, m2, omega, a, b, l2);
+        kbc_vjp_shifted<float2, Arith>(h2, m2, omega, a, b, l2);
         float* lo = lam_out + (int64_t)p.m * Q * g.n + p.node;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {

@@ -190,10 +190,11 @@ __device__ __forceinline__ void kbc_vjp(const T (&h)[Q], const T (&mu)[Q], T ome
 // and a pair (c, -c) contributes 3 w [(nq_+ - nq_-) + 3 (c . u)(nq_+ + nq_-)] c - 3 w u (nq_+ + nq_-)
 // to NV.  Forward quantities are those of kbc_shifted (same operations up to k); gamma = 2 and
 // no dgamma where <Dh|Dh> is at or below kHHGuard.
-template <class V>
+template <class V, class Ar = lanes::Asm>
 __device__ __forceinline__ void kbc_vjp_shifted(const V (&h)[Q], const V (&mu)[Q], float omega, float a, float b,
                                                 V (&lam)[Q])
 {
+    static_assert(std::is_same<Ar, lanes::Asm>::value, "the D3Q19 transposed collision takes the Asm arithmetic");
     using namespace lanes;
     const V one = bc<V>(1.f), W0 = bc<V>(1.0f / 3.0f), W1 = bc<V>(1.0f / 18.0f), W2 = bc<V>(1.0f / 36.0f);
     const auto frcp = [](float x) { return rcp_approx(x); };
@@ -378,11 +379,17 @@ __device__ __forceinline__ void kbc_vjp_shifted(const V (&h)[Q], const V (&mu)[Q
 // coefficients are written through kr_j = k_j / (1 + heq_j) (k dies after the forward sums):
 // gh_j = -beta mu_j + 2 c2 kr_j + c1s_j ie_j, ng_j = kr_j (c2 kr_j + c1s_j ie_j), and each
 // velocity keeps only u_j = mu_j + gh_j (for lambda) and v_j = ng_j + gh_j (for the chain).
-template <class V>
+template <class V, class Ar = lanes::Asm>
 __device__ __forceinline__ void kbc_vjp_shifted(const V (&h)[Q], const V (&mu)[Q], float omega, float a, float b,
                                                 V (&lam)[Q])
 {
-    using namespace lanes;
+    using lanes::bc;
+    using lanes::map;
+    using lanes::rcp_approx;
+    const auto add = [](auto x, auto y) { return Ar::add(x, y); };
+    const auto mul = [](auto x, auto y) { return Ar::mul(x, y); };
+    const auto fma = [](auto x, auto y, auto z) { return Ar::fma(x, y, z); };
+    const auto sub = [](auto x, auto y) { return Ar::sub(x, y); };
     const V one = bc<V>(1.f);
     const V W0 = bc<V>(8.0f / 27.0f), W1 = bc<V>(2.0f / 27.0f), W2 = bc<V>(1.0f / 54.0f), W3 = bc<V>(1.0f / 216.0f);
     const auto frcp = [](float x) { return rcp_approx(x); };
@@ -413,7 +420,7 @@ __device__ __forceinline__ void kbc_vjp_shifted(const V (&h)[Q], const V (&mu)[Q
 #pragma unroll
     for (int p = 0; p < 13; ++p) {
         const int i = 2 * p + 1;
-        const V cj = c_dot(i, jx, jy, jz);
+        const V cj = c_dot<V, Ar>(i, jx, jy, jz);
         const V q = fma(rinv, fma(bc<V>(4.5f), mul(cj, cj), jj15), drho);
         const V ha = fma(bc<V>(3.f), cj, q), hb = fma(bc<V>(-3.f), cj, q);
         eh[i] = add(one, ha);
@@ -483,7 +490,7 @@ __device__ __forceinline__ void kbc_vjp_shifted(const V (&h)[Q], const V (&mu)[Q
     const V ihh = map(hh, [](float x) { return x > kHHGuard ? rcp_approx(x) : 0.f; });
     const V R2 = mul(sh, ihh);
     const V R1 = mul(mk, ihh);
-    const V gamma = map(hh, R2, [a, b](float x, float r2) { return x > kHHGuard ? fma(-b, r2, a) : 2.0f; });
+    const V gamma = map(hh, R2, [a, b, fma](float x, float r2) { return x > kHHGuard ? fma(-b, r2, a) : 2.0f; });
     const V nbeta = mul(bc<V>(-0.5f * omega), gamma);
     const V c1 = mul(bc<V>(0.5f * omega * b), R1);
     const V c2 = mul(c1, mul(bc<V>(-1.f), R2));
@@ -557,7 +564,7 @@ __device__ __forceinline__ void kbc_vjp_shifted(const V (&h)[Q], const V (&mu)[Q
         const V nqa = add(v[i], at), nqb = add(v[i + 1], at);
         const V ep = fma(nqb, eh[i + 1], mul(nqa, eh[i]));
         const V sg = add(nqa, nqb);
-        const V w = fma(sg, mul(c_dot(i, jx, jy, jz), rinv3), sub(nqa, nqb));
+        const V w = fma(sg, mul(c_dot<V, Ar>(i, jx, jy, jz), rinv3), sub(nqa, nqb));
         if (p < 3) {
             ef = p == 0 ? ep : add(ef, ep);
             sgf = p == 0 ? sg : add(sgf, sg);
@@ -591,7 +598,7 @@ __device__ __forceinline__ void kbc_vjp_shifted(const V (&h)[Q], const V (&mu)[Q
     for (int p = 0; p < 13; ++p) {
         const int i = 2 * p + 1;
         const V at = at_of(p);
-        const V cN = c_dot(i, NVx, NVy, NVz);
+        const V cN = c_dot<V, Ar>(i, NVx, NVy, NVz);
         lam[i] = add(add(u[i], at), sub(base, cN));
         lam[i + 1] = add(add(u[i + 1], at), add(base, cN));
     }
