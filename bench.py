@@ -142,8 +142,8 @@ def oracle_sample(wl, budget_s=10.0, max_samples=2):
     stats.mean_var(up)
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    desc = (f"{max_samples} of {wl['M']} samples x {steps} of {wl['updates_per_step']} updates of "
-            f"{wl['N']}^3, then E(t) and mean/var; FP64 C oracle, OpenMP over planes")
+    desc = (f"{max_samples} of {wl['M']} samples x {steps} updates of {wl['N']}^3 (a step of the workload is "
+            f"{wl['updates_per_step']} updates), then E(t) and mean/var; FP64 C oracle, OpenMP over planes")
     return lu / dt / 1e9, desc, cores
 
 
