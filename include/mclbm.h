@@ -124,7 +124,8 @@ MCLBM_API int mclbm_compute_units(const mclbm_config* cfg, mclbm_units* out);
 
 /* Bytes of caller-allocated device memory a configuration needs:
  * pop_bytes for the population lattice(s), work_bytes for reductions and
- * statistics (velocity field, FFT buffers, partial sums of one sample at a time).
+ * statistics (the velocity fields and power spectra of two samples at a time, the FFT
+ * buffer, partial sums).
  * Errors: INVALID_ARG, SHAPE, UNSTABLE_TAU. */
 MCLBM_API int mclbm_required_bytes(const mclbm_config* cfg, size_t* pop_bytes, size_t* work_bytes);
 

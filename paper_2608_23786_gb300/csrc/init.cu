@@ -47,6 +47,9 @@ __global__ void k_trig_tables(double* t, int N)
 // then consecutive threads take consecutive nodes, so every population's stores are coalesced.
 constexpr int kInitChunk = 2048;
 
+// Row factors, with U_lat / U_c and the 1/8 of the perturbation folded in: along the row,
+// u_x = ux_yz sin x + B[0][0] sin 2x + B[0][1] cos 2x, u_y = uy_yz cos x + B[1][0] sin 2x +
+// B[1][1] cos 2x, u_z = B[2][0] sin 2x + B[2][1] cos 2x.
 struct InitRow {
     double B[3][2];
     double ux_yz, uy_yz, dr_yz, c2y;
@@ -87,10 +90,10 @@ __global__ void __launch_bounds__(kBlock) k_init(E* __restrict__ lat, Geom g, in
                     for (int j = 0; j < 2; ++j)
 #pragma unroll
                         for (int k = 0; k < 2; ++k) bsum = fma(Xm[8 * al + 4 * i + 2 * j + k], P[j][k], bsum);
-                    ir.B[al][i] = bsum;
+                    ir.B[al][i] = 0.125 * sc * bsum;
                 }
-            ir.ux_yz = uc * cyy * czz;  // u_det = (ux_yz sin x, uy_yz cos x, 0)
-            ir.uy_yz = -uc * sy * czz;
+            ir.ux_yz = sc * (uc * cyy * czz);  // u_det = (ux_yz sin x, uy_yz cos x, 0)
+            ir.uy_yz = sc * (-uc * sy * czz);
             ir.dr_yz = 3.0 * (ulat * ulat / 16.0) * (c2z + 2.0);
             ir.c2y = c2y;
             rows[r] = ir;
@@ -101,9 +104,10 @@ __global__ void __launch_bounds__(kBlock) k_init(E* __restrict__ lat, Geom g, in
             decode(g, c0 + q, m, x, y, z);
             const InitRow& ir = rows[q >> g.logN < rows_per_chunk ? q >> g.logN : 0];
             const double sx = trig[4 * x], cxx = trig[4 * x + 1], s2x = trig[4 * x + 2], c2x = trig[4 * x + 3];
-            double u[3] = {ir.ux_yz * sx, ir.uy_yz * cxx, 0.0};
-#pragma unroll
-            for (int al = 0; al < 3; ++al) u[al] = fma(fma(s2x, ir.B[al][0], c2x * ir.B[al][1]), 0.125, u[al]) * sc;
+            // three FP64 operations per component (the row factors carry U_lat / U_c and 1/8)
+            const double u[3] = {fma(sx, ir.ux_yz, fma(s2x, ir.B[0][0], c2x * ir.B[0][1])),
+                                 fma(cxx, ir.uy_yz, fma(s2x, ir.B[1][0], c2x * ir.B[1][1])),
+                                 fma(s2x, ir.B[2][0], c2x * ir.B[2][1])};
             const double drho = density_mode == 1 ? ir.dr_yz * (c2x + ir.c2y) : 0.0;
             E* base = lat + (int64_t)m * Q * g.n;
             if constexpr (Storage<E>::shifted) {
