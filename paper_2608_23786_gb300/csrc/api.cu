@@ -225,7 +225,7 @@ WorkLayout work_layout(int N, int M)
     wl.real = take(n * sizeof(double) > sfb ? n * sizeof(double) : sfb);
     wl.real2 = take(n * sizeof(double));
     wl.twiddle = take((size_t)(N / 2) * 2 * sizeof(double));
-    wl.trig = take((size_t)N * 4 * sizeof(double));
+    wl.trig = take((size_t)N * 4 * (sizeof(double) + sizeof(float)));  // FP64 table, then its FP32 copy
     size_t per = 2 * (size_t)(N / 2 + 1);
     if ((size_t)7 * (N / 2) > per) per = (size_t)7 * (N / 2);
     wl.bins = take((size_t)M * per * sizeof(double) + 2 * (size_t)M * sizeof(double));
