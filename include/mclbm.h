@@ -194,14 +194,17 @@ MCLBM_API int mclbm_energy(mclbm_ctx* ctx, double* E, double* Z);
 /* Ensemble mean and unbiased (M - 1) variance of the physical velocity at every
  * node (Eqs. (spectrum_mean), (spectrum_var) applied pointwise): d_mean, d_var
  * device FP64 [3][N^3], from one pass over the samples that accumulates, per node, the sums
- * of u_m - u_0 and of its square in FP64 (u_m formed as the stepper's moments).  Errors: SHAPE
- * if M < 2.  Enqueued only. */
+ * of u_m - u_0 and of its square in FP64 (u_m formed as the stepper's moments; with FP32 or FP16
+ * storage, whose velocity carries FP32 rounding at best, these sums are formed in FP32 over
+ * chunks of 8 samples and the chunks accumulated in FP64).  Errors: SHAPE if M < 2.
+ * Enqueued only. */
 MCLBM_API int mclbm_mean_var(mclbm_ctx* ctx, double* d_mean, double* d_var);
 
 /* mclbm_energy and mclbm_mean_var in one pass over the populations (each population is read
- * once for both): E [M] host FP64 (the kinetic energy of every sample, as mclbm_energy; the
- * sums are taken in another fixed order, so the last bits may differ), d_mean / d_var as
- * mclbm_mean_var.  Synchronises.  Errors: INVALID_ARG, SHAPE (M < 2). */
+ * once for both): E [M] host FP64 (the kinetic energy of every sample, as mclbm_energy, the
+ * sums taken in another fixed order; with FP32 or FP16 storage each warp's sum of |u|^2 is
+ * formed in FP32 before its FP64 accumulation, within about 1e-6 relative of mclbm_energy),
+ * d_mean / d_var as mclbm_mean_var.  Synchronises.  Errors: INVALID_ARG, SHAPE (M < 2). */
 MCLBM_API int mclbm_energy_mean_var(mclbm_ctx* ctx, double* E, double* d_mean, double* d_var);
 
 /* Shell energy spectrum (Eqs. (dftCoeff), (energySpecDisc)) of every sample:

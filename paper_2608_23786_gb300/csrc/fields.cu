@@ -151,10 +151,16 @@ __global__ void k_reduce_rows(const double* __restrict__ partial, int rows, int 
 // (slot opp(i) of x - c_i).  The moments are formed in the storage's compute type, as the
 // stepper's.  Per node the sums of d_m = u_m - u_0 and d_m^2 (m >= 1) are accumulated in FP64
 // (one-pass variance about the first sample: mean = u_0 + S1 / M, var = (S2 - S1^2 / M) / (M - 1),
-// free of the cancellation of raw sums because d is of the size of the spread).  WANT_E: each
-// sample's sum of |u|^2 over the run is reduced across the warp in FP64 and accumulated per warp
-// in shared memory, then per block in a fixed order: partial[m][block].
+// free of the cancellation of raw sums because d is of the size of the spread), from partial sums
+// over chunks of kSampleChunk samples in the compute type.  WANT_E: each sample's sum of |u|^2
+// over the run is reduced across the warp in the compute type and accumulated per warp in FP64 in
+// shared memory, then per block in a fixed order: partial[m][block].  For FP32 and FP16 storage,
+// whose velocity carries FP32 rounding at best, the FP32 partial sums (at most 8 samples, or a
+// warp's 64 squares: within 5e-7 relative for the positive terms) leave about one FP64
+// operation per node and sample, and the pass runs at memory speed rather than at the rate of
+// GB300's FP64 units.
 constexpr int kRunVec = 2;
+constexpr int kSampleChunk = 8;
 
 template <class E, int MODE>
 __device__ __forceinline__ void gather_run(const E* base, const Geom& g, int x0, int y, int z,
@@ -191,16 +197,20 @@ __global__ void __launch_bounds__(kBlock) k_stats_pass(const E* __restrict__ lat
     }
     const int64_t runs = g.n / kRunVec;
     const double invM = 1.0 / M;
+    const double vscale = M > 1 ? uscale * uscale / (M - 1) : 0.0;  // var = (S2 - S1^2 / M) uscale^2 / (M - 1)
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < runs; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t node = t * kRunVec;
         int x0, y, z;
         xyz_of(g, node, x0, y, z);
-        C u0[3][kRunVec];
+        C u0[3][kRunVec], p1[3][kRunVec], p2[3][kRunVec];
         double s1[3][kRunVec], s2[3][kRunVec];
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
-            for (int k = 0; k < kRunVec; ++k) s1[a][k] = s2[a][k] = 0.0;
+            for (int k = 0; k < kRunVec; ++k) {
+                s1[a][k] = s2[a][k] = 0.0;
+                p1[a][k] = p2[a][k] = C(0);
+            }
         for (int m = 0; m < M; ++m) {
             C f[Q][kRunVec];
             gather_run<E, MODE>(lat + (int64_t)m * Q * g.n, g, x0, y, z, f);
@@ -224,18 +234,32 @@ __global__ void __launch_bounds__(kBlock) k_stats_pass(const E* __restrict__ lat
                 for (int a = 0; a < 3; ++a) {
                     if (m == 0) {
                         u0[a][k] = u[a];
-                    } else {
-                        const double d = (double)(u[a] - u0[a][k]);
+                    } else if constexpr (std::is_same<C, double>::value) {  // FP64 storage: directly
+                        const double d = u[a] - u0[a][k];
                         s1[a][k] += d;
                         s2[a][k] = fma(d, d, s2[a][k]);
+                    } else {
+                        const C d = u[a] - u0[a][k];
+                        p1[a][k] += d;
+                        p2[a][k] = fma(d, d, p2[a][k]);
                     }
                 }
             }
-            if constexpr (WANT_E) {
-                double es = (double)e;
+            // the chunk's partial sums into the FP64 ones (after samples 8, 16, ... and the last)
+            if (!std::is_same<C, double>::value && m > 0 && (m % kSampleChunk == 0 || m == M - 1)) {
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) es += __shfl_xor_sync(0xffffffffu, es, o);
-                if (lane == 0) ered[m * nw + warp] += es;
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int k = 0; k < kRunVec; ++k) {
+                        s1[a][k] += (double)p1[a][k];
+                        s2[a][k] += (double)p2[a][k];
+                        p1[a][k] = p2[a][k] = C(0);
+                    }
+            }
+            if constexpr (WANT_E) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+                if (lane == 0) ered[m * nw + warp] += (double)e;
             }
         }
 #pragma unroll
@@ -243,7 +267,7 @@ __global__ void __launch_bounds__(kBlock) k_stats_pass(const E* __restrict__ lat
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 mean[a * g.n + node + k] = fma(s1[a][k], invM, (double)u0[a][k]) * uscale;
-                var[a * g.n + node + k] = M > 1 ? fma(-s1[a][k] * invM, s1[a][k], s2[a][k]) / (M - 1) * uscale * uscale : 0.0;
+                var[a * g.n + node + k] = fma(-s1[a][k] * invM, s1[a][k], s2[a][k]) * vscale;
             }
     }
     if constexpr (WANT_E) {
@@ -344,7 +368,6 @@ cudaError_t energy_t(mclbm_ctx* c, bool with_z, double* h_E, double* h_Z)
 }
 
 constexpr int kStatsBlocks = 152 * 6;  // persistent grid of the statistics pass (fixed: deterministic sums)
-constexpr int kStatsMaxM = 1024;        // samples whose energies the pass reduces in shared memory
 
 template <class E>
 cudaError_t stats_pass_t(const mclbm_ctx* c, double* d_mean, double* d_var, double* h_E)

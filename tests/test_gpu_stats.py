@@ -64,6 +64,26 @@ def test_mean_var():
     np.testing.assert_allclose(var.cpu().numpy(), ov, rtol=1e-9, atol=1e-18)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_mean_var_reduced_precision_storage_chunks(precision):
+    """FP32/FP16 storage: the per-node differences to sample 0 and their squares summed in FP32
+    over chunks of 8 samples, the chunks accumulated in FP64.  M = 11 spans a full chunk and a
+    partial one; against NumPy's FP64 mean and variance of the library's own velocity field (whose
+    FP32 velocities divide where the pass multiplies by a reciprocal: a few ulp apart, about 1e-5
+    of the sample-to-sample differences): mean within 1e-6 of the velocity scale, variance within
+    2e-4 relative where it holds at least 1e-3 of its maximum; E against the library's own FP64
+    energy reduction within 2e-6.  A chunk flushed twice or not at all would be off by O(1/M)."""
+    ens = Ensemble(16, 11, Re=300.0, Ma=0.1, precision=precision, seed=21).init().step(12)
+    u = _gpu_field(ens)
+    E, mean, var = ens.energy_mean_var()
+    rm, rv = stats.mean_var(u)
+    mean, var = mean.cpu().numpy(), var.cpu().numpy()
+    assert np.max(np.abs(mean - rm)) <= 1e-6 * np.max(np.abs(u))
+    big = rv >= 1e-3 * rv.max()
+    assert np.max(np.abs(var - rv)[big] / rv[big]) <= 2e-4
+    assert _rel(E, ens.energy()) <= 2e-6
+
+
 def test_mean_var_needs_two_samples():
     ens = Ensemble(8, 1, Re=100.0, Ma=0.1, precision="fp32").init()
     with pytest.raises(mclbm.MclbmError) as e:
