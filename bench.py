@@ -926,20 +926,31 @@ def main():
     value = lu_per_rank * world / elapsed / 1e9
 
     # ---- end to end through the public API with host buffers: params H2D from pinned memory,
-    # init + S updates + reductions, E and the mean/var fields D2H every step
+    # init + S updates + reductions, E and the mean/var fields D2H every step.  The fields of step
+    # k travel to the host on a copy stream while step k + 1 computes (two device buffers, each
+    # reused only after its copy has finished); E comes back inside the reduction call.
     params_h = torch.from_numpy(X.copy()).pin_memory()
     E_h = torch.empty(wl["M"], dtype=torch.float64).pin_memory()
-    mv_h = torch.empty((2, 3) + (wl["N"],) * 3, dtype=torch.float64).pin_memory()
+    mv_h = torch.empty((2, 2, 3) + (wl["N"],) * 3, dtype=torch.float64).pin_memory()
+    mv_d = torch.empty((2, 2, 3) + (wl["N"],) * 3, dtype=torch.float64, device=dev)
+    copy_stream = torch.cuda.Stream(dev)
+    copied = [None, None]  # event: the copy out of buffer b has finished
+    e2e_k = [0]
 
     def e2e_step():
+        b = e2e_k[0] & 1
+        e2e_k[0] += 1
+        if copied[b] is not None:
+            copied[b].synchronize()
         mclbm.mclbm_init_ensemble(ens.ctx, params_h.numpy())  # host parameters, H2D inside the call
         mclbm.mclbm_step(ens.ctx, S)
         e = np.zeros(wl["M"])
-        mclbm.mclbm_energy_mean_var(ens.ctx, e, mean.data_ptr(), var.data_ptr())
+        mclbm.mclbm_energy_mean_var(ens.ctx, e, mv_d[b, 0].data_ptr(), mv_d[b, 1].data_ptr())  # synchronises
         E_h.copy_(torch.from_numpy(e))
-        mv_h[0].copy_(mean, non_blocking=True)
-        mv_h[1].copy_(var, non_blocking=True)
-        stream.synchronize()
+        with torch.cuda.stream(copy_stream):
+            mv_h[b].copy_(mv_d[b], non_blocking=True)
+            copied[b] = torch.cuda.Event()
+            copied[b].record(copy_stream)
 
     e2e_steps = max(2, args.steps // 4)
     if args.no_e2e:
@@ -950,6 +961,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         e2e_step()
+    copy_stream.synchronize()  # the last step's fields are on the host
     torch.cuda.synchronize()
     e2e_dt = max(time.perf_counter() - t0, 1e-9)
     if world > 1:
@@ -1056,7 +1068,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": None if args.no_e2e else {"value": e2e_value, "unit": "GLUPS",
                                          "h2d_bytes_per_step": int(params_h.numel() * 8),
-                                         "d2h_bytes_per_step": int(E_h.numel() * 8 + mv_h.numel() * 8)},
+                                         "d2h_bytes_per_step": int(E_h.numel() * 8 + mv_h[0].numel() * 8)},
         "gpu_launches": kernels_per_step * args.steps,
         "fp64_plain_single_sample": dict({"value": plain_glups, "unit": "GLUPS", "N": wl["N"], "M": 1},
                                          **(plain_ratio or {})),
