@@ -464,6 +464,67 @@ def run_precision(args):
     print(json.dumps(res))
 
 
+def run_precision_large(args):
+    """The error per observable at 512^3 x 4 RTGV samples (Re 6400, Ma 0.003125, 200 steps): FP16 and
+    FP32 shifted storage with in-place AA streaming against the plain FP64 GPU stepper (AA) on the
+    same samples: kinetic energy, velocity field (relative L2, formed on the GPU), E(kappa), trace
+    S_2, S_p along the axes (p = 2..6), mean and variance fields, and the one-point W1 against a
+    256^3 x 8 level (Re 3200, Ma 0.00625, 50 steps: the same physical time under diffusive scaling;
+    FP64), as the relative change of that distance against the FP64 512^3 law's."""
+    import torch
+    from paper_2608_23786_gb300 import Ensemble, mclbm
+    import ensemble_inputs as gen
+    mclbm.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    N, M, Re, Ma, T = 512, 4, 6400.0, 0.003125, 200
+    X = gen.draw_params(5, M)
+    t0 = time.perf_counter()
+    lev = Ensemble(256, 8, Re=3200.0, Ma=0.00625, precision="fp64", pattern="aa", seed=6, device=dev,
+                   stream=stream).init(gen.draw_params(6, 8)).step(T // 4)
+    r256 = lev.restrict(8).cpu().numpy()
+    del lev
+    torch.cuda.empty_cache()
+
+    def w1_vs_level(e):
+        da, db = e.restrict(8), torch.as_tensor(r256, device=dev)
+        nb = mclbm.mclbm_w1_work_bytes(M, r256.shape[0], da.shape[1])
+        work = torch.empty(nb, dtype=torch.uint8, device=dev)
+        return mclbm.mclbm_w1_restricted(da.data_ptr(), M, db.data_ptr(), r256.shape[0], da.shape[1],
+                                         work.data_ptr(), nb, stream.cuda_stream)
+
+    def observe(prec):
+        e = Ensemble(N, M, Re=Re, Ma=Ma, precision=prec, pattern="aa", seed=5, device=dev,
+                     stream=stream).init(X).step(T)
+        o = {"ke": e.energy(), "spectrum": e.spectrum(), "s2": e.sf_trace(), "sp": e.sf_axes(6)}
+        _, o["mean"], o["var"] = e.energy_mean_var()
+        o["u"] = [e.moments(m)[1] for m in range(M)]  # device tensors
+        o["w1"] = w1_vs_level(e)
+        del e
+        torch.cuda.empty_cache()
+        return o
+
+    def l2(a, b):
+        return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+    ref = observe("fp64")
+    table = {}
+    for prec in ("fp16", "fp32"):
+        o = observe(prec)
+        err = _precision_errors({k: o[k] for k in ("ke", "spectrum", "s2", "sp")},
+                                {k: ref[k] for k in ("ke", "spectrum", "s2", "sp")})
+        err["u_l2"] = max(l2(a, b) for a, b in zip(o["u"], ref["u"]))
+        err["mean_l2"], err["var_l2"] = l2(o["mean"], ref["mean"]), l2(o["var"], ref["var"])
+        err["w1_vs_256_level"] = abs(o["w1"] - ref["w1"]) / ref["w1"]
+        table[f"{prec}_aa"] = err
+        del o
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "precision_errors", "unit": "relative error against the FP64 GPU run",
+                      "rtgv_512cube_x4_200steps": {"errors": table, "w1_vs_256_level_fp64": ref["w1"],
+                                                   "seconds": time.perf_counter() - t0}}))
+
+
 def run_reference(args, wl):
     """Reference arm: the FP64 oracle timed on the host cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -807,10 +868,12 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="let the library's autotuner pick the launch shape")
     ap.add_argument("--workload", default="ensemble64",
                     choices=["ensemble64", "levels_fp32", "levels_fp16", "large", "adjoint", "oracle_report",
-                             "peaks", "stats", "w1_2pt", "precision"],
+                             "peaks", "stats", "w1_2pt", "precision", "precision_large"],
                     help="ensemble64 (default): 64^3 x 64 FP32; levels_*: 3-level batch; large: 512^3 x 4 FP16 AA; "
                          "adjoint: gradient of E(T), 64^3 x 16, 500 steps; oracle_report: the oracle on cfg1/cfg2 "
-                         "(all cores and one core), its statistics per snapshot, and the GPU on cfg1")
+                         "(all cores and one core), its statistics per snapshot, and the GPU on cfg1; precision / "
+                         "precision_large: FP32 and FP16 storage against the FP64 GPU run per observable (128^3 x 32 "
+                         "and the three-level batch / 512^3 x 4)")
     ap.add_argument("--T", type=int, default=500, help="adjoint horizon (steps) of --workload adjoint")
     ap.add_argument("--Q", type=int, default=8, help="restriction grid Q^3 of --workload w1_2pt")
     ap.add_argument("--oracle-child", default=None, choices=["all", "one"], help=argparse.SUPPRESS)
@@ -835,6 +898,8 @@ def main():
         return run_w1_2pt(args)
     if args.workload == "precision":
         return run_precision(args)
+    if args.workload == "precision_large":
+        return run_precision_large(args)
     wl = dict(WORKLOAD)
     if args.N or args.M:
         wl["N"] = args.N or wl["N"]
