@@ -216,9 +216,9 @@ __device__ __forceinline__ void consume_tile(const StagedArgs<E>& a, const TileC
 template <class E, int PATTERN, int VEC>
 __global__ void __launch_bounds__(kStagedThreads) k_step_staged(const StagedArgs<E> a)
 {
-    extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);  // [stages] full, [stages] empty
-    E* stage0 = reinterpret_cast<E*>(smem + 256);
+    extern __shared__ __align__(128) unsigned char staged_smem[];  // the dynamic shared memory
+    uint64_t* bars = reinterpret_cast<uint64_t*>(staged_smem);  // [stages] full, [stages] empty
+    E* stage0 = reinterpret_cast<E*>(staged_smem + 256);
     const int S = a.stages;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
