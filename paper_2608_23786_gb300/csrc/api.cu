@@ -224,7 +224,7 @@ WorkLayout work_layout(int N, int M)
     const size_t sfb = sf_axes_partial_bytes(N);
     wl.real = take(n * sizeof(double) > sfb ? n * sizeof(double) : sfb);
     wl.real2 = take(n * sizeof(double));
-    wl.twiddle = take((size_t)(N / 2) * 2 * sizeof(double));
+    wl.twiddle = take((size_t)N * 2 * sizeof(double));
     wl.trig = take((size_t)N * 4 * (sizeof(double) + sizeof(float)));  // FP64 table, then its FP32 copy
     size_t per = 2 * (size_t)(N / 2 + 1);
     if ((size_t)7 * (N / 2) > per) per = (size_t)7 * (N / 2);

@@ -22,7 +22,7 @@ struct WorkLayout {
     size_t cplx;      // complex FFT buffer [n] double2
     size_t real;      // power spectrum / autocorrelation [n] double
     size_t real2;     // power spectrum of the second sample of a pair [n] double
-    size_t twiddle;   // [N/2] double2
+    size_t twiddle;   // [N] double2: exp(-2 pi i j / N), j < N
     size_t trig;      // [N][4] double: sin, cos of x_n and 2 x_n; then the same [N][4] as float
     size_t bins;      // shell sums [2][N/2+1] double x M
     size_t total;

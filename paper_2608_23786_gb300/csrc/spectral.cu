@@ -1,12 +1,12 @@
 // Spectral statistics: FP64 3-D FFT, shell energy spectrum and the trace
 // second-order structure function of Algorithm "SF_spectral".
 //
-// FFT: complex-to-complex, radix-2, N a power of two.  A 3-D transform is three
-// passes of batched 1-D transforms, one per axis.  Each block stages a tile of
-// T lines in shared memory (T consecutive x for the y and z passes, so every
-// global access is a coalesced run of T complex values), applies the
-// bit-reversal permutation on load and log2 N butterfly stages in place, and
-// writes the tile back.  Twiddles exp(-2 pi i k / N) come from a table made
+// FFT: complex-to-complex, N a power of two.  A 3-D transform is three passes of
+// batched 1-D transforms, one per axis.  Each block stages a tile of T lines in
+// shared memory (T consecutive x for the y and z passes, so every global access is
+// a coalesced run of T complex values), applies the bit-reversal permutation on
+// load, the butterfly stages in place (radix-2^2: stages in pairs), and writes the
+// tile back.  Twiddles exp(-2 pi i k / N) come from a table made
 // once per context.  Real fields share complex transforms two at a time: samples
 // are taken in pairs (a, b), u_x + i u_y of each sample is one transform (only the
 // sum of the two powers is needed), and u_z of a with u_z of b is a third, whose two
@@ -35,6 +35,11 @@ __device__ __forceinline__ unsigned bitrev(unsigned v, int bits) { return __brev
 __device__ __forceinline__ double2 cmul(double2 a, double2 b)
 {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a conj(b)
+__device__ __forceinline__ double2 cmul_conj(double2 a, double2 b)
+{
+    return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 
 // Batched 1-D FFT of length N along one axis; `stride` is the element distance
@@ -68,30 +73,58 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pass(double2* __restrict__ 
         }
     }
     __syncthreads();
-    const int halfN = N >> 1;
-    for (int s = 0; s < logN; ++s) {
+    // Decimation in time on the bit-reversed tile, the stages in pairs as radix-2^2 butterflies
+    // (three twiddle products per four points where the two radix-2 stages take four; the first
+    // pair's twiddles are all 1): with w = W_{4h}^p for position p of a group of 4h points,
+    // t1 = w^2 x1, t2 = w x2, t3 = w^3 x3, the stages h and 2h give (x0 + t1) +- (t2 + t3) and
+    // (x0 - t1) -+ i (t2 - t3) (forward; the inverse conjugates w and i).  An odd log2 N ends with
+    // one radix-2 stage.  tw holds W_N^j for j < N.
+    const int quarterN = N >> 2;
+    int s = 0;
+    for (; s + 1 < logN; s += 2) {
         const int half = 1 << s;
-        const int twstep = halfN >> s;  // N / (2 half)
-        for (int b = threadIdx.x; b < T * halfN; b += blockDim.x) {
-            const int t = b / halfN, q = b % halfN;
+        const int tstep = N >> (s + 2);  // W_{4h}^k = W_N^{k tstep}
+        for (int b = threadIdx.x; b < T * quarterN; b += blockDim.x) {
+            const int t = b / quarterN, q = b % quarterN;
             const int pos = q & (half - 1);
-            const int i0 = ((q >> s) << (s + 1)) + pos;
-            const int i1 = i0 + half;
-            double2* L = buf + t * N;
-            const double2 u = L[i0];
-            const double2 x = L[i1];
-            double2 v;
-            if (s == 0) {  // twiddle 1
-                v = x;
-            } else if (s == 1) {  // twiddle 1 or -i (forward) / +i (inverse): a swap, exactly
-                v = pos == 0 ? x : (inverse ? make_double2(-x.y, x.x) : make_double2(x.y, -x.x));
-            } else {
-                double2 w = tw[pos * twstep];
-                if (inverse) w.y = -w.y;
-                v = cmul(x, w);
+            double2* L = buf + t * N + ((q >> s) << (s + 2)) + pos;
+            const double2 x0 = L[0];
+            double2 t1 = L[half], t2 = L[2 * half], t3 = L[3 * half];
+            if (half > 1) {  // uniform: the first pair has p = 0
+                const int j1 = pos * tstep;
+                if (inverse) {
+                    t1 = cmul_conj(t1, tw[2 * j1]);
+                    t2 = cmul_conj(t2, tw[j1]);
+                    t3 = cmul_conj(t3, tw[3 * j1]);
+                } else {
+                    t1 = cmul(t1, tw[2 * j1]);
+                    t2 = cmul(t2, tw[j1]);
+                    t3 = cmul(t3, tw[3 * j1]);
+                }
             }
-            L[i0] = make_double2(u.x + v.x, u.y + v.y);
-            L[i1] = make_double2(u.x - v.x, u.y - v.y);
+            const double2 a = make_double2(x0.x + t1.x, x0.y + t1.y), c = make_double2(x0.x - t1.x, x0.y - t1.y);
+            const double2 e = make_double2(t2.x + t3.x, t2.y + t3.y), d = make_double2(t2.x - t3.x, t2.y - t3.y);
+            L[0] = make_double2(a.x + e.x, a.y + e.y);
+            L[2 * half] = make_double2(a.x - e.x, a.y - e.y);
+            if (inverse) {  // c +- i d
+                L[half] = make_double2(c.x - d.y, c.y + d.x);
+                L[3 * half] = make_double2(c.x + d.y, c.y - d.x);
+            } else {  // c -+ i d
+                L[half] = make_double2(c.x + d.y, c.y - d.x);
+                L[3 * half] = make_double2(c.x - d.y, c.y + d.x);
+            }
+        }
+        __syncthreads();
+    }
+    if (s < logN) {  // the last stage, h = N/2: W_N^p
+        const int halfN = N >> 1;
+        for (int b = threadIdx.x; b < T * halfN; b += blockDim.x) {
+            const int t = b / halfN, pos = b % halfN;
+            double2* L = buf + t * N + pos;
+            const double2 u = L[0];
+            const double2 v = inverse ? cmul_conj(L[halfN], tw[pos]) : cmul(L[halfN], tw[pos]);
+            L[0] = make_double2(u.x + v.x, u.y + v.y);
+            L[halfN] = make_double2(u.x - v.x, u.y - v.y);
         }
         __syncthreads();
     }
@@ -110,7 +143,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_pass(double2* __restrict__ 
 
 __global__ void k_twiddles(double2* tw, int N)
 {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N / 2; k += gridDim.x * blockDim.x) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
         double s, c;
         sincospi(-2.0 * k / N, &s, &c);
         tw[k] = make_double2(c, s);
@@ -315,7 +348,7 @@ cudaError_t fft3d(const mclbm_ctx* c, double2* data, const double2* tw, int inve
 
 cudaError_t launch_twiddles(const mclbm_ctx* c)
 {
-    k_twiddles<<<grid_for(c->N / 2), 256, 0, c->stream>>>((double2*)(c->work + c->wl.twiddle), c->N);
+    k_twiddles<<<grid_for(c->N), 256, 0, c->stream>>>((double2*)(c->work + c->wl.twiddle), c->N);
     return cudaGetLastError();
 }
 
