@@ -28,11 +28,12 @@ namespace mclbm {
         else if ((sgn) < 0) acc -= (v); \
     } while (0)
 
-// Plain KBC on raw populations (in place).  Returns gamma.  Divisions are the costly FP64
-// operations here: 1/rho and the 1/f^eq_i of the inner products are each formed once (one
-// correctly rounded reciprocal each) and multiplied in, 20 divisions per node instead of 41.
+// Plain KBC on raw populations (in place).  Returns gamma.  a = 2/omega and b = 2 - 2/omega
+// are passed in (formed once on the host).  Divisions are the costly FP64 operations here: 1/rho
+// and the 1/f^eq_i of the inner products are each formed once (one correctly rounded reciprocal
+// each) and multiplied in, and tr(P)/3 is a product with 1/3: 21 divisions per node instead of 45.
 template <class T>
-__host__ __device__ __forceinline__ T kbc_raw(T (&f)[Q], T omega)
+__host__ __device__ __forceinline__ T kbc_raw(T (&f)[Q], T omega, T a, T b)
 {
     T rho = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
@@ -66,7 +67,7 @@ __host__ __device__ __forceinline__ T kbc_raw(T (&f)[Q], T omega)
         MCLBM_SIGNED_ADD(pxz, cx(i) * cz(i), fneq[i]);
         MCLBM_SIGNED_ADD(pyz, cy(i) * cz(i), fneq[i]);
     }
-    const T tr3 = (pxx + pyy + pzz) / T(3);
+    const T tr3 = (pxx + pyy + pzz) * (T(1) / T(3));
     T ds[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -87,7 +88,7 @@ __host__ __device__ __forceinline__ T kbc_raw(T (&f)[Q], T omega)
         sh += ds[i] * dhw;
         hh += dh * dhw;
     }
-    const T gamma = (hh == T(0)) ? T(2) : T(2) / omega - (T(2) - T(2) / omega) * sh / hh;
+    const T gamma = (hh == T(0)) ? T(2) : a - b * sh / hh;
     const T bo = T(0.5) * omega * gamma;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {

@@ -49,6 +49,7 @@ struct LevelArgs {
     float omega32;
     double omega64;
     float a32, b32;  // 2/omega and 2 - 2/omega of Eq. (entropyControl)
+    double a64, b64; // the same in FP64 (raw FP64 storage)
 };
 
 template <class E>
@@ -307,7 +308,7 @@ __device__ __forceinline__ void collide_run(typename Storage<E>::compute (&v)[Q]
             if constexpr (Storage<E>::shifted)
                 kbc_shifted<float, Ar>(t, omega, L.a32, L.b32);
             else
-                kbc_raw(t, omega);
+                kbc_raw(t, omega, (C)L.a64, (C)L.b64);
 #pragma unroll
             for (int i = 0; i < Q; ++i) v[i][k] = t[i];
         }
