@@ -93,8 +93,10 @@ void fill_level(LevelArgs<E>& L, const mclbm_ctx* c)
     L.omega64 = c->units.omega;
     L.a32 = (float)(2.0 / c->units.omega);
     L.b32 = (float)(2.0 - 2.0 / c->units.omega);
-    L.a64 = 2.0 / c->units.omega;
-    L.b64 = 2.0 - 2.0 / c->units.omega;
+    if constexpr (std::is_same<E, double>::value) {
+        L.a64 = 2.0 / c->units.omega;
+        L.b64 = 2.0 - 2.0 / c->units.omega;
+    }
 }
 
 template <class E>

@@ -39,8 +39,17 @@ namespace mclbm {
 
 
 
+// 2/omega and 2 - 2/omega of Eq. (entropyControl) in FP64, for raw FP64 storage only (an empty
+// base elsewhere: the FP32 and FP16 launch arguments keep their layout).
 template <class E>
-struct LevelArgs {
+struct LevelArgsFP64 {};
+template <>
+struct LevelArgsFP64<double> {
+    double a64, b64;
+};
+
+template <class E>
+struct LevelArgs : LevelArgsFP64<E> {
     const E* src;   // pull: current lattice; AA: the lattice
     E* dst;         // pull: next lattice; AA: same as src
     Geom g;
@@ -49,7 +58,6 @@ struct LevelArgs {
     float omega32;
     double omega64;
     float a32, b32;  // 2/omega and 2 - 2/omega of Eq. (entropyControl)
-    double a64, b64; // the same in FP64 (raw FP64 storage)
 };
 
 template <class E>
