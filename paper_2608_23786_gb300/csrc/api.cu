@@ -157,12 +157,13 @@ LaunchConfig default_launch(int precision, int pattern, int options)
 {
     if (options & MCLBM_OPT_EXACT_GAMMA) return LaunchConfig{exact_vec(precision), 128, 6};
 #ifdef MCLBM_D3Q27
-    // D3Q27 (measured at 128^3 x 32): FP32 prefetching kernel in blocks of 256; FP16 pull the
-    // shared-memory ring (81% with the row rotation, against 67% for the direct kernel), AA even
-    // steps the packed prefetching one in blocks of 256
+    // D3Q27 (measured at 128^3 x 32): FP32 prefetching kernel in blocks of 256; FP16 pull and AA
+    // even steps the shared-memory ring (pull 85% with the row rotation and the single-level
+    // kernel, against 67% for the direct kernel; AA even 89.0% against 87.7% for the packed
+    // prefetching kernel)
     if (precision == MCLBM_FP64) return LaunchConfig{1, 128, 0};
     if (precision == MCLBM_FP32) return LaunchConfig{2, 256, 2};
-    return pattern == MCLBM_PULL ? LaunchConfig{4, 128, 4} : LaunchConfig{4, 256, 3};
+    return LaunchConfig{4, 128, 4};
 #else
     if (precision == MCLBM_FP64) return LaunchConfig{2, 128, 0};
     if (precision == MCLBM_FP32) return LaunchConfig{2, 128, 3};
@@ -173,8 +174,8 @@ LaunchConfig default_launch(int precision, int pattern, int options)
 // AA odd steps read and write shifted rows and favour other shapes (measured per parity at
 // 128^3 x 32 and 64^3 x 64): D3Q19 FP32 the two-stage cp.async ring with 4 nodes per thread,
 // FP16 the packed prefetching kernel with 4; D3Q27 FP32 and FP16 the packed prefetching kernel in
-// blocks of 256 (D3Q27 FP16 with the row rotation at 128^3: 81.7% of the copy bandwidth, against
-// 52% for the one-node prefetching kernel without it).
+// blocks of 256 (D3Q27 FP16 with the row rotation at 128^3: 83.2% of the copy bandwidth, against
+// 80.7% for the ring and 52% for the one-node prefetching kernel without the rotation).
 // Nmax: the largest lattice the shape serves (a context's N, a batch's largest level): D3Q19 FP16
 // odd steps with Nmax <= 256 take the two-stage ring with 8 nodes per thread, whose rows of up to
 // 256 nodes lie within one warp and rotate (128^3 x 32: 81.4% of the copy bandwidth against 80.7%

@@ -131,18 +131,21 @@ __device__ __forceinline__ void async_finish_all(const unsigned char* smem, int 
 // FIX as in k_step_prefetch.  STAGES - 1 runs ahead are in flight; a thread's k-th run is
 // read from stage k mod STAGES.  Every thread commits one copy group per run slot (empty
 // past its last run), so wait_group STAGES - 1 always means "the current run has landed".
-template <class E, int VEC, int PATTERN, int BLOCK, int FIX, int STAGES, bool WRAP = false>
+// ONE: a single-level launch (the level's arguments at a compile-time index; see locate).
+template <class E, int VEC, int PATTERN, int BLOCK, int FIX, int STAGES, bool WRAP = false, bool ONE = false>
 __global__ void __launch_bounds__(BLOCK) k_step_async(const BatchArgs<E> args)
 {
     static_assert(Storage<E>::shifted, "the shared-memory prefetch variant serves the FP32 and FP16 storage");
     static_assert(sizeof(E) == 4 || VEC % 2 == 0, "FP16 runs must be whole 4-byte words");
     using C = typename Storage<E>::compute;
     using Ring = AsyncRing<E, VEC, BLOCK, STAGES>;
-    // the D3Q19 FP16 AA even step collides with the intrinsic arithmetic (the same bits; its
-    // schedule measured 86.7% -> 89.9% of the copy bandwidth at 128^3 x 32, while the other
-    // kernels keep the assembly form, which measured faster for them: FP16 AA odd 81.2% against
-    // 78.1%, FP32 pull 99.5% against 99.1%)
-    using Arith = std::conditional_t<Q == 19 && std::is_same<E, __half>::value && FIX == 1, lanes::Native, lanes::Asm>;
+    // the D3Q19 FP16 AA even step of a multi-level launch collides with the intrinsic arithmetic
+    // (the same bits; its schedule measured 86.7% -> 89.9% of the copy bandwidth at 128^3 x 32),
+    // every other kernel with the assembly form, which measured faster for them (FP16 AA odd 81.2%
+    // against 78.1%, FP32 pull 99.5% against 99.1%, the single-level FP16 even step 90.0% against
+    // 87.5%)
+    using Arith = std::conditional_t<Q == 19 && std::is_same<E, __half>::value && FIX == 1 && !ONE, lanes::Native,
+                                     lanes::Asm>;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int64_t total = args.prefix[args.nlev];
@@ -158,8 +161,8 @@ __global__ void __launch_bounds__(BLOCK) k_step_async(const BatchArgs<E> args)
     for (int s = 0; s < STAGES - 1; ++s) {
         const int64_t ts = t + s * stride;
         if (ts < total) {
-            loc[s] = locate<E, VEC>(args, ts, PATTERN);
-            const LevelArgs<E>& L = args.lev[loc[s].l];
+            loc[s] = locate<E, VEC, ONE>(args, ts, PATTERN);
+            const LevelArgs<E>& L = args.lev[ONE ? 0 : loc[s].l];
             async_issue_all<E, VEC, BLOCK, STAGES, FIX, WRAP>(L.src + (int64_t)loc[s].m * Q * L.g.n, L.g, loc[s], lane,
                                                              ring, s);
         }
@@ -171,8 +174,8 @@ __global__ void __launch_bounds__(BLOCK) k_step_async(const BatchArgs<E> args)
         const int64_t ta = t + (int64_t)(STAGES - 1) * stride;  // run to issue now
         RunLoc ahead = cur;
         if (ta < total) {
-            ahead = locate<E, VEC>(args, ta, PATTERN);
-            const LevelArgs<E>& La = args.lev[ahead.l];
+            ahead = locate<E, VEC, ONE>(args, ta, PATTERN);
+            const LevelArgs<E>& La = args.lev[ONE ? 0 : ahead.l];
             int sa = stage + STAGES - 1;
             if (sa >= STAGES) sa -= STAGES;
             async_issue_all<E, VEC, BLOCK, STAGES, FIX, WRAP>(La.src + (int64_t)ahead.m * Q * La.g.n, La.g, ahead, lane,
@@ -180,7 +183,7 @@ __global__ void __launch_bounds__(BLOCK) k_step_async(const BatchArgs<E> args)
         }
         cp_async_commit();
         cp_async_wait<STAGES - 1>();
-        const LevelArgs<E>& L = args.lev[cur.l];
+        const LevelArgs<E>& L = args.lev[ONE ? 0 : cur.l];
         const Geom g = L.g;
         C v[Q][VEC];
         async_finish_all<E, VEC, BLOCK, STAGES, FIX, WRAP>(smem, stage, threadIdx.x, g, cur, lane, v);

@@ -598,15 +598,20 @@ __device__ __forceinline__ void finish_all(const Geom& g, const RunLoc& p, int l
     }
 }
 
-template <class E, int VEC>
+// ONE: the launch has a single level (a context's own step), whose arguments are then read at a
+// compile-time index, which the compiler takes as constant operands instead of loading them into
+// registers by a run-time index.  Only the FP16 ring kernel uses it (see k_step_async).
+template <class E, int VEC, bool ONE = false>
 __device__ __forceinline__ RunLoc locate(const BatchArgs<E>& args, int64_t t, int pattern)
 {
     RunLoc p;
     int l = 0;
+    if constexpr (!ONE) {
 #pragma unroll 1
-    while (l + 1 < args.nlev && t >= args.prefix[l + 1]) ++l;
+        while (l + 1 < args.nlev && t >= args.prefix[l + 1]) ++l;
+    }
     const Geom& g = args.lev[l].g;
-    const int64_t first = (t - args.prefix[l]) * VEC;
+    const int64_t first = (ONE ? t : t - args.prefix[l]) * VEC;
     p.l = l;
     p.m = (int)(first >> (3 * g.logN));
     p.node = first & (g.n - 1);

@@ -95,10 +95,10 @@ cudaError_t launch_prefetch_variant(const BatchArgs<E>& a, int grid_cap, cudaStr
     }
 }
 
-template <class E, int VEC, int PATTERN, int BLOCK, int FIX, int STAGES, bool WRAP = false>
+template <class E, int VEC, int PATTERN, int BLOCK, int FIX, int STAGES, bool WRAP, bool ONE>
 cudaError_t launch_async_fixed(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, int* occupancy_out)
 {
-    auto kern = k_step_async<E, VEC, PATTERN, BLOCK, FIX, STAGES, WRAP>;
+    auto kern = k_step_async<E, VEC, PATTERN, BLOCK, FIX, STAGES, WRAP, ONE>;
     constexpr int smem = AsyncRing<E, VEC, BLOCK, STAGES>::kBytes;
     static int occ = -1;
     if (occ < 0) {
@@ -120,8 +120,8 @@ cudaError_t launch_async_fixed(const BatchArgs<E>& a, int grid_cap, cudaStream_t
     return cudaGetLastError();
 }
 
-template <class E, int VEC, int PATTERN, int BLOCK, int STAGES>
-cudaError_t launch_async_variant(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, int* occ)
+template <class E, int VEC, int PATTERN, int BLOCK, int STAGES, bool ONE>
+cudaError_t launch_async_levels(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, int* occ)
 {
     // steps with shifted rows (pull, AA odd) of FP16 storage take the row rotation where every
     // level's row lies within one warp (measured at 128^3 x 32 with 8 nodes per thread: FP16 pull
@@ -131,18 +131,31 @@ cudaError_t launch_async_variant(const BatchArgs<E>& a, int grid_cap, cudaStream
     const bool wrap = kWrapKind && rows_in_warp(a, VEC);
     if constexpr (PATTERN == 0) {
         if constexpr (kWrapKind)
-            if (wrap) return launch_async_fixed<E, VEC, 0, BLOCK, 0, STAGES, true>(a, grid_cap, s, occ);
-        return launch_async_fixed<E, VEC, 0, BLOCK, 0, STAGES>(a, grid_cap, s, occ);
+            if (wrap) return launch_async_fixed<E, VEC, 0, BLOCK, 0, STAGES, true, ONE>(a, grid_cap, s, occ);
+        return launch_async_fixed<E, VEC, 0, BLOCK, 0, STAGES, false, ONE>(a, grid_cap, s, occ);
     } else {
         const int par = launch_parity(a);
-        if (par == 0) return launch_async_fixed<E, VEC, 1, BLOCK, 1, STAGES>(a, grid_cap, s, occ);
+        if (par == 0) return launch_async_fixed<E, VEC, 1, BLOCK, 1, STAGES, false, ONE>(a, grid_cap, s, occ);
         if (par == 1) {
             if constexpr (kWrapKind)
-                if (wrap) return launch_async_fixed<E, VEC, 1, BLOCK, 2, STAGES, true>(a, grid_cap, s, occ);
-            return launch_async_fixed<E, VEC, 1, BLOCK, 2, STAGES>(a, grid_cap, s, occ);
+                if (wrap) return launch_async_fixed<E, VEC, 1, BLOCK, 2, STAGES, true, ONE>(a, grid_cap, s, occ);
+            return launch_async_fixed<E, VEC, 1, BLOCK, 2, STAGES, false, ONE>(a, grid_cap, s, occ);
         }
         return cudaErrorInvalidValue;
     }
+}
+
+// A launch of one level (a context's own step) of FP16 storage takes the single-level kernel
+// (measured at 128^3 x 32: D3Q19 pull 90.7% -> 94.4% of the copy bandwidth, AA even steps 89.6% ->
+// 90.0%, AA odd steps 81.4% -> 83.8%, D3Q27 pull 82.9% -> 85.1%); FP32 ring launches, and the
+// prefetching kernels, measured slower with it (FP32 AA odd steps 100.3% -> 92.4%; the prefetching
+// kernel's FP32 pull 99.6% -> 86.6%, D3Q27 FP16 AA even steps 87.7% -> 69.8%) and keep the level index.
+template <class E, int VEC, int PATTERN, int BLOCK, int STAGES>
+cudaError_t launch_async_variant(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, int* occ)
+{
+    if constexpr (std::is_same<E, __half>::value)
+        if (a.nlev == 1) return launch_async_levels<E, VEC, PATTERN, BLOCK, STAGES, true>(a, grid_cap, s, occ);
+    return launch_async_levels<E, VEC, PATTERN, BLOCK, STAGES, false>(a, grid_cap, s, occ);
 }
 
 template <class E, int PATTERN, int... VECS>
