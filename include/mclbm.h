@@ -88,8 +88,9 @@ typedef struct {
  * parameters stay the 24 coefficients X of s; the gradient of mclbm_grad is with respect to
  * them (the projection's transpose is applied). */
 #define MCLBM_OPT_LERAY 1
-/* MCLBM_OPT_EXACT_GAMMA: gamma is the exact minimiser of Eq. (kbc_entropy), the root of
- * sum Dh ln(f* / w) = 0 by safeguarded Newton iteration from the closed form (Eq.
+/* MCLBM_OPT_EXACT_GAMMA: gamma is the exact minimiser of Eq. (kbc_entropy) over
+ * 0 <= gamma <= 4 / omega, the root of sum Dh ln(f* / w) = 0 (or the nearer end of that range)
+ * by a safeguarded Newton (FP32) or Halley (FP64) iteration from the closed form (Eq.
  * (entropyControl)), in FP64 (FP64 storage) or FP32; the stepper then runs launch kind 6 (the
  * direct kernel).  mclbm_grad rejects contexts with this option. */
 #define MCLBM_OPT_EXACT_GAMMA 2

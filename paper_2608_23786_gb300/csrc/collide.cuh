@@ -525,64 +525,100 @@ __device__ __forceinline__ V kbc_shifted(V (&h)[Q], float omega, float a, float 
 // the root of G(g) = sum Dh_i ln(f*_i / w_i); G decreases (G' = -(omega / 2) sum Dh_i^2 / f*_i)
 // where every f*_i > 0, so the constrained minimiser is the root or the nearer end point.
 // Written with r_i = f*_i / w_i = 1 + am1_i - g b_i (b_i = (omega / 2) Dh_i / w_i):
-// safeguarded Newton from the closed form, keeping a bracket of the root and bisecting where a
-// Newton step leaves it.  T = double (FP64) or float (FP32).
+// safeguarded Newton (FP32) or Halley (FP64) iteration from the closed form, keeping a bracket
+// of the root and bisecting where a step leaves it.  T = double (FP64) or float (FP32).
 template <class T>
-__device__ __forceinline__ T log_ratio(T a_minus_one, T g, T b)
+__device__ __forceinline__ T log1p_of(T x)
 {
-    // ln(r) with r - 1 = a_minus_one - g b formed first, so that r close to 1 keeps its digits
     if constexpr (sizeof(T) == 8)
-        return log1p(a_minus_one - g * b);
+        return log1p(x);
     else
-        return log1pf(a_minus_one - g * b);
+        return log1pf(x);
 }
 
 template <class T>
 __device__ __forceinline__ T exact_gamma_refine(const T (&am1)[Q], const T (&b)[Q], T omega, T g0, int max_iter,
                                                 T rel_tol)
 {
-    // constrained interval: 0 <= g <= 4 / omega and every r_i = 1 + am1_i - g b_i > 0
+    // constrained interval: 0 <= g <= 4 / omega and every r_i = 1 + am1_i - g b_i > 0 (a
+    // division only where the positivity bound binds)
     T lo = T(0), hi = T(4) / omega;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        if (b[i] > T(0)) hi = fmin(hi, (T(1) + am1[i]) / b[i]);
-        else if (b[i] < T(0)) lo = fmax(lo, (T(1) + am1[i]) / b[i]);
+        const T a = T(1) + am1[i];
+        if (b[i] > T(0) && hi * b[i] > a) hi = a / b[i];
+        else if (b[i] < T(0) && lo * b[i] > a) lo = a / b[i];
     }
     if (!(lo < hi)) return g0;
     // H is convex along the line.  G = sum w_i b_i ln r_i equals -dH/dg up to a positive factor
-    // (sum w_i b_i = 0: Dh carries no mass), so G decreases with g, and G(hi) >= 0 means that H
-    // still decreases at hi.  Near equilibrium the minimiser lies beyond the interval (reading of
-    // the constrained exact gamma), so the upper end is tested first; the lower end only when the
-    // root lies below the start (G < 0 there: H increases, and G(lo) <= 0 puts the minimum at lo).
-    T G_hi = 0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) G_hi += weight<T>(i) * b[i] * log_ratio<T>(am1[i], hi, b[i]);
-    if (!(G_hi < T(0))) return hi;  // H decreases over the whole interval
+    // (sum w_i b_i = 0: Dh carries no mass), so G decreases with g: G(hi) >= 0 means that H still
+    // decreases at hi (the minimum is at hi), G(lo) <= 0 that it increases from lo.  The sign of G
+    // at a bracket end is known once an iterate has replaced that end; an end of the interval is
+    // evaluated (probe) only when a step would leave the bracket through it, since the closed-form
+    // start lies close to an interior root for most nodes.  One evaluation site serves the
+    // iterates and the probes (the sum is unrolled over the velocities with a logarithm each).
+    // FP64 takes Halley steps (G'' = -sum w_i b_i^3 / r_i^2), FP32 Newton steps; G' and G'' only
+    // steer the step, so FP32 forms b_i / r_i with the approximate division.
     const T eps = sizeof(T) == 8 ? T(2.220446049250313e-16) : T(1.1920929e-7);
     T g = (g0 > lo && g0 < hi) ? g0 : T(0.5) * (lo + hi);
-    bool lo_tested = false;
+    bool lo_known = false, hi_known = false;
+    int probe = 0;  // 0: G at the iterate g; 1: at hi; 2: at lo
     for (int it = 0; it < max_iter; ++it) {
-        T G = 0, Gp = 0, S = 0;
+        const T ge = probe == 0 ? g : (probe == 1 ? hi : lo);
+        T G = 0, Gp = 0, Gpp = 0, S = 0;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const T r = T(1) + am1[i] - g * b[i];
-            const T t = weight<T>(i) * b[i] * log_ratio<T>(am1[i], g, b[i]);
+            // r_i - 1 formed first, so that r close to 1 keeps its digits in the logarithm
+            const T x = am1[i] - ge * b[i];
+            const T wb = weight<T>(i) * b[i];
+            const T t = wb * log1p_of<T>(x);
             G += t;
             S += fabs(t);
-            Gp -= weight<T>(i) * b[i] * b[i] / r;
+            T q;  // b_i / r_i
+            if constexpr (sizeof(T) == 8)
+                q = b[i] / (T(1) + x);
+            else
+                q = __fdividef(b[i], T(1) + x);
+            Gp -= wb * q;
+            if constexpr (sizeof(T) == 8) Gpp -= wb * q * q;
         }
-        if (fabs(G) <= T(4 * Q) * eps * S) return g;  // G at the rounding level of its own terms
-        if (G < T(0) && !lo_tested) {  // the root, if any, lies below g: does H increase from lo?
-            lo_tested = true;
-            T G_lo = 0;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) G_lo += weight<T>(i) * b[i] * log_ratio<T>(am1[i], lo, b[i]);
-            if (!(G_lo > T(0))) return lo;
+        T gn;
+        if (probe != 0) {
+            if (probe == 1) {
+                if (!(G < T(0))) return hi;  // H decreases up to hi
+                hi_known = true;
+            } else {
+                if (!(G > T(0))) return lo;  // H increases from lo
+                lo_known = true;
+            }
+            probe = 0;
+            gn = T(0.5) * (lo + hi);
+        } else {
+            if (fabs(G) <= T(4 * Q) * eps * S) return g;  // G at the rounding level of its own terms
+            if (G > T(0)) {
+                lo = g;
+                lo_known = true;
+            } else {
+                hi = g;
+                hi_known = true;
+            }
+            gn = g - G / Gp;
+            if constexpr (sizeof(T) == 8) {
+                const T den = T(2) * Gp * Gp - G * Gpp;
+                if (den > T(0)) gn = g - T(2) * G * Gp / den;
+            }
+            if (!(gn > lo && gn < hi)) {
+                if (!(gn < hi) && !hi_known) {
+                    probe = 1;
+                    continue;
+                }
+                if (!(gn > lo) && !lo_known) {
+                    probe = 2;
+                    continue;
+                }
+                gn = T(0.5) * (lo + hi);
+            }
         }
-        if (G > T(0)) lo = g;
-        else hi = g;
-        T gn = g - G / Gp;
-        if (!(gn > lo && gn < hi)) gn = T(0.5) * (lo + hi);
         if (fabs(gn - g) <= rel_tol * fabs(g)) return gn;
         g = gn;
     }
@@ -645,7 +681,12 @@ __device__ __forceinline__ T kbc_exact(T (&f)[Q], T omega)
             s[i] = (sg > 0 ? T(0.25) : -T(0.25)) * inv_weight<T>(i) * p;
         }
         k[i] = n[i] - s[i];
-        const T wk = weight<T>(i) * k[i] / (T(1) + heq[i]);
+        // the closed form only starts the iteration: FP32 divides approximately
+        T wk;
+        if constexpr (sizeof(T) == 8)
+            wk = weight<T>(i) * k[i] / (T(1) + heq[i]);
+        else
+            wk = __fdividef(weight<T>(i) * k[i], T(1) + heq[i]);
         sh += wk * s[i];
         hh += wk * k[i];
     }

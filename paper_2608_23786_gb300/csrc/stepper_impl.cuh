@@ -284,14 +284,25 @@ __device__ __forceinline__ void collide_run(typename Storage<E>::compute (&v)[Q]
     const typename Storage<E>::compute omega = omega_of<E>(L);
     using C = typename Storage<E>::compute;
     if constexpr (EXACT) {  // exact entropic gamma (kind 6), node by node
-#pragma unroll
+        // one copy of the solver for the VEC nodes: a rolled loop whose node column is moved in
+        // and out of the register array by compile-time selects
+#pragma unroll 1
         for (int k = 0; k < VEC; ++k) {
             C t[Q];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) t[i] = v[i][k];
+            for (int i = 0; i < Q; ++i) {
+                t[i] = v[i][0];
+#pragma unroll
+                for (int kk = 1; kk < VEC; ++kk)
+                    if (k == kk) t[i] = v[i][kk];
+            }
             kbc_exact<C, Storage<E>::shifted>(t, omega);
 #pragma unroll
-            for (int i = 0; i < Q; ++i) v[i][k] = t[i];
+            for (int i = 0; i < Q; ++i) {
+#pragma unroll
+                for (int kk = 0; kk < VEC; ++kk)
+                    if (k == kk) v[i][kk] = t[i];
+            }
         }
     } else if constexpr (PACK) {
         static_assert(Storage<E>::shifted && VEC % 2 == 0, "packed collision needs FP32 lanes in pairs");
@@ -414,9 +425,12 @@ __device__ __forceinline__ void store_own_opp(E* base, const Geom& g, int64_t no
     }
 }
 
-// PATTERN: 0 pull, 1 AA.  EXACT: the exact entropic gamma (launch kind 6).
+// PATTERN: 0 pull, 1 AA.  EXACT: the exact entropic gamma (launch kind 6); its D3Q19 FP32 and
+// FP16 forms are held to four blocks per SM (128 registers: the Newton solve is latency-bound,
+// 16 warps per SM; the D3Q27 forms would spill).
 template <class E, int VEC, int PATTERN, int BLOCK, bool EXACT = false>
-__global__ void __launch_bounds__(BLOCK) k_step_batch(const BatchArgs<E> args)
+__global__ void __launch_bounds__(BLOCK, (EXACT && Q == 19 && sizeof(typename Storage<E>::compute) == 4) ? 4 : 1)
+    k_step_batch(const BatchArgs<E> args)
 {
     using C = typename Storage<E>::compute;
     const int lane = threadIdx.x & 31;

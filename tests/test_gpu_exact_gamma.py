@@ -1,6 +1,6 @@
 """The exact entropic gamma (option MCLBM_OPT_EXACT_GAMMA, Eq. (kbc_entropy)) on the GPU
-(safeguarded Newton) against the oracle's exact gamma (bisection): FP64 per population, FP32
-velocity error, D3Q27, and the option's launch and adjoint rules."""
+(safeguarded Newton / Halley) against the oracle's exact gamma (bisection): FP64 per population,
+FP32 and FP16 velocity error, D3Q27, and the option's launch and adjoint rules."""
 import numpy as np
 import pytest
 import torch
@@ -55,6 +55,40 @@ def test_fp32_exact_gamma_velocity_error():
     X = gen.draw_params(63, M)
     ens = Ensemble(N, M, Re=Re, Ma=Ma, precision="fp32", exact_gamma=True).init(X).step(steps)
     f, un = _oracle_exact(N, X, Re, Ma, steps)
+    _, u = oracle.moments(f)
+    got = np.stack([ens.moments(m)[1].cpu().numpy() for m in range(M)])
+    assert rel_l2(got, u / un["ulat"]) <= 1e-5
+
+
+@pytest.mark.parametrize("pattern", ["pull", "aa"])
+def test_fp32_exact_gamma_velocity_error_ma01(pattern):
+    """Larger deviations (Ma 0.1: |f*/w - 1| up to a few tenths) and both streaming patterns."""
+    N, M, Re, Ma, steps = 16, 2, 400.0, 0.1, 40
+    X = gen.draw_params(65, M)
+    ens = Ensemble(N, M, Re=Re, Ma=Ma, precision="fp32", pattern=pattern, exact_gamma=True).init(X).step(steps)
+    f, un = _oracle_exact(N, X, Re, Ma, steps)
+    _, u = oracle.moments(f)
+    got = np.stack([ens.moments(m)[1].cpu().numpy() for m in range(M)])
+    assert rel_l2(got, u / un["ulat"]) <= 1e-5
+
+
+def test_fp16_exact_gamma_velocity_error():
+    """FP16 storage with the exact gamma (collided in FP32): the storage rounding's bound."""
+    N, M, Re, Ma, steps = 32, 2, 800.0, 0.025, 100
+    X = gen.draw_params(66, M)
+    ens = Ensemble(N, M, Re=Re, Ma=Ma, precision="fp16", exact_gamma=True).init(X).step(steps)
+    assert mclbm.mclbm_get_launch(ens.ctx)[0] == 6
+    f, un = _oracle_exact(N, X, Re, Ma, steps)
+    _, u = oracle.moments(f)
+    got = np.stack([ens.moments(m)[1].cpu().numpy() for m in range(M)])
+    assert rel_l2(got, u / un["ulat"]) <= 1e-3
+
+
+def test_d3q27_fp32_exact_gamma_velocity_error():
+    N, M, Re, Ma, steps = 16, 2, 400.0, 0.1, 20
+    X = gen.draw_params(67, M)
+    ens = Ensemble(N, M, Re=Re, Ma=Ma, precision="fp32", exact_gamma=True, lattice=27).init(X).step(steps)
+    f, un = _oracle_exact(N, X, Re, Ma, steps, lattice=27)
     _, u = oracle.moments(f)
     got = np.stack([ens.moments(m)[1].cpu().numpy() for m in range(M)])
     assert rel_l2(got, u / un["ulat"]) <= 1e-5
