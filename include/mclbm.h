@@ -19,7 +19,10 @@
  *  - Every device call is enqueued on the CUDA stream given at creation (NULL =
  *    legacy default stream).  Calls that return host data synchronise that
  *    stream before returning; the others return as soon as work is enqueued.
- *  - A context may be used by one host thread at a time.
+ *  - A context may be used by one host thread at a time; contexts on several
+ *    devices may be used from one process.  A call on a context (or batch) runs on
+ *    the context's device, the device current at mclbm_create: the call makes it
+ *    current and restores the caller's current device before returning.
  *  - Arrays are C order.  A scalar field on the lattice is [z][y][x] (x fastest),
  *    node (x, y, z) at physical position 2 pi (x, y, z) / N.
  *  - Velocities returned by the library are physical: u_phys = u_lat U_c / U_lat.
@@ -235,7 +238,8 @@ MCLBM_API int mclbm_restrict(const mclbm_ctx* ctx, int32_t Q, double* d_out);
  * every point and component the 1-D W1 of the two empirical laws (L1 distance of the
  * empirical CDFs, Eq. (wassersteinPermutations) for equal M), summed over components
  * and averaged over points.  W: host scalar.  per_point: host [Q^3][3] or NULL.
- * Uses A's work buffer and stream; synchronises.  Errors: SHAPE. */
+ * A and B are on one device.  Uses A's work buffer and stream; synchronises.
+ * Errors: SHAPE; INVALID_ARG for contexts on different devices. */
 MCLBM_API int mclbm_w1_1pt(mclbm_ctx* A, const mclbm_ctx* B, int32_t Q, double* W, double* per_point);
 
 /* Same on restricted fields already on the device: d_a [MA][G][3], d_b [MB][G][3]

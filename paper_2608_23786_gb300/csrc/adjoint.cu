@@ -459,15 +459,11 @@ cudaError_t launch_adjoint_async(mclbm_ctx* c, const Geom& g, int64_t runs, cons
     constexpr int kStages = 2;
     auto kern = k_adjoint_async<E, VEC, kStages, WRAP>;
     constexpr int smem = AdjRing<E, VEC, kStages, WRAP>::kBytes;
-    static int occ = -1;
-    if (occ < 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        int o = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kRunBlock, smem);
-        if (e != cudaSuccess) return e;
-        occ = o > 0 ? o : 1;
-    }
+    static std::atomic<int> occ_cache[kMaxDevices];
+    int occ = 0;
+    const cudaError_t e = resident_blocks(kern, kRunBlock, smem, occ_cache, &occ);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
     int64_t blocks = (runs + kRunBlock - 1) / kRunBlock;
     if (blocks > (int64_t)c->num_sms * occ) blocks = (int64_t)c->num_sms * occ;
     kern<<<(unsigned)blocks, kRunBlock, smem, c->stream>>>((const E*)state, (const float*)lin, (float*)lout, g, runs,
@@ -712,6 +708,7 @@ int mclbm_grad(mclbm_ctx* ctx, int32_t objective, int64_t nsteps, int32_t ckpt_e
         return set_error(MCLBM_ERR_INVALID_ARG, "the adjoint covers the closed-form gamma only (not MCLBM_OPT_EXACT_GAMMA)");
     if (!ctx || !d_buf || !J || !dJdX || nsteps < 0 || ckpt_every < 1 || (objective != 0 && objective != 1))
         return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    MCLBM_ON_DEVICE(ctx->device);
     if (ctx->cfg.pattern != MCLBM_PULL) return set_error(MCLBM_ERR_INVALID_ARG, "the adjoint needs pull streaming");
     if (ctx->steps != 0) return set_error(MCLBM_ERR_INVALID_ARG, "mclbm_grad must directly follow an initialisation");
     if ((uintptr_t)d_buf & 255) return set_error(MCLBM_ERR_INVALID_ARG, "gradient buffer must be 256-byte aligned");
@@ -728,6 +725,7 @@ int mclbm_grad_timing(const mclbm_ctx* ctx, double* ms)
 int mclbm_adjoint_step(const mclbm_ctx* ctx, const double* d_f, const double* d_lambda_next, double* d_lambda)
 {
     if (!ctx || !d_f || !d_lambda_next || !d_lambda) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    MCLBM_ON_DEVICE(ctx->device);
     MCLBM_CUDA(launch_adjoint_natural(ctx, d_f, d_lambda_next, d_lambda));
     return MCLBM_OK;
 }

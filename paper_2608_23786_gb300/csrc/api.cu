@@ -367,6 +367,7 @@ static int do_init(mclbm_ctx* c)
 int mclbm_init_ensemble(mclbm_ctx* ctx, const double* params)
 {
     if (!ctx) return set_error(MCLBM_ERR_INVALID_ARG, "ctx is NULL");
+    MCLBM_ON_DEVICE(ctx->device);
     if (params) {
         for (size_t k = 0; k < ctx->params.size(); ++k) {
             if (!std::isfinite(params[k])) return set_error(MCLBM_ERR_INVALID_ARG, "params must be finite");
@@ -389,6 +390,7 @@ int mclbm_draw_params(uint64_t seed, int32_t first_sample, int32_t M, double wid
 int mclbm_init_tgv(mclbm_ctx* ctx)
 {
     if (!ctx) return set_error(MCLBM_ERR_INVALID_ARG, "ctx is NULL");
+    MCLBM_ON_DEVICE(ctx->device);
     std::fill(ctx->params.begin(), ctx->params.end(), 0.0);
     return do_init(ctx);
 }
@@ -410,6 +412,7 @@ int mclbm_get_params(const mclbm_ctx* ctx, double* params)
 int mclbm_step(mclbm_ctx* ctx, int64_t nsteps)
 {
     if (!ctx || nsteps < 0) return set_error(MCLBM_ERR_INVALID_ARG, "bad ctx or nsteps < 0");
+    MCLBM_ON_DEVICE(ctx->device);
     for (int64_t s = 0; s < nsteps; ++s) MCLBM_CUDA(launch_step(ctx));
     return MCLBM_OK;
 }
@@ -419,6 +422,7 @@ int64_t mclbm_steps_taken(const mclbm_ctx* ctx) { return ctx ? ctx->steps : -1; 
 int mclbm_get_populations(const mclbm_ctx* ctx, int32_t sample, double* d_out)
 {
     if (!ctx || !d_out || sample < 0 || sample >= ctx->M) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    MCLBM_ON_DEVICE(ctx->device);
     MCLBM_CUDA(launch_get_populations(ctx, sample, d_out));
     return MCLBM_OK;
 }
@@ -426,6 +430,7 @@ int mclbm_get_populations(const mclbm_ctx* ctx, int32_t sample, double* d_out)
 int mclbm_set_populations(mclbm_ctx* ctx, int32_t sample, const double* d_in)
 {
     if (!ctx || !d_in || sample < 0 || sample >= ctx->M) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    MCLBM_ON_DEVICE(ctx->device);
     MCLBM_CUDA(launch_set_populations(ctx, sample, d_in));
     return MCLBM_OK;
 }
@@ -433,6 +438,7 @@ int mclbm_set_populations(mclbm_ctx* ctx, int32_t sample, const double* d_in)
 int mclbm_moments(const mclbm_ctx* ctx, int32_t sample, double* d_rho, double* d_u)
 {
     if (!ctx || !d_u || sample < 0 || sample >= ctx->M) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    MCLBM_ON_DEVICE(ctx->device);
     MCLBM_CUDA(launch_moments(ctx, sample, d_rho, d_u));
     return MCLBM_OK;
 }
@@ -440,6 +446,7 @@ int mclbm_moments(const mclbm_ctx* ctx, int32_t sample, double* d_rho, double* d
 int mclbm_energy(mclbm_ctx* ctx, double* E, double* Z)
 {
     if (!ctx || !E) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    MCLBM_ON_DEVICE(ctx->device);
     MCLBM_CUDA(launch_energy(ctx, Z != nullptr, E, Z));
     return MCLBM_OK;
 }
@@ -447,6 +454,7 @@ int mclbm_energy(mclbm_ctx* ctx, double* E, double* Z)
 int mclbm_mean_var(mclbm_ctx* ctx, double* d_mean, double* d_var)
 {
     if (!ctx || !d_mean || !d_var) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    MCLBM_ON_DEVICE(ctx->device);
     if (ctx->M < 2) return set_error(MCLBM_ERR_SHAPE, "variance needs M >= 2");
     MCLBM_CUDA(launch_mean_var(ctx, d_mean, d_var));
     return MCLBM_OK;
@@ -455,6 +463,7 @@ int mclbm_mean_var(mclbm_ctx* ctx, double* d_mean, double* d_var)
 int mclbm_energy_mean_var(mclbm_ctx* ctx, double* E, double* d_mean, double* d_var)
 {
     if (!ctx || !E || !d_mean || !d_var) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    MCLBM_ON_DEVICE(ctx->device);
     if (ctx->M < 2) return set_error(MCLBM_ERR_SHAPE, "variance needs M >= 2");
     if (ctx->M > 1024) {  // the one-pass kernel reduces up to 1024 energies in shared memory
         MCLBM_CUDA(launch_mean_var(ctx, d_mean, d_var));
@@ -477,6 +486,7 @@ static int ensure_twiddles(mclbm_ctx* ctx)
 int mclbm_spectrum(mclbm_ctx* ctx, double* E)
 {
     if (!ctx || !E) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    MCLBM_ON_DEVICE(ctx->device);
     int st = ensure_twiddles(ctx);
     if (st != MCLBM_OK) return st;
     MCLBM_CUDA(launch_spectral(ctx, E, nullptr));
@@ -486,6 +496,7 @@ int mclbm_spectrum(mclbm_ctx* ctx, double* E)
 int mclbm_sf_trace(mclbm_ctx* ctx, double* S2)
 {
     if (!ctx || !S2) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    MCLBM_ON_DEVICE(ctx->device);
     int st = ensure_twiddles(ctx);
     if (st != MCLBM_OK) return st;
     MCLBM_CUDA(launch_spectral(ctx, nullptr, S2));
@@ -495,6 +506,7 @@ int mclbm_sf_trace(mclbm_ctx* ctx, double* S2)
 int mclbm_sf_axes(mclbm_ctx* ctx, int32_t pmax, double* S)
 {
     if (!ctx || !S || pmax < 2 || pmax > 8) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument (2 <= pmax <= 8)");
+    MCLBM_ON_DEVICE(ctx->device);
     if (ctx->N > 512) return set_error(MCLBM_ERR_SHAPE, "axis structure functions support N <= 512");
     MCLBM_CUDA(launch_sf_axes(ctx, pmax, S));
     return MCLBM_OK;
@@ -503,6 +515,7 @@ int mclbm_sf_axes(mclbm_ctx* ctx, int32_t pmax, double* S)
 int mclbm_restrict(const mclbm_ctx* ctx, int32_t Qd, double* d_out)
 {
     if (!ctx || !d_out || Qd < 1) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    MCLBM_ON_DEVICE(ctx->device);
     if (ctx->N % Qd != 0) return set_error(MCLBM_ERR_SHAPE, "N must be a multiple of Q");
     MCLBM_CUDA(launch_restrict(ctx, Qd, d_out));
     return MCLBM_OK;
@@ -524,6 +537,8 @@ int mclbm_w1_restricted(const double* d_a, int32_t MA, const double* d_b, int32_
 int mclbm_w1_1pt(mclbm_ctx* A, const mclbm_ctx* B, int32_t Qd, double* W, double* per_point)
 {
     if (!A || !B || !W || Qd < 1) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    if (A->device != B->device) return set_error(MCLBM_ERR_INVALID_ARG, "both ensembles must be on one device");
+    MCLBM_ON_DEVICE(A->device);
     if (A->N % Qd || B->N % Qd) return set_error(MCLBM_ERR_SHAPE, "N of both ensembles must be multiples of Q");
     if (Qd > 8) return set_error(MCLBM_ERR_SHAPE, "context W1 supports Q <= 8");
     if (B->M > kMaxW1Samples || A->M > kMaxW1Samples)
@@ -546,6 +561,7 @@ int mclbm_w1_1pt(mclbm_ctx* A, const mclbm_ctx* B, int32_t Qd, double* W, double
 int mclbm_device_status(mclbm_ctx* ctx)
 {
     if (!ctx) return set_error(MCLBM_ERR_INVALID_ARG, "ctx is NULL");
+    MCLBM_ON_DEVICE(ctx->device);
     int flags[2] = {0, 0};
     MCLBM_CUDA(cudaMemcpyAsync(flags, ctx->work + ctx->wl.flag, sizeof(flags), cudaMemcpyDeviceToHost, ctx->stream));
     MCLBM_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -557,6 +573,7 @@ int mclbm_device_status(mclbm_ctx* ctx)
 int mclbm_selftest_timeout(mclbm_ctx* ctx)
 {
     if (!ctx) return set_error(MCLBM_ERR_INVALID_ARG, "ctx is NULL");
+    MCLBM_ON_DEVICE(ctx->device);
     MCLBM_CUDA(launch_wait_selftest(ctx));
     return MCLBM_OK;
 }
@@ -585,6 +602,7 @@ bool same_dynamics(const mclbm_config& a, const mclbm_units& ua, const mclbm_con
 int mclbm_save(const mclbm_ctx* ctx, const char* path)
 {
     if (!ctx || !path) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    MCLBM_ON_DEVICE(ctx->device);
     const size_t bytes = ctx->elem_bytes * Q * (size_t)ctx->n * ctx->M;
     std::vector<char> host(bytes);
     MCLBM_CUDA(cudaMemcpyAsync(host.data(), lattice_ptr(ctx, ctx->cur), bytes, cudaMemcpyDeviceToHost, ctx->stream));
@@ -607,6 +625,7 @@ int mclbm_save(const mclbm_ctx* ctx, const char* path)
 int mclbm_load(mclbm_ctx* ctx, const char* path)
 {
     if (!ctx || !path) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    MCLBM_ON_DEVICE(ctx->device);
     FILE* fp = std::fopen(path, "rb");
     if (!fp) return set_error(MCLBM_ERR_IO, std::string("cannot open ") + path);
     uint64_t magic = 0, steps = 0;
@@ -658,6 +677,7 @@ int mclbm_load(mclbm_ctx* ctx, const char* path)
 int mclbm_check_finite(mclbm_ctx* ctx)
 {
     if (!ctx) return set_error(MCLBM_ERR_INVALID_ARG, "ctx is NULL");
+    MCLBM_ON_DEVICE(ctx->device);
     int bad = 0;
     MCLBM_CUDA(launch_check_finite(ctx, &bad));
     if (bad) return set_error(MCLBM_ERR_NONFINITE, "non-finite population found");

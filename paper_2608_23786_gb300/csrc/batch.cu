@@ -232,6 +232,7 @@ int mclbm_get_launch_parity(const mclbm_ctx* ctx, int32_t parity, int32_t* kind,
 int mclbm_autotune(mclbm_ctx* ctx, int32_t trial_steps, int32_t* kind, int32_t* vec, int32_t* block, double* best_ms)
 {
     if (!ctx || trial_steps < 1) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    MCLBM_ON_DEVICE(ctx->device);
     if (ctx->steps != 0) return set_error(MCLBM_ERR_INVALID_ARG, "autotune must directly follow an initialisation");
     // per candidate the time of its even and of its odd steps (one event pair per step; pull
     // steps all count as even).  AA: the fastest shape of each parity, unless the staged
@@ -341,7 +342,10 @@ int mclbm_batch_create(mclbm_ctx* const* levels, int32_t nlev, const int32_t* su
 void mclbm_batch_destroy(mclbm_batch* b)
 {
     if (!b) return;
-    clear_graphs(b);
+    {
+        const DeviceScope scope(b->lev[0]->device);
+        clear_graphs(b);
+    }
     delete b;
 }
 
@@ -357,6 +361,7 @@ int mclbm_batch_set_graph(mclbm_batch* b, int32_t enable)
 int mclbm_batch_set_launch(mclbm_batch* b, int32_t kind, int32_t vec, int32_t block)
 {
     if (!b) return set_error(MCLBM_ERR_INVALID_ARG, "batch is NULL");
+    MCLBM_ON_DEVICE(b->lev[0]->device);
     const LaunchConfig lc{vec, kind == 1 ? 0 : block, kind};
     for (auto* c : b->lev) {
         int st = check_shape(c, lc);
@@ -371,6 +376,7 @@ int mclbm_batch_set_launch(mclbm_batch* b, int32_t kind, int32_t vec, int32_t bl
 int mclbm_batch_set_launch_parity(mclbm_batch* b, int32_t parity, int32_t kind, int32_t vec, int32_t block)
 {
     if (!b) return set_error(MCLBM_ERR_INVALID_ARG, "batch is NULL");
+    MCLBM_ON_DEVICE(b->lev[0]->device);
     int st = set_parity_shape(b->lev, b->launch, b->launch_odd, parity, LaunchConfig{vec, kind == 1 ? 0 : block, kind});
     if (st != MCLBM_OK) return st;
     clear_graphs(b);
@@ -392,6 +398,7 @@ int mclbm_batch_get_launch_parity(const mclbm_batch* b, int32_t parity, int32_t*
 int mclbm_batch_step(mclbm_batch* b, int64_t macro_steps)
 {
     if (!b || macro_steps < 0) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    MCLBM_ON_DEVICE(b->lev[0]->device);
     while (macro_steps > 0) {
         if (b->use_graph && b->warmed && macro_steps >= b->period) {
             const auto sig = signature(b);
@@ -419,6 +426,7 @@ int mclbm_batch_step(mclbm_batch* b, int64_t macro_steps)
 int mclbm_batch_autotune(mclbm_batch* b, int32_t trials, int32_t* kind, int32_t* vec, int32_t* block, double* best_ms)
 {
     if (!b || trials < 1) return set_error(MCLBM_ERR_INVALID_ARG, "bad argument");
+    MCLBM_ON_DEVICE(b->lev[0]->device);
     for (auto* c : b->lev)
         if (c->steps != 0) return set_error(MCLBM_ERR_INVALID_ARG, "autotune must directly follow an initialisation");
     int prec = b->lev[0]->cfg.precision, Nmin = 1 << 30;

@@ -68,6 +68,37 @@ int cuda_check(cudaError_t e, const char* what);
         if (e_ != cudaSuccess) return ::mclbm::cuda_check(e_, #call); \
     } while (0)
 
+// Makes a context's device (the device current at its creation) current for the duration of a
+// call on it, and restores the caller's device afterwards.  A call whose switch fails returns
+// MCLBM_ERR_CUDA before it enqueues anything (MCLBM_ON_DEVICE).
+class DeviceScope {
+public:
+    explicit DeviceScope(int device)
+    {
+        if (cudaGetDevice(&prev_) != cudaSuccess) return;
+        if (prev_ == device) {
+            ok_ = true;
+        } else if (cudaSetDevice(device) == cudaSuccess) {
+            ok_ = switched_ = true;
+        }
+    }
+    ~DeviceScope()
+    {
+        if (switched_) cudaSetDevice(prev_);
+    }
+    bool ok() const { return ok_; }
+    DeviceScope(const DeviceScope&) = delete;
+    DeviceScope& operator=(const DeviceScope&) = delete;
+
+private:
+    int prev_ = -1;
+    bool ok_ = false, switched_ = false;
+};
+#define MCLBM_ON_DEVICE(device)                                                                         \
+    ::mclbm::DeviceScope mclbm_device_scope_(device);                                                   \
+    if (!mclbm_device_scope_.ok())                                                                      \
+        return ::mclbm::set_error(MCLBM_ERR_CUDA, "the context's device could not be made current")
+
 WorkLayout work_layout(int N, int M);
 
 // pointers of the population lattices

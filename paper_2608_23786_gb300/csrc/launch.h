@@ -3,12 +3,40 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <type_traits>
 
 namespace mclbm {
 
 constexpr int kMaxLevels = 8;  // levels of one batched launch
+
+// Launch facts of one kernel per device, filled on its first launch on each device: the kernel's
+// dynamic shared-memory limit is set there (a per-device attribute) and its resident blocks per
+// SM recorded.  Concurrent first launches may both fill a slot, with the same value.
+constexpr int kMaxDevices = 64;
+template <class K>
+cudaError_t resident_blocks(K kern, int block, int smem, std::atomic<int> (&cache)[kMaxDevices], int* occ)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::atomic<int>* slot = (dev >= 0 && dev < kMaxDevices) ? &cache[dev] : nullptr;
+    int o = slot ? slot->load(std::memory_order_acquire) : 0;
+    if (o > 0) {
+        *occ = o;
+        return cudaSuccess;
+    }
+    if (smem > 0) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, block, smem);
+    if (e != cudaSuccess) return e;
+    if (o > 0 && slot) slot->store(o, std::memory_order_release);
+    *occ = o;
+    return cudaSuccess;
+}
 
 struct LaunchConfig {
     int vec;       // nodes per thread along x

@@ -2,6 +2,8 @@
 // pattern.  Each stepper_<type>_<pattern>.cu translation unit includes this file
 // once, so the variants compile in parallel.
 #pragma once
+#include <mutex>
+
 #include "launch.h"
 #include "stepper_async.cuh"
 #include "stepper_impl.cuh"
@@ -13,13 +15,11 @@ template <class E, int VEC, int PATTERN, int BLOCK, bool EXACT = false>
 cudaError_t launch_variant(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, int* occupancy_out)
 {
     auto kern = k_step_batch<E, VEC, PATTERN, BLOCK, EXACT>;
-    static int occ = -1;  // resident blocks per SM of this variant (device-independent enough)
-    if (occ < 0) {
-        int o = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, BLOCK, 0);
-        if (e != cudaSuccess) return e;
-        occ = o > 0 ? o : 1;
-    }
+    static std::atomic<int> occ_cache[kMaxDevices];  // resident blocks per SM, per device
+    int occ = 0;
+    const cudaError_t e = resident_blocks(kern, BLOCK, 0, occ_cache, &occ);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
     if (occupancy_out) *occupancy_out = occ;
     const int64_t total = a.prefix[a.nlev];
     int64_t blocks = (total + BLOCK - 1) / BLOCK;
@@ -34,13 +34,11 @@ template <class E, int VEC, int PATTERN, int BLOCK, int FIX, bool PACK, bool WRA
 cudaError_t launch_prefetch_fixed(const BatchArgs<E>& a, int grid_cap, cudaStream_t s, int* occupancy_out)
 {
     auto kern = k_step_prefetch<E, VEC, PATTERN, BLOCK, FIX, PACK, WRAP>;
-    static int occ = -1;
-    if (occ < 0) {
-        int o = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, BLOCK, 0);
-        if (e != cudaSuccess) return e;
-        occ = o > 0 ? o : 1;
-    }
+    static std::atomic<int> occ_cache[kMaxDevices];
+    int occ = 0;
+    const cudaError_t e = resident_blocks(kern, BLOCK, 0, occ_cache, &occ);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
     if (occupancy_out) *occupancy_out = occ;
     const int64_t total = a.prefix[a.nlev];
     int64_t blocks = (total + BLOCK - 1) / BLOCK;
@@ -100,16 +98,11 @@ cudaError_t launch_async_fixed(const BatchArgs<E>& a, int grid_cap, cudaStream_t
 {
     auto kern = k_step_async<E, VEC, PATTERN, BLOCK, FIX, STAGES, WRAP, ONE>;
     constexpr int smem = AsyncRing<E, VEC, BLOCK, STAGES>::kBytes;
-    static int occ = -1;
-    if (occ < 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        int o = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, BLOCK, smem);
-        if (e != cudaSuccess) return e;
-        if (o < 1) return cudaErrorInvalidConfiguration;
-        occ = o;
-    }
+    static std::atomic<int> occ_cache[kMaxDevices];
+    int occ = 0;
+    const cudaError_t e = resident_blocks(kern, BLOCK, smem, occ_cache, &occ);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
     if (occupancy_out) *occupancy_out = occ;
     const int64_t total = a.prefix[a.nlev];
     int64_t blocks = (total + BLOCK - 1) / BLOCK;
@@ -230,12 +223,20 @@ cudaError_t launch_staged_variant(StagedArgs<E>& a, int grid_cap, cudaStream_t s
     stages = stages < 2 ? 2 : (stages > 4 ? 4 : stages);
     a.stages = stages;
     const size_t smem = 256 + (size_t)stages * stage_bytes;
-    static size_t configured = 0;
-    cudaError_t e;
-    if (smem > configured) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
+    // the dynamic shared-memory limit is a per-device attribute: the largest set so far, per device
+    static std::mutex mu;
+    static size_t configured[kMaxDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        const bool cached = dev >= 0 && dev < kMaxDevices;
+        if (!cached || smem > configured[dev]) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            if (cached) configured[dev] = smem;
+        }
     }
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kStagedThreads, smem);

@@ -130,7 +130,6 @@ cudaError_t launch_w1(const double* d_a, int MA, const double* d_b, int MB, int 
 // other host threads) share the array and race.
 
 constexpr int kNoAllocMaxPoints = 4096;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_w1_scratch[3 * kNoAllocMaxPoints + 32];
 
