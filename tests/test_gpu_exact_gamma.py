@@ -94,6 +94,20 @@ def test_d3q27_fp32_exact_gamma_velocity_error():
     assert rel_l2(got, u / un["ulat"]) <= 1e-5
 
 
+@pytest.mark.parametrize("pattern", ["pull", "aa"])
+def test_d3q27_fp16_exact_gamma_velocity_error(pattern):
+    """FP16 storage on D3Q27: four nodes per thread through the exact-gamma solver in turn."""
+    N, M, Re, Ma, steps = 16, 2, 400.0, 0.1, 20
+    X = gen.draw_params(68, M)
+    ens = Ensemble(N, M, Re=Re, Ma=Ma, precision="fp16", pattern=pattern, exact_gamma=True, lattice=27).init(X)
+    ens.step(steps)
+    assert mclbm.mclbm_get_launch(ens.ctx)[0] == 6
+    f, un = _oracle_exact(N, X, Re, Ma, steps, lattice=27)
+    _, u = oracle.moments(f)
+    got = np.stack([ens.moments(m)[1].cpu().numpy() for m in range(M)])
+    assert rel_l2(got, u / un["ulat"]) <= 1e-3
+
+
 def test_d3q27_fp64_exact_gamma_parity():
     N, M, Re, Ma, steps = 16, 2, 400.0, 0.1, 6
     X = gen.draw_params(64, M)
