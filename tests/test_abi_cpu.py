@@ -136,3 +136,26 @@ def test_leray_coefficient_map_against_fft_projection(lib):
     E = np.eye(24)
     L = mclbm.mclbm_leray_params(E).T  # column q = L e_q
     np.testing.assert_allclose(mclbm.mclbm_leray_params(E, transpose=True).T, L.T, atol=0)
+
+
+def _cuda_present():
+    import torch
+    return torch.cuda.is_available()
+
+
+@pytest.mark.skipif(_cuda_present(), reason="checks the failure without a GPU")
+def test_no_gpu_fails_loudly(lib):
+    """There is no CPU path: without a device, context creation reports the CUDA error (after the
+    host-side checks, before any buffer is touched) and Ensemble refuses to start."""
+    cfg = _cfg(N=16, M=2)
+    pop, work = mclbm.mclbm_required_bytes(cfg)
+    with pytest.raises(mclbm.MclbmError) as e:
+        mclbm.mclbm_create(cfg, 256, pop, 512, work)  # aligned stand-in addresses, never dereferenced
+    assert e.value.status == "CUDA"
+    assert "cudaGetDevice" in mclbm.mclbm_last_error()
+    with pytest.raises(mclbm.MclbmError) as e:  # the host checks come first: a short buffer is OOM
+        mclbm.mclbm_create(cfg, 256, pop - 1, 512, work)
+    assert e.value.status == "OOM"
+    from paper_2608_23786_gb300 import Ensemble
+    with pytest.raises(RuntimeError, match="CUDA"):
+        Ensemble(16, 2, Re=400.0, Ma=0.1)
