@@ -147,7 +147,7 @@ def oracle_sample(wl, budget_s=10.0, max_samples=2):
     return lu / dt / 1e9, desc, cores
 
 
-# Spec target and the other large configurations, measured after the default timed region
+# The 128^3 x 32 target shape and the other large configurations, measured after the default timed region
 # (each entry times its own stepper launches with CUDA events on the ensemble's stream, for about
 # half a second, with its own clock record).  (name, N, M, Re, Ma, precision, pattern)
 TARGETS = [("rtgv_128cube_x32_fp32_pull", 128, 32, 1600.0, 0.0125, "fp32", "pull"),
@@ -179,7 +179,7 @@ def _event_time(stream, fn, n):
 
 
 def measure_targets(dev, stream, peaks, peak_kind, lattice=19):
-    """The benchmark spec's target configuration (128^3 x 32, FP32 and FP16 shifted storage, pull and
+    """The 128^3 x 32 target configuration (FP32 and FP16 shifted storage, pull and
     AA), the 512^3 x 4 FP16 AA configuration, and the three-level batch (FP32 pull, FP16 AA),
     each with the library's default launch shape: GLUPS and HBM fraction of the stepper from
     CUDA events over whole steps (every step is one stepper launch; a batch macro step is one
